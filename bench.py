@@ -1,0 +1,323 @@
+#!/usr/bin/env python3
+"""Benchmark of the double FFT filter (arXiv:2305.01537, Sec. II.C) on GB300.
+
+One step = one application of the whole filter (theta pass, then phi pass) to every field of the
+28-field state of the Nr=128, Ntheta=64, Nphi=128 workload (29,360,128 points, FP64 in and out,
+470 MB of I/O: larger than the 126 MB L2, so no flush is needed between steps).
+
+Prints one JSON line. `value` is filtered points per second over all ranks (Gpoints/s), timed on
+the device with CUDA events around K steps after W warm-up steps, inputs already in HBM. `e2e`
+is the same metric through the host-buffer C-ABI call (sph_filter_apply_host), with the
+host->device copy of the state and the device->host copy of the result inside every step.
+
+--impl reference times the oracle (the plain CPU definition) on the host cores instead.
+Multi-GPU (torchrun): every rank filters its own copy of the state (independent shards, no
+data collective: weak scaling); the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2305_01537_gb300 import workloads as W  # noqa: E402
+
+HBM_FALLBACK_GBS = 6800.0
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": HBM_FALLBACK_GBS}, "fallback"
+
+
+def algorithmic_flops(grid) -> float:
+    """FFT-form flop count of one application: 5 log2(2 Ntheta) + 1 per point of a shell whose
+    theta pass is active, 5 log2(Nphi) + 1 per point of an active ring. Identity shells (exponential
+    or sharp filter with l_max >= Ntheta) and rings (m_max >= Nphi/2) cost nothing."""
+    flops = 0.0
+    th = (np.arange(grid.Ntheta) + 0.5) * math.pi / grid.Ntheta
+    for v in range(grid.nvars):
+        for i in range(grid.Nr):
+            lm = max(grid.floor, 2 * grid.r[i] / grid.dr_min * grid.L[v])
+            gauss = grid.kind[v] == W.GAUSS
+            if gauss or lm < grid.Ntheta:
+                flops += grid.Ntheta * grid.Nphi * (5 * math.log2(2 * grid.Ntheta) + 1)
+            mm = np.maximum(grid.floor, 2 * grid.r[i] / grid.dr_min * np.sin(th) * grid.L[v])
+            nact = grid.Ntheta if gauss else int((mm < grid.Nphi / 2).sum())
+            flops += nact * grid.Nphi * (5 * math.log2(grid.Nphi) + 1)
+    return flops
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons every 200 ms while running."""
+
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.window = None
+        self._stop = threading.Event()
+        self._proc = None
+
+    def __enter__(self):
+        try:
+            self._proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, FileNotFoundError):
+            self._proc = None
+        return self
+
+    def _read(self):
+        for line in self._proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append((time.time(), parts[1:]))
+
+    def mark(self, t0: float, t1: float):
+        """Keep only the samples taken between wall-clock times t0 and t1 (the timed region)."""
+        self.window = (t0, t1)
+
+    def __exit__(self, *exc):
+        if self._proc is not None:
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self._proc.kill()
+
+    def summary(self):
+        rows = [r for (t, r) in self.rows if self.window is None or self.window[0] <= t <= self.window[1] + 0.15]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.rows = rows
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[4 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows),
+                "power_w_max": max(float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit())
+                if any(r[2].replace(".", "").isdigit() for r in self.rows) else None}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(grid, x, seconds_target=10.0):
+    """The oracle as it stands, on all host cores, over a stratified sample of shells (every s-th
+    radial shell of every field), grown until it has run for about `seconds_target` seconds."""
+    import oracle
+    threads = oracle.max_threads()
+    stride = 16
+    total_pts, total_t = 0, 0.0
+    sample_shells = 0
+    while True:
+        idx = np.arange(0, grid.Nr, stride)
+        xs = np.ascontiguousarray(x[:, idx])
+        t0 = time.perf_counter()
+        oracle.filter(xs, grid.parity, grid.kind, grid.L, grid.r[idx], grid.dr_min, grid.floor)
+        dt = time.perf_counter() - t0
+        total_pts, total_t = xs.size, dt
+        sample_shells = xs.shape[0] * xs.shape[1]
+        if dt >= seconds_target / 4 or stride == 1:
+            break
+        stride = max(1, stride // 4)
+    return {"value": total_pts / total_t / 1e9, "unit": "Gpoints/s", "cores": threads, "kind": "oracle",
+            "sample": f"{sample_shells} shells (every {stride}th radial shell of all {grid.nvars} fields), "
+                      f"{total_pts} points in {total_t:.2f} s"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import oracle
+    wl = W.full_state_128x64x128()
+    g = wl.grids[0]
+    x = wl.state()
+    threads = oracle.max_threads()
+    # each step: a bounded sample (every 16th radial shell of every field)
+    idx = np.arange(0, g.Nr, 16)
+    xs = np.ascontiguousarray(x[:, idx])
+    for _ in range(args.warmup):
+        oracle.filter(xs, g.parity, g.kind, g.L, g.r[idx], g.dr_min, g.floor)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.filter(xs, g.parity, g.kind, g.L, g.r[idx], g.dr_min, g.floor)
+    dt = time.perf_counter() - t0
+    value = xs.size * args.steps / dt / 1e9
+    line = {
+        "impl": "reference", "metric": "filtered Gpoints/s (theta+phi double FFT filter, FP64 I/O)",
+        "value": value, "unit": "Gpoints/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "Nr": g.Nr, "Ntheta": g.Ntheta, "Nphi": g.Nphi, "nvars": g.nvars,
+                   "sample_per_step": f"{xs.shape[1]} of {g.Nr} radial shells x {g.nvars} fields"},
+        "cpu_baseline": {"value": value, "unit": "Gpoints/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{xs.shape[0] * xs.shape[1]} shells per step ({xs.size} points)"},
+        "e2e": {"value": value, "unit": "Gpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="f64", choices=["f64", "f32x2", "tc"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2305_01537_gb300 import Plan, SPH_PREC_F64, SPH_PREC_F32X2, SPH_PREC_SPLIT_TC
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    prec = {"f64": SPH_PREC_F64, "f32x2": SPH_PREC_F32X2, "tc": SPH_PREC_SPLIT_TC}[args.precision]
+
+    wl = W.full_state_128x64x128()
+    g = wl.grids[0]
+    x_host = torch.from_numpy(wl.state()).pin_memory()
+    x = x_host.cuda()
+    y = torch.empty_like(x)
+    plan = Plan.from_grid(g, precision=prec)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    clk = ClockSampler(local).__enter__()
+    time.sleep(0.5)  # let nvidia-smi start sampling before the timed region
+    for _ in range(args.warmup):
+        plan.apply(x, out=y)
+    torch.cuda.synchronize()
+
+    # device-resident timing: one event pair per launch on the launching stream
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    wall0 = time.time()
+    if True:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for k in range(args.steps):
+            evs[k][0].record(stream)
+            plan.apply(x, out=y)
+            evs[k][1].record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    wall1 = time.time()
+    clk.mark(wall0, wall1)
+    clk.__exit__(None, None, None)
+    elapsed_ms = t_start.elapsed_time(t_end)
+    kernel_ms = [a.elapsed_time(b) for a, b in evs]
+    assert plan.sync_status() == 0
+
+    # end to end through the host-buffer entry point
+    out_host = torch.empty_like(x_host).pin_memory()
+    for _ in range(args.warmup):
+        plan.apply_host(x_host, out_host)
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.apply_host(x_host, out_host)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+
+    if world > 1:
+        t = torch.tensor([elapsed_ms, e2e_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms, e2e_ms = float(t[0]), float(t[1])
+
+    points = g.points
+    value = world * points * args.steps / (elapsed_ms * 1e-3) / 1e9
+    e2e_value = world * points * args.steps / (e2e_ms * 1e-3) / 1e9
+    if rank == 0:
+        peaks, src = measured_peaks()
+        avg_kernel_s = statistics.mean(kernel_ms) * 1e-3
+        bytes_per_launch = 16.0 * points
+        hbm_gbs = bytes_per_launch / avg_kernel_s / 1e9
+        flops = algorithmic_flops(g)
+        tflops = flops / avg_kernel_s / 1e12
+        traffic = None
+        tp = os.path.join(ROOT, "profiles", "traffic.json")
+        if os.path.exists(tp):
+            with open(tp) as f:
+                traffic = json.load(f).get(f"{args.precision}:{wl.name}")
+        if args.precision == "f64":
+            roof = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
+                    "peak_source": "FP64 FMA: 152 SMs x 2/clk x 2 flop x 2.07 GHz (recipe's 1.25 TFLOP/s)",
+                    "kernel": "plain_shell_kernel<double>", "flops_per_launch": flops}
+        else:
+            roof = {"bound": "hbm", "achieved": hbm_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": hbm_gbs / peaks["hbm_gbs"], "traffic": traffic,
+                    "peak_source": f"hbm_gbs of {src}", "bytes_per_launch": bytes_per_launch}
+        line = {
+            "metric": "filtered Gpoints/s (theta+phi double FFT filter, FP64 I/O)",
+            "value": value, "unit": "Gpoints/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "Nr": g.Nr, "Ntheta": g.Ntheta, "Nphi": g.Nphi, "nvars": g.nvars,
+                       "precision": args.precision, "l2": "inputs (235 MB) larger than L2; no flush",
+                       "parallelism": f"independent shards x{world}"},
+            "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": peaks["hbm_gbs"], "frac": hbm_gbs / peaks["hbm_gbs"],
+                    "peak_source": src, "bytes_per_point": 16},
+            "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": "Gpoints/s", "h2d_bytes_per_step": 8 * points,
+                    "d2h_bytes_per_step": 8 * points},
+            "gpu_launches": args.steps * plan.launches,
+            "clocks": clk.summary(),
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(g, x_host.numpy())
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,141 @@
+/*
+ * sph_filter — double FFT filter for fields on a spherical (r, theta, phi) grid, on one GB300 GPU.
+ *
+ * The operation is the filter of Ji et al., arXiv:2305.01537, Sec. II.C "Filtering algorithms":
+ * every evolved field is first low-passed in theta, on the double-covered great circle made by
+ * joining the meridians at phi and phi + pi (with the field's parity sign across the pole), and
+ * then low-passed in phi on every (r, theta) ring. Each Fourier mode is multiplied by a filter
+ * function f(|l|, l_max) (exponential, Gaussian or spectrally sharp) whose cutoffs
+ *     l_max = max(floor, 2 r / dr_min * L),   m_max = max(floor, 2 r / dr_min * sin(theta) * L)
+ * depend on the shell radius r and (for phi) on the colatitude theta.
+ *
+ * Conventions shared by every entry point:
+ *  - A state is `nvars * Nr * Ntheta * Nphi` contiguous values in the layout
+ *    [var][shell i][theta index j][phi index k], k fastest. theta_j = (j + 1/2) pi / Ntheta
+ *    (cell centred), phi_k = 2 pi k / Nphi. Nphi must be even (the phi + pi pairing).
+ *  - Device pointers are caller-owned CUDA device memory on the plan's device. `in == out`
+ *    (in place) is allowed; any other overlap is rejected with SPH_EALIAS.
+ *  - Calls are asynchronous on `stream` (NULL = the legacy default stream) and return after
+ *    enqueueing. Argument errors are returned immediately and nothing is enqueued. Errors a
+ *    kernel detects on the device are latched in the plan and reported by
+ *    sph_filter_plan_sync_status().
+ *  - There is no CPU fallback: without a usable CUDA device every call fails with SPH_ECUDA.
+ *  - The plan is immutable after creation; concurrent calls on different streams with the same
+ *    plan are allowed.
+ */
+#ifndef SPH_FILTER_H
+#define SPH_FILTER_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+/* A cudaStream_t. */
+typedef struct CUstream_st* sph_stream_t;
+
+/* Opaque plan, created by sph_filter_plan_create and owned by the library until destroyed. */
+typedef struct sph_filter_plan_s* sph_filter_plan;
+
+typedef enum {
+  SPH_OK = 0,
+  SPH_EINVAL = 1,       /* invalid argument (sizes, parity, kind, cutoff parameters, NULL) */
+  SPH_ENOMEM = 2,       /* device or host allocation failed */
+  SPH_ECUDA = 3,        /* a CUDA runtime call failed (no device, launch failure, ...) */
+  SPH_EUNSUPPORTED = 4, /* valid request this build cannot run (e.g. a shell too large) */
+  SPH_ETIMEOUT = 5,     /* a bounded device-side wait gave up (latched by the device) */
+  SPH_EALIAS = 6,       /* input and output partially overlap */
+  SPH_EDEVICE = 7       /* a kernel latched an internal consistency error */
+} sph_status;
+
+/* Filter functions (Sec. II.C):
+ *  SPH_FILTER_EXP   Eq. (exp_filter): 1 for |l| <= l_max, exp(-(|l| - l_max)) above.
+ *  SPH_FILTER_GAUSS Eq. (gaussian_filter): exp(log(0.9) (l / (l_max + 1))^2) for every l.
+ *  SPH_FILTER_SHARP the spectrally sharp low-pass: 1 for |l| <= l_max, 0 above. */
+typedef enum { SPH_FILTER_EXP = 0, SPH_FILTER_GAUSS = 1, SPH_FILTER_SHARP = 2 } sph_kind;
+
+/* Arithmetic of the plan's kernels. Inputs and outputs are FP64 for every choice.
+ *  SPH_PREC_F64     plain form: FFTs in FP64 arithmetic.
+ *  SPH_PREC_F32X2   plain form with FFTs in compensated FP32-pair arithmetic (about 48-bit
+ *                   significands).
+ *  SPH_PREC_SPLIT_TC split-precision tensor-core form. */
+typedef enum { SPH_PREC_F64 = 0, SPH_PREC_SPLIT_TC = 1, SPH_PREC_F32X2 = 2 } sph_precision;
+
+/* Cutoff parameters (Sec. II.C, cutoff equations), copied into the plan at creation. */
+typedef struct {
+  const double* r;  /* [Nr] physical radius of each shell (any radial map already applied), >= 0 */
+  double dr_min;    /* smallest radial spacing of the grid, > 0 */
+  const double* L;  /* [nvars] the calligraphic-L factor per field, > 0 (paper: 3 metric, 12 matter) */
+  const int* kind;  /* [nvars] sph_kind per field */
+  double floor;     /* lower bound of l_max and m_max; the paper's value is 2; >= 0 */
+  int precision;    /* sph_precision */
+} sph_cutoff_params;
+
+/* Create a plan for states of nvars fields on an Nr x Ntheta x Nphi grid, on the current CUDA
+ * device. parity[v] in {0, 1} is the axis parity exponent a of field v in the double covering
+ * X(vartheta) = (-1)^a X(2 pi - vartheta, phi + pi) (Sec. II.C). Builds the cutoff tables
+ * (l_max per shell and field class, m_max per ring and class) and the twiddle tables in FP64 on
+ * the host and copies them to the device. *out is set to NULL on failure.
+ * Errors: SPH_EINVAL (Nr, Ntheta, nvars < 1; Nphi < 2 or odd; parity not 0/1; kind unknown;
+ * dr_min <= 0; r < 0; L <= 0; floor < 0; precision unknown; NULL pointer), SPH_ENOMEM, SPH_ECUDA. */
+sph_status sph_filter_plan_create(sph_filter_plan* out, int Nr, int Ntheta, int Nphi, int nvars,
+                                  const int* parity, const sph_cutoff_params* params);
+
+/* Release the plan and its device tables. Synchronises the plan's device first. NULL is a no-op. */
+void sph_filter_plan_destroy(sph_filter_plan plan);
+
+/* out = F in: the double filter (theta pass on the double-covered circles, then the phi pass on
+ * the rings), Sec. II.C. in/out: device FP64 states in the layout above. */
+sph_status sph_filter_apply(sph_filter_plan plan, const double* in, double* out, sph_stream_t stream);
+
+/* out = F^T in: the transpose of the filter, i.e. the phi pass followed by the theta pass (each
+ * pass is a real symmetric operator: a circulant with an even real multiplier, conjugated by the
+ * signed doubling permutation). Used for reverse-mode differentiation. */
+sph_status sph_filter_apply_adjoint(sph_filter_plan plan, const double* in, double* out,
+                                    sph_stream_t stream);
+
+/* Pointwise maps fused into the filter for a chain x_{k+1} = F(tanh(x_k)) (Sec. II.C's filter
+ * composed with an elementwise nonlinearity):
+ *   sph_filter_apply_tanh:          out = F(tanh(z))
+ *   sph_filter_apply_adjoint_tanh:  out = (1 - tanh(z)^2) * F^T(g)    (chain rule through tanh)
+ * z, g, out are device FP64 states; out may alias g (not z). */
+sph_status sph_filter_apply_tanh(sph_filter_plan plan, const double* z, double* out,
+                                 sph_stream_t stream);
+sph_status sph_filter_apply_adjoint_tanh(sph_filter_plan plan, const double* g, const double* z,
+                                         double* out, sph_stream_t stream);
+
+/* FP32 input/output variants of the four calls above (FP32 arithmetic inside). */
+sph_status sph_filter_apply_f32(sph_filter_plan plan, const float* in, float* out, sph_stream_t stream);
+sph_status sph_filter_apply_adjoint_f32(sph_filter_plan plan, const float* in, float* out,
+                                        sph_stream_t stream);
+sph_status sph_filter_apply_tanh_f32(sph_filter_plan plan, const float* z, float* out,
+                                     sph_stream_t stream);
+sph_status sph_filter_apply_adjoint_tanh_f32(sph_filter_plan plan, const float* g, const float* z,
+                                             float* out, sph_stream_t stream);
+
+/* End-to-end variant for host-resident states: copies host_in to the device, filters, copies
+ * the result to host_out, all on `stream`, and returns after enqueueing. host_in/host_out should
+ * be page-locked for the copies to overlap. The device staging buffers are allocated by the plan
+ * on first use and kept until the plan is destroyed. Synchronise the stream before reading
+ * host_out. Errors as sph_filter_apply, plus SPH_ENOMEM. */
+sph_status sph_filter_apply_host(sph_filter_plan plan, const double* host_in, double* host_out,
+                                 sph_stream_t stream);
+
+/* Wait for all work on the plan's device and return the first error a kernel latched for this
+ * plan (SPH_OK if none), then clear it. */
+sph_status sph_filter_plan_sync_status(sph_filter_plan plan);
+
+/* Number of filtered points per application: nvars * Nr * Ntheta * Nphi (0 for NULL). */
+long long sph_filter_plan_points(sph_filter_plan plan);
+
+/* Number of kernel launches one sph_filter_apply enqueues for this plan. */
+int sph_filter_plan_launches(sph_filter_plan plan);
+
+/* Static description of a status code. */
+const char* sph_filter_status_string(sph_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPH_FILTER_H */

@@ -1,0 +1,334 @@
+// C ABI of the double FFT filter library: plan creation (argument validation, FP64 cutoff and
+// twiddle tables built on the host), the apply entry points and status handling.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+namespace sph {
+
+int max_smem_optin(int device) {
+  int v = 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) return 0;
+  return v;
+}
+
+cudaError_t set_plain_smem_attr(size_t bytes);
+
+namespace {
+
+// Radix order for a length: 8s, then 4, 2, 3, then any remaining prime (direct DFT stage).
+bool factorize(int n, Factors* f) {
+  f->n = n;
+  f->nst = 0;
+  int m = n;
+  auto push = [&](int r) {
+    if (f->nst >= kMaxStages) return false;
+    f->radix[f->nst++] = r;
+    m /= r;
+    return true;
+  };
+  while (m % 8 == 0) if (!push(8)) return false;
+  while (m % 4 == 0) if (!push(4)) return false;
+  while (m % 2 == 0) if (!push(2)) return false;
+  while (m % 3 == 0) if (!push(3)) return false;
+  for (int p = 5; m > 1; p += 2) {
+    while (m % p == 0) {
+      if (p > 64) return false;  // the direct-DFT stage is limited to radix 64
+      if (!push(p)) return false;
+    }
+    if ((long)p * p > m && m > 1) {
+      if (m > 64) return false;
+      if (!push(m)) return false;
+    }
+  }
+  return true;
+}
+
+// exp(-2 pi i n / N) for n < N, evaluated in long double and rounded once.
+std::vector<double2> twiddles(int N) {
+  std::vector<double2> t((size_t)N);
+  const long double twopi = 2.0L * acosl(-1.0L);
+  for (int n = 0; n < N; ++n) {
+    const long double a = twopi * (long double)n / (long double)N;
+    t[(size_t)n] = make_double2((double)cosl(a), (double)(-sinl(a)));
+  }
+  return t;
+}
+
+// Cutoffs of Sec. II.C evaluated with the same double operations, in the same order, as the
+// plain definition: l_max = max(floor, 2 r / dr_min L); m_max = max(floor, 2 r / dr_min sin(theta) L).
+double lmax_of(double r, double dr_min, double L, double floor_) {
+  const double v = 2 * r / dr_min * L;
+  return v > floor_ ? v : floor_;
+}
+double mmax_of(double r, double dr_min, double L, double floor_, int j, int Nth) {
+  const double pi = std::acos(-1.0);
+  const double theta = ((double)j + 0.5) * pi / (double)Nth;
+  const double v = 2 * r / dr_min * std::sin(theta) * L;
+  return v > floor_ ? v : floor_;
+}
+
+bool overlaps_partially(const void* a, const void* b, size_t bytes) {
+  if (a == b) return false;
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return x < y + bytes && y < x + bytes;
+}
+
+template <typename T>
+sph_status upload(T** dst, const T* src, size_t n) {
+  if (cudaMalloc((void**)dst, sizeof(T) * std::max<size_t>(n, 1)) != cudaSuccess) return SPH_ENOMEM;
+  if (n && cudaMemcpy(*dst, src, sizeof(T) * n, cudaMemcpyHostToDevice) != cudaSuccess) return SPH_ECUDA;
+  return SPH_OK;
+}
+
+void free_plan(sph_filter_plan_s* p) {
+  if (!p) return;
+  cudaFree(p->d_lmax);
+  cudaFree(p->d_mmax);
+  cudaFree(p->d_var);
+  cudaFree(p->d_tw_th);
+  cudaFree(p->d_tw_ph);
+  cudaFree(p->d_status);
+  cudaFree(p->d_stage_in);
+  cudaFree(p->d_stage_out);
+  delete p;
+}
+
+sph_status check_io(const sph_filter_plan_s* p, const void* in, const void* out, size_t elem) {
+  if (!p || !in || !out) return SPH_EINVAL;
+  const size_t bytes = elem * (size_t)p->nvars * p->Nr * p->Nth * p->Nph;
+  if (overlaps_partially(in, out, bytes)) return SPH_EALIAS;
+  return SPH_OK;
+}
+
+sph_status launch(sph_filter_plan p, const void* in, const void* aux, void* out, int map_in, int map_out,
+                  int transpose, int is_f32, sph_stream_t stream) {
+  sph_status st = check_io(p, in, out, is_f32 ? sizeof(float) : sizeof(double));
+  if (st != SPH_OK) return st;
+  if (map_out == kOutTanhGrad) {
+    if (!aux) return SPH_EINVAL;
+    if (aux == out) return SPH_EALIAS;
+    st = check_io(p, aux, out, is_f32 ? sizeof(float) : sizeof(double));
+    if (st != SPH_OK) return st;
+  }
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return SPH_ECUDA;
+  if (cur != p->device && cudaSetDevice(p->device) != cudaSuccess) return SPH_ECUDA;
+  LaunchIO io{in, aux, out, map_in, map_out, transpose, is_f32};
+  cudaError_t e = launch_plain(*p, io, (cudaStream_t)stream);
+  if (cur != p->device) cudaSetDevice(cur);
+  return e == cudaSuccess ? SPH_OK : SPH_ECUDA;
+}
+
+}  // namespace
+}  // namespace sph
+
+using namespace sph;
+
+extern "C" {
+
+sph_status sph_filter_plan_create(sph_filter_plan* out, int Nr, int Ntheta, int Nphi, int nvars,
+                                  const int* parity, const sph_cutoff_params* prm) {
+  if (!out) return SPH_EINVAL;
+  *out = nullptr;
+  if (!parity || !prm || !prm->r || !prm->L || !prm->kind) return SPH_EINVAL;
+  if (Nr < 1 || Ntheta < 1 || nvars < 1 || Nphi < 2 || (Nphi % 2) != 0) return SPH_EINVAL;
+  if (!(prm->dr_min > 0) || !(prm->floor >= 0) || !std::isfinite(prm->dr_min) || !std::isfinite(prm->floor))
+    return SPH_EINVAL;
+  if (prm->precision != SPH_PREC_F64 && prm->precision != SPH_PREC_SPLIT_TC && prm->precision != SPH_PREC_F32X2)
+    return SPH_EINVAL;
+  for (int v = 0; v < nvars; ++v) {
+    if (parity[v] != 0 && parity[v] != 1) return SPH_EINVAL;
+    if (prm->kind[v] < SPH_FILTER_EXP || prm->kind[v] > SPH_FILTER_SHARP) return SPH_EINVAL;
+    if (!(prm->L[v] > 0) || !std::isfinite(prm->L[v])) return SPH_EINVAL;
+  }
+  for (int i = 0; i < Nr; ++i)
+    if (!(prm->r[i] >= 0) || !std::isfinite(prm->r[i])) return SPH_EINVAL;
+  if (prm->precision != SPH_PREC_F64) return SPH_EUNSUPPORTED;
+
+  sph_filter_plan_s* p = new (std::nothrow) sph_filter_plan_s();
+  if (!p) return SPH_ENOMEM;
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    delete p;
+    return SPH_ECUDA;
+  }
+  p->Nr = Nr;
+  p->Nth = Ntheta;
+  p->Nph = Nphi;
+  p->nvars = nvars;
+  p->precision = prm->precision;
+  p->dr_min = prm->dr_min;
+  p->floor_ = prm->floor;
+  p->parity.assign(parity, parity + nvars);
+  p->kind.assign(prm->kind, prm->kind + nvars);
+  p->L.assign(prm->L, prm->L + nvars);
+  p->r.assign(prm->r, prm->r + Nr);
+  // cutoff classes: distinct (kind, L)
+  p->var_cls.resize((size_t)nvars);
+  for (int v = 0; v < nvars; ++v) {
+    int c = 0;
+    for (; c < p->ncls; ++c)
+      if (p->cls_kind[(size_t)c] == p->kind[(size_t)v] && p->cls_L[(size_t)c] == p->L[(size_t)v]) break;
+    if (c == p->ncls) {
+      p->cls_kind.push_back(p->kind[(size_t)v]);
+      p->cls_L.push_back(p->L[(size_t)v]);
+      ++p->ncls;
+    }
+    p->var_cls[(size_t)v] = c;
+  }
+  p->h_lmax.resize((size_t)p->ncls * Nr);
+  p->h_mmax.resize((size_t)p->ncls * Nr * Ntheta);
+  for (int c = 0; c < p->ncls; ++c)
+    for (int i = 0; i < Nr; ++i) {
+      p->h_lmax[(size_t)c * Nr + i] = lmax_of(p->r[(size_t)i], p->dr_min, p->cls_L[(size_t)c], p->floor_);
+      for (int j = 0; j < Ntheta; ++j)
+        p->h_mmax[((size_t)c * Nr + i) * Ntheta + j] =
+            mmax_of(p->r[(size_t)i], p->dr_min, p->cls_L[(size_t)c], p->floor_, j, Ntheta);
+    }
+  std::vector<VarInfo> vi((size_t)nvars);
+  for (int v = 0; v < nvars; ++v) vi[(size_t)v] = VarInfo{p->parity[(size_t)v], p->kind[(size_t)v], p->var_cls[(size_t)v], 0};
+
+  ShellArgs& a = p->args;
+  a.Nr = Nr;
+  a.Nth = Ntheta;
+  a.Nph = Nphi;
+  a.nvars = nvars;
+  a.ldS = Nphi + 1;
+  if (!factorize(2 * Ntheta, &a.f_th) || !factorize(Nphi, &a.f_ph)) {
+    delete p;
+    return SPH_EUNSUPPORTED;
+  }
+  p->smem_bytes = plain_smem_bytes(a, &a.chunk_th, &a.chunk_ph);
+  if (p->smem_bytes == 0) {
+    delete p;
+    return SPH_EUNSUPPORTED;
+  }
+  auto tth = twiddles(2 * Ntheta);
+  auto tph = twiddles(Nphi);
+  sph_status st = SPH_OK;
+  if (st == SPH_OK) st = upload(&p->d_lmax, p->h_lmax.data(), p->h_lmax.size());
+  if (st == SPH_OK) st = upload(&p->d_mmax, p->h_mmax.data(), p->h_mmax.size());
+  if (st == SPH_OK) st = upload(&p->d_var, vi.data(), vi.size());
+  if (st == SPH_OK) st = upload(&p->d_tw_th, tth.data(), tth.size());
+  if (st == SPH_OK) st = upload(&p->d_tw_ph, tph.data(), tph.size());
+  if (st == SPH_OK) {
+    if (cudaMalloc((void**)&p->d_status, sizeof(unsigned)) != cudaSuccess) st = SPH_ENOMEM;
+    else if (cudaMemset(p->d_status, 0, sizeof(unsigned)) != cudaSuccess) st = SPH_ECUDA;
+  }
+  if (st == SPH_OK && set_plain_smem_attr(p->smem_bytes) != cudaSuccess) st = SPH_ECUDA;
+  if (st != SPH_OK) {
+    free_plan(p);
+    return st;
+  }
+  a.lmax = p->d_lmax;
+  a.mmax = p->d_mmax;
+  a.var = p->d_var;
+  a.tw_th = p->d_tw_th;
+  a.tw_ph = p->d_tw_ph;
+  a.status = p->d_status;
+  p->launches = 1;
+  *out = p;
+  return SPH_OK;
+}
+
+void sph_filter_plan_destroy(sph_filter_plan plan) {
+  if (!plan) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  cudaSetDevice(plan->device);
+  cudaDeviceSynchronize();
+  free_plan(plan);
+  if (cur >= 0) cudaSetDevice(cur);
+}
+
+sph_status sph_filter_apply(sph_filter_plan plan, const double* in, double* out, sph_stream_t stream) {
+  return launch(plan, in, nullptr, out, kMapNone, kOutNone, 0, 0, stream);
+}
+
+sph_status sph_filter_apply_adjoint(sph_filter_plan plan, const double* in, double* out, sph_stream_t stream) {
+  return launch(plan, in, nullptr, out, kMapNone, kOutNone, 1, 0, stream);
+}
+
+sph_status sph_filter_apply_tanh(sph_filter_plan plan, const double* z, double* out, sph_stream_t stream) {
+  return launch(plan, z, nullptr, out, kMapTanh, kOutNone, 0, 0, stream);
+}
+
+sph_status sph_filter_apply_adjoint_tanh(sph_filter_plan plan, const double* g, const double* z, double* out,
+                                         sph_stream_t stream) {
+  return launch(plan, g, z, out, kMapNone, kOutTanhGrad, 1, 0, stream);
+}
+
+sph_status sph_filter_apply_f32(sph_filter_plan plan, const float* in, float* out, sph_stream_t stream) {
+  return launch(plan, in, nullptr, out, kMapNone, kOutNone, 0, 1, stream);
+}
+
+sph_status sph_filter_apply_adjoint_f32(sph_filter_plan plan, const float* in, float* out, sph_stream_t stream) {
+  return launch(plan, in, nullptr, out, kMapNone, kOutNone, 1, 1, stream);
+}
+
+sph_status sph_filter_apply_tanh_f32(sph_filter_plan plan, const float* z, float* out, sph_stream_t stream) {
+  return launch(plan, z, nullptr, out, kMapTanh, kOutNone, 0, 1, stream);
+}
+
+sph_status sph_filter_apply_adjoint_tanh_f32(sph_filter_plan plan, const float* g, const float* z, float* out,
+                                             sph_stream_t stream) {
+  return launch(plan, g, z, out, kMapNone, kOutTanhGrad, 1, 1, stream);
+}
+
+sph_status sph_filter_apply_host(sph_filter_plan plan, const double* host_in, double* host_out,
+                                 sph_stream_t stream) {
+  if (!plan || !host_in || !host_out) return SPH_EINVAL;
+  const size_t n = (size_t)plan->nvars * plan->Nr * plan->Nth * plan->Nph;
+  if (!plan->d_stage_in) {
+    if (cudaMalloc((void**)&plan->d_stage_in, sizeof(double) * n) != cudaSuccess) return SPH_ENOMEM;
+    if (cudaMalloc((void**)&plan->d_stage_out, sizeof(double) * n) != cudaSuccess) {
+      cudaFree(plan->d_stage_in);
+      plan->d_stage_in = nullptr;
+      return SPH_ENOMEM;
+    }
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(plan->d_stage_in, host_in, sizeof(double) * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return SPH_ECUDA;
+  sph_status st = sph_filter_apply(plan, plan->d_stage_in, plan->d_stage_out, stream);
+  if (st != SPH_OK) return st;
+  if (cudaMemcpyAsync(host_out, plan->d_stage_out, sizeof(double) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return SPH_ECUDA;
+  return SPH_OK;
+}
+
+sph_status sph_filter_plan_sync_status(sph_filter_plan plan) {
+  if (!plan) return SPH_EINVAL;
+  if (cudaDeviceSynchronize() != cudaSuccess) return SPH_ECUDA;
+  unsigned h = 0;
+  if (cudaMemcpy(&h, plan->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return SPH_ECUDA;
+  if (h != 0 && cudaMemset(plan->d_status, 0, sizeof(unsigned)) != cudaSuccess) return SPH_ECUDA;
+  return (sph_status)h;
+}
+
+long long sph_filter_plan_points(sph_filter_plan plan) {
+  if (!plan) return 0;
+  return (long long)plan->nvars * plan->Nr * plan->Nth * plan->Nph;
+}
+
+int sph_filter_plan_launches(sph_filter_plan plan) { return plan ? plan->launches : 0; }
+
+const char* sph_filter_status_string(sph_status s) {
+  switch (s) {
+    case SPH_OK: return "ok";
+    case SPH_EINVAL: return "invalid argument";
+    case SPH_ENOMEM: return "out of memory";
+    case SPH_ECUDA: return "CUDA runtime error";
+    case SPH_EUNSUPPORTED: return "unsupported configuration";
+    case SPH_ETIMEOUT: return "device-side wait timed out";
+    case SPH_EALIAS: return "input and output partially overlap";
+    case SPH_EDEVICE: return "device-side consistency error";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,172 @@
+"""Parity of the plain form (SPH_PREC_F64) with the oracle, through the C ABI, on a GB300.
+
+Error measure: per field, max over points |y - y_oracle| / max |y_oracle|. Tolerance 1e-13: the
+oracle's own rounding error is below 2e-15 of the field maximum (checked by its extended-precision
+build) and the FFT path adds O(log N) roundings of 1.1e-16 per stage; 1e-13 leaves margin for the
+largest transforms while still catching any wrong multiplier, index or sign (those give errors
+of order 1e-3 or larger).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2305_01537_gb300 import workloads as W
+
+TOL = 1e-13
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2305_01537_gb300 import build as B
+    B.build()
+    return torch
+
+
+def field_errors(y, ref):
+    y = np.asarray(y)
+    ref = np.asarray(ref)
+    nv = ref.shape[0]
+    return np.array([np.abs(y[v] - ref[v]).max() / max(np.abs(ref[v]).max(), 1e-300) for v in range(nv)])
+
+
+def run_plan(torch, grid, x, fn="apply", precision=0, **kw):
+    from paper_2305_01537_gb300 import Plan
+    plan = Plan.from_grid(grid, precision=precision)
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    out = getattr(plan, fn)(xd, **kw)
+    torch.cuda.synchronize()
+    assert plan.sync_status() == 0
+    return out.cpu().numpy(), plan
+
+
+def oracle_of(grid, x, transpose=False):
+    f = oracle.filter_T if transpose else oracle.filter
+    return f(x, grid.parity, grid.kind, grid.L, grid.r, grid.dr_min, grid.floor)
+
+
+def test_single_field_workload(torch_cuda):
+    wl = W.single_field()
+    g = wl.grids[0]
+    x = wl.state()
+    y, _ = run_plan(torch_cuda, g, x)
+    assert field_errors(y, oracle_of(g, x)).max() <= TOL
+
+
+@pytest.mark.parametrize("Nth,Nph", [(1, 2), (2, 4), (3, 6), (4, 8), (5, 10), (6, 12), (8, 4), (7, 18),
+                                     (12, 24), (16, 30)])
+def test_tiny_and_ragged_grids(torch_cuda, Nth, Nph):
+    """Every kind and parity, radii from the origin (floor) to past the identity threshold, on
+    small, odd and prime-factor sizes (radix 2, 3, 5, 7 and 9 stages, single-ring shells)."""
+    parity = [0, 1, 0, 1, 0, 1]
+    kind = [0, 0, 1, 1, 2, 2]
+    L = [0.7, 1.3, 2.0, 0.5, 0.9, 1.1]
+    r = np.array([0.0, 0.3, 1.1, 2.6, 7.0, 40.0])
+    g = W.Grid(len(r), Nth, Nph, parity, kind, L, r)
+    x = W.random_state(g.shape, seed=Nth * 1000 + Nph)
+    y, _ = run_plan(torch_cuda, g, x)
+    assert field_errors(y, oracle_of(g, x)).max() <= TOL
+    yt, _ = run_plan(torch_cuda, g, x, fn="apply_adjoint")
+    assert field_errors(yt, oracle_of(g, x, transpose=True)).max() <= TOL
+
+
+def test_28_field_mix_medium(torch_cuda):
+    """All field classes of the 28-field mix on a grid whose theta transforms need several batches."""
+    g = W.grid_28(10, 24, 48)
+    g.r = np.array([0.5, 1.5, 2.5, 3.5, 4.5, 6.5, 9.5, 14.5, 30.5, 100.5])
+    x = W.band_limited_state(g, seed=77, mode_max=6, noise=0.05)
+    y, _ = run_plan(torch_cuda, g, x)
+    assert field_errors(y, oracle_of(g, x)).max() <= TOL
+
+
+def test_full_state_128x64x128_sampled(torch_cuda):
+    """The 28-field Nr=128, Ntheta=64, Nphi=128 workload at full size, in the launch configuration the
+    benchmark times; the oracle checks a sample of shells covering every field class and both
+    parities, at radii inside and past the identity thresholds."""
+    wl = W.full_state_128x64x128()
+    g = wl.grids[0]
+    x = wl.state()
+    y, _ = run_plan(torch_cuda, g, x)
+    rng = np.random.default_rng(0)
+    shells = [(v, int(i)) for v in range(g.nvars) for i in ([0, 1, 5, 10, 11, 127] + list(rng.integers(0, 128, 2)))]
+    ref = oracle.filter_shells(x, shells, g.parity, g.kind, g.L, g.r, g.dr_min, g.floor)
+    got = np.stack([y[v, i] for (v, i) in shells])
+    err = np.array([np.abs(got[n] - ref[n]).max() / np.abs(ref[n]).max() for n in range(len(shells))])
+    assert err.max() <= TOL, shells[int(err.argmax())]
+    # rings the exponential filter leaves alone (theta-identity shell, m_max >= Nphi/2) are copied
+    # bit for bit: field 0 at the outer shell, rings away from the poles
+    rows = [j for j in range(g.Ntheta) if oracle.mmax(g.r[127], g.dr_min, g.L[0], j, g.Ntheta) >= g.Nphi / 2]
+    assert len(rows) > g.Ntheta // 2
+    assert np.array_equal(y[0, 127, rows], x[0, 127, rows])
+
+
+def test_in_place(torch_cuda):
+    from paper_2305_01537_gb300 import Plan
+    torch = torch_cuda
+    g = W.grid_28(4, 16, 32)
+    x = W.band_limited_state(g, seed=5, mode_max=4, noise=0.05)
+    plan = Plan.from_grid(g)
+    xd = torch.from_numpy(x).cuda()
+    plan.apply(xd, out=xd)
+    torch.cuda.synchronize()
+    assert field_errors(xd.cpu().numpy(), oracle_of(g, x)).max() <= TOL
+
+
+def test_tanh_maps(torch_cuda):
+    """F(tanh z) and (1 - tanh(z)^2) F^T g, the fused steps of a filter/tanh chain."""
+    from paper_2305_01537_gb300 import Plan
+    torch = torch_cuda
+    wl = W.chain_8field()
+    g = W.Grid(6, 16, 32, wl.grids[0].parity, wl.grids[0].kind, wl.grids[0].L)
+    z = W.random_state(g.shape, 3)
+    gr = W.random_state(g.shape, 4)
+    plan = Plan.from_grid(g)
+    zd, gd = torch.from_numpy(z).cuda(), torch.from_numpy(gr).cuda()
+    y = plan.apply_tanh(zd).cpu().numpy()
+    assert field_errors(y, oracle_of(g, np.tanh(z))).max() <= TOL
+    d = plan.apply_adjoint_tanh(gd, zd).cpu().numpy()
+    ref = (1 - np.tanh(z) ** 2) * oracle_of(g, gr, transpose=True)
+    assert field_errors(d, ref).max() <= TOL
+
+
+def test_fp32_io(torch_cuda):
+    """FP32 storage: errors are those of rounding the input and the output to FP32."""
+    from paper_2305_01537_gb300 import Plan
+    torch = torch_cuda
+    g = W.grid_28(4, 16, 32)
+    x = W.band_limited_state(g, seed=6, mode_max=4, noise=0.05).astype(np.float32)
+    plan = Plan.from_grid(g)
+    y = plan.apply(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert y.dtype == np.float32
+    assert field_errors(y.astype(np.float64), oracle_of(g, x.astype(np.float64))).max() <= 2e-6
+
+
+def test_host_entry_point(torch_cuda):
+    from paper_2305_01537_gb300 import Plan
+    torch = torch_cuda
+    g = W.grid_28(3, 8, 16)
+    x = torch.from_numpy(W.band_limited_state(g, seed=8, mode_max=2, noise=0.05)).pin_memory()
+    out = torch.empty_like(x).pin_memory()
+    plan = Plan.from_grid(g)
+    plan.apply_host(x, out)
+    torch.cuda.synchronize()
+    assert field_errors(out.numpy(), oracle_of(g, x.numpy())).max() <= TOL
+
+
+def test_alias_and_errors(torch_cuda):
+    from paper_2305_01537_gb300 import Plan, SphFilterError
+    torch = torch_cuda
+    g = W.grid_28(2, 8, 16)
+    plan = Plan.from_grid(g)
+    buf = torch.zeros(g.points + 16, dtype=torch.float64, device="cuda")
+    a = buf[:g.points].view(g.shape)
+    b = buf[8:8 + g.points].view(g.shape)
+    with pytest.raises(SphFilterError) as e:
+        plan.apply(a, out=b)
+    assert e.value.status == 6
+    with pytest.raises(SphFilterError):
+        Plan(2, 8, 15, [0], [0], [3.0], [0.5, 1.5])
