@@ -28,8 +28,22 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build the library")
 
 
-def sources():
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+# shell_inst.cu is compiled once per (precision, FFT length) instantiation of the shell kernel
+SHELL_INST = [(d, n) for d in (0, 1) for n in (0, 32, 64, 96, 128, 192, 256)]
+
+
+def jobs():
+    """(source, object, extra flags) for every compilation."""
+    out = []
+    for src in sorted(glob.glob(os.path.join(CSRC, "*.cu"))):
+        base = os.path.basename(src)[:-3]
+        if base == "shell_inst":
+            for d, n in SHELL_INST:
+                out.append((src, os.path.join(OBJ, f"shell_inst_d{d}_n{n}.o"),
+                            [f"-DSPH_SHELL_DF={d}", f"-DSPH_SHELL_LEN={n}"]))
+        else:
+            out.append((src, os.path.join(OBJ, base + ".o"), []))
+    return out
 
 
 def _stale(obj: str, deps) -> bool:
@@ -41,13 +55,13 @@ def _stale(obj: str, deps) -> bool:
 
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OBJ, exist_ok=True)
-    headers = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(HERE, "..", "include", "*.h"))
+    headers = (glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))
+               + glob.glob(os.path.join(HERE, "..", "include", "*.h")))
     objs, procs = [], []
-    for src in sources():
-        obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
+    for src, obj, extra in jobs():
         objs.append(obj)
         if force or _stale(obj, [src] + headers):
-            cmd = [nvcc()] + NVCC_FLAGS + ["-c", src, "-o", obj]
+            cmd = [nvcc()] + NVCC_FLAGS + extra + ["-c", src, "-o", obj]
             if verbose:
                 print(" ".join(cmd))
             procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

@@ -18,6 +18,7 @@ int max_smem_optin(int device) {
 
 cudaError_t set_plain_smem_attr(size_t bytes);
 
+
 namespace {
 
 // Radix order for a length: 8s, then 4, 2, 3, then any remaining prime (direct DFT stage).
@@ -72,6 +73,141 @@ double mmax_of(double r, double dr_min, double L, double floor_, int j, int Nth)
   return v > floor_ ? v : floor_;
 }
 
+
+// Filter function f(|l|, l_max) of Sec. II.C in extended precision (tables are rounded once).
+long double fval(int kind, long double al, long double lmax) {
+  if (kind == SPH_FILTER_GAUSS) {
+    const long double t = al / (lmax + 1.0L);
+    return expl(logl(0.9L) * t * t);
+  }
+  if (al <= lmax) return 1.0L;
+  return kind == SPH_FILTER_EXP ? expl(-(al - lmax)) : 0.0L;
+}
+
+// Radices the register-staged kernel implements: 8, 4, 2, 3.
+bool factorize_v2(int n, Factors* f) {
+  f->n = n;
+  f->nst = 0;
+  int m = n;
+  while (m > 1) {
+    int r = (m % 8 == 0) ? 8 : (m % 4 == 0) ? 4 : (m % 2 == 0) ? 2 : (m % 3 == 0) ? 3 : 0;
+    if (r == 0 || f->nst >= kMaxStages) return false;
+    f->radix[f->nst++] = r;
+    m /= r;
+  }
+  return true;
+}
+
+// Real values written either as FP64 or as FP32 pairs (hi, lo).
+struct TabWriter {
+  bool pair;
+  std::vector<unsigned char>& buf;
+  void real(size_t at, long double v) const {
+    if (pair) {
+      const float hi = (float)v;
+      const float lo = (float)(v - (long double)hi);
+      std::memcpy(&buf[at], &hi, 4);
+      std::memcpy(&buf[at + 4], &lo, 4);
+    } else {
+      const double d = (double)v;
+      std::memcpy(&buf[at], &d, 8);
+    }
+  }
+};
+
+// Builds the tables of the register-staged kernel; false if the shape does not fit it.
+sph_status setup_v2(sph_filter_plan_s* p) {
+  ShellArgs2& a = p->args2;
+  a.Nr = p->Nr;
+  a.Nth = p->Nth;
+  a.Nph = p->Nph;
+  a.nvars = p->nvars;
+  a.ldS = p->Nph + 1;
+  if (!factorize_v2(2 * p->Nth, &a.f_th) || !factorize_v2(p->Nph, &a.f_ph)) return SPH_EUNSUPPORTED;
+  int cap = kMaxV;
+  for (int s = 0; s < a.f_th.nst; ++s) cap = std::min(cap, a.f_th.radix[s] * (kMaxV / a.f_th.radix[s]));
+  for (int s = 0; s < a.f_ph.nst; ++s) cap = std::min(cap, a.f_ph.radix[s] * (kMaxV / a.f_ph.radix[s]));
+  const long tot_th = (long)((p->Nph / 2 + 1) / 2) * 2 * p->Nth;
+  const long tot_ph = (long)((p->Nth + 1) / 2) * p->Nph;
+  const long need = (std::max(tot_th, tot_ph) + cap - 1) / cap;
+  int threads = (int)std::max<long>(64, (need + 31) / 32 * 32);
+  if (threads > 512) return SPH_EUNSUPPORTED;
+  a.min_threads = (int)need;
+  const size_t smem = shell_smem_bytes(a, p->precision);
+  if (smem > (size_t)max_smem_optin(p->device)) return SPH_EUNSUPPORTED;
+
+  const bool pair = p->precision == SPH_PREC_F32X2;
+  const int Nr = p->Nr, Nth = p->Nth, Nph = p->Nph, nh = Nph / 2 + 1, ncls = p->ncls;
+  const size_t n_ring = (size_t)ncls * Nr * Nth, n_gth = (size_t)ncls * Nr * (Nth + 1);
+  const size_t n_gph = n_ring * nh;
+  auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+  const size_t o_ring = 0;
+  const size_t o_gth = up(o_ring + n_ring);
+  const size_t o_gph = up(o_gth + 8 * n_gth);
+  const size_t o_tth = up(o_gph + 8 * n_gph);
+  const size_t o_tph = up(o_tth + 16 * (size_t)(2 * Nth));
+  const size_t o_con = up(o_tph + 16 * (size_t)Nph);
+  const size_t total = up(o_con + 16);
+  std::vector<unsigned char> buf(total, 0);
+  TabWriter W{pair, buf};
+  const long double pi = acosl(-1.0L);
+  for (int c = 0; c < ncls; ++c)
+    for (int i = 0; i < Nr; ++i) {
+      const double lm = p->h_lmax[(size_t)c * Nr + i];
+      for (int l = 0; l <= Nth; ++l)
+        W.real(o_gth + 8 * (((size_t)c * Nr + i) * (Nth + 1) + l), fval(p->cls_kind[c], l, lm) / (2.0L * Nth));
+      for (int j = 0; j < Nth; ++j) {
+        const double mm = p->h_mmax[((size_t)c * Nr + i) * Nth + j];
+        const bool active = p->cls_kind[c] == SPH_FILTER_GAUSS || mm < 0.5 * Nph;
+        buf[o_ring + ((size_t)c * Nr + i) * Nth + j] = active ? 1 : 0;
+        for (int m = 0; m < nh; ++m)
+          W.real(o_gph + 8 * ((((size_t)c * Nr + i) * Nth + j) * nh + m), fval(p->cls_kind[c], m, mm) / (long double)Nph);
+      }
+      // mirror rings share one complex FFT; flag pairs whose multipliers differ beyond rounding
+      for (int j = 0; j < Nth / 2; ++j) {
+        const int jj = Nth - 1 - j;
+        const double m1 = p->h_mmax[((size_t)c * Nr + i) * Nth + j], m2 = p->h_mmax[((size_t)c * Nr + i) * Nth + jj];
+        bool differ = false;
+        for (int m = 0; m < nh && !differ; ++m) {
+          const long double d = fval(p->cls_kind[c], m, m1) - fval(p->cls_kind[c], m, m2);
+          differ = fabsl(d) > 4e-16L;
+        }
+        if (differ) {
+          buf[o_ring + ((size_t)c * Nr + i) * Nth + j] |= 2;
+          buf[o_ring + ((size_t)c * Nr + i) * Nth + jj] |= 2;
+        }
+      }
+    }
+  for (int t = 0; t < 2; ++t) {
+    const int N = t == 0 ? 2 * Nth : Nph;
+    const size_t o = t == 0 ? o_tth : o_tph;
+    for (int n = 0; n < N; ++n) {
+      const long double ang = 2.0L * pi * (long double)n / (long double)N;
+      W.real(o + 16 * (size_t)n, cosl(ang));
+      W.real(o + 16 * (size_t)n + 8, -sinl(ang));
+    }
+  }
+  W.real(o_con, sqrtl(0.5L));
+  W.real(o_con + 8, sqrtl(3.0L) / 2.0L);
+  if (cudaMalloc(&p->d_tabs, total) != cudaSuccess) return SPH_ENOMEM;
+  if (cudaMemcpy(p->d_tabs, buf.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) return SPH_ECUDA;
+  if (set_shell_smem_attr(p->device) != cudaSuccess) return SPH_ECUDA;
+  unsigned char* base = static_cast<unsigned char*>(p->d_tabs);
+  a.ring_info = base + o_ring;
+  a.g_th = base + o_gth;
+  a.g_ph = base + o_gph;
+  a.tw_th = base + o_tth;
+  a.tw_ph = base + o_tph;
+  a.consts = base + o_con;
+  a.lmax = p->d_lmax;
+  a.var = p->d_var;
+  a.status = p->d_status;
+  p->threads2 = threads;
+  p->smem2 = smem;
+  p->use_v2 = true;
+  return SPH_OK;
+}
+
 bool overlaps_partially(const void* a, const void* b, size_t bytes) {
   if (a == b) return false;
   const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
@@ -93,6 +229,7 @@ void free_plan(sph_filter_plan_s* p) {
   cudaFree(p->d_tw_th);
   cudaFree(p->d_tw_ph);
   cudaFree(p->d_status);
+  cudaFree(p->d_tabs);
   cudaFree(p->d_stage_in);
   cudaFree(p->d_stage_out);
   delete p;
@@ -119,7 +256,8 @@ sph_status launch(sph_filter_plan p, const void* in, const void* aux, void* out,
   if (cudaGetDevice(&cur) != cudaSuccess) return SPH_ECUDA;
   if (cur != p->device && cudaSetDevice(p->device) != cudaSuccess) return SPH_ECUDA;
   LaunchIO io{in, aux, out, map_in, map_out, transpose, is_f32};
-  cudaError_t e = launch_plain(*p, io, (cudaStream_t)stream);
+  cudaError_t e = p->use_v2 ? launch_shell(p->args2, p->precision, p->threads2, p->smem2, io, (cudaStream_t)stream)
+                            : launch_plain(*p, io, (cudaStream_t)stream);
   if (cur != p->device) cudaSetDevice(cur);
   return e == cudaSuccess ? SPH_OK : SPH_ECUDA;
 }
@@ -148,7 +286,7 @@ sph_status sph_filter_plan_create(sph_filter_plan* out, int Nr, int Ntheta, int 
   }
   for (int i = 0; i < Nr; ++i)
     if (!(prm->r[i] >= 0) || !std::isfinite(prm->r[i])) return SPH_EINVAL;
-  if (prm->precision != SPH_PREC_F64) return SPH_EUNSUPPORTED;
+  if (prm->precision == SPH_PREC_SPLIT_TC) return SPH_EUNSUPPORTED;
 
   sph_filter_plan_s* p = new (std::nothrow) sph_filter_plan_s();
   if (!p) return SPH_ENOMEM;
@@ -192,44 +330,60 @@ sph_status sph_filter_plan_create(sph_filter_plan* out, int Nr, int Ntheta, int 
   std::vector<VarInfo> vi((size_t)nvars);
   for (int v = 0; v < nvars; ++v) vi[(size_t)v] = VarInfo{p->parity[(size_t)v], p->kind[(size_t)v], p->var_cls[(size_t)v], 0};
 
-  ShellArgs& a = p->args;
-  a.Nr = Nr;
-  a.Nth = Ntheta;
-  a.Nph = Nphi;
-  a.nvars = nvars;
-  a.ldS = Nphi + 1;
-  if (!factorize(2 * Ntheta, &a.f_th) || !factorize(Nphi, &a.f_ph)) {
-    delete p;
-    return SPH_EUNSUPPORTED;
-  }
-  p->smem_bytes = plain_smem_bytes(a, &a.chunk_th, &a.chunk_ph);
-  if (p->smem_bytes == 0) {
-    delete p;
-    return SPH_EUNSUPPORTED;
-  }
-  auto tth = twiddles(2 * Ntheta);
-  auto tph = twiddles(Nphi);
   sph_status st = SPH_OK;
   if (st == SPH_OK) st = upload(&p->d_lmax, p->h_lmax.data(), p->h_lmax.size());
   if (st == SPH_OK) st = upload(&p->d_mmax, p->h_mmax.data(), p->h_mmax.size());
   if (st == SPH_OK) st = upload(&p->d_var, vi.data(), vi.size());
-  if (st == SPH_OK) st = upload(&p->d_tw_th, tth.data(), tth.size());
-  if (st == SPH_OK) st = upload(&p->d_tw_ph, tph.data(), tph.size());
   if (st == SPH_OK) {
     if (cudaMalloc((void**)&p->d_status, sizeof(unsigned)) != cudaSuccess) st = SPH_ENOMEM;
     else if (cudaMemset(p->d_status, 0, sizeof(unsigned)) != cudaSuccess) st = SPH_ECUDA;
   }
-  if (st == SPH_OK && set_plain_smem_attr(p->smem_bytes) != cudaSuccess) st = SPH_ECUDA;
   if (st != SPH_OK) {
     free_plan(p);
     return st;
   }
-  a.lmax = p->d_lmax;
-  a.mmax = p->d_mmax;
-  a.var = p->d_var;
-  a.tw_th = p->d_tw_th;
-  a.tw_ph = p->d_tw_ph;
-  a.status = p->d_status;
+  // the register-staged kernel when the shape fits it; otherwise the chunked FP64 kernel
+  st = setup_v2(p);
+  if (st != SPH_OK && st != SPH_EUNSUPPORTED) {
+    free_plan(p);
+    return st;
+  }
+  if (!p->use_v2) {
+    if (p->precision != SPH_PREC_F64) {
+      free_plan(p);
+      return SPH_EUNSUPPORTED;
+    }
+    ShellArgs& a = p->args;
+    a.Nr = Nr;
+    a.Nth = Ntheta;
+    a.Nph = Nphi;
+    a.nvars = nvars;
+    a.ldS = Nphi + 1;
+    if (!factorize(2 * Ntheta, &a.f_th) || !factorize(Nphi, &a.f_ph)) {
+      free_plan(p);
+      return SPH_EUNSUPPORTED;
+    }
+    p->smem_bytes = plain_smem_bytes(a, &a.chunk_th, &a.chunk_ph);
+    if (p->smem_bytes == 0) {
+      free_plan(p);
+      return SPH_EUNSUPPORTED;
+    }
+    auto tth = twiddles(2 * Ntheta);
+    auto tph = twiddles(Nphi);
+    st = upload(&p->d_tw_th, tth.data(), tth.size());
+    if (st == SPH_OK) st = upload(&p->d_tw_ph, tph.data(), tph.size());
+    if (st == SPH_OK && set_plain_smem_attr(p->smem_bytes) != cudaSuccess) st = SPH_ECUDA;
+    if (st != SPH_OK) {
+      free_plan(p);
+      return st;
+    }
+    a.lmax = p->d_lmax;
+    a.mmax = p->d_mmax;
+    a.var = p->d_var;
+    a.tw_th = p->d_tw_th;
+    a.tw_ph = p->d_tw_ph;
+    a.status = p->d_status;
+  }
   p->launches = 1;
   *out = p;
   return SPH_OK;

@@ -11,7 +11,8 @@
 namespace sph {
 
 constexpr int kMaxStages = 12;   // radix stages of one FFT length
-constexpr int kThreads = 256;    // threads per CTA of the shell kernels
+constexpr int kThreads = 256;    // threads per CTA of the chunked FP64 kernel
+constexpr int kMaxV = 8;         // complex values a thread of the register-staged kernel holds per stage
 
 // Mixed-radix factorisation of an FFT length, radices in the order the stages run.
 struct Factors {
@@ -58,6 +59,57 @@ struct LaunchIO {
   int is_f32;         // 0: FP64 I/O, 1: FP32 I/O
 };
 
+// Arguments of the register-staged shell kernel (filter_shell.cu). Tables hold FP64 values, or
+// FP32 pairs (hi, lo) for the compensated FP32 precision.
+struct ShellArgs2 {
+  int Nr, Nth, Nph, nvars;
+  int ldS;                    // row stride of the staged shell (elements)
+  int min_threads;            // threads each CTA needs to hold one stage in registers
+  Factors f_th, f_ph;         // radices (2, 3, 4, 8) of 2 Ntheta and Nphi
+  const double* lmax;         // [ncls][Nr]
+  const VarInfo* var;         // [nvars]
+  const uint8_t* ring_info;   // [ncls][Nr][Nth]: bit 0 ring active, bit 1 mirror ring differs
+  const void* g_th;           // [ncls][Nr][Nth+1]       f(l, l_max) / (2 Ntheta)
+  const void* g_ph;           // [ncls][Nr][Nth][Nph/2+1] f(m, m_max) / Nphi
+  const void* tw_th;          // [2 Nth] exp(-2 pi i n / (2 Nth))
+  const void* tw_ph;          // [Nph]   exp(-2 pi i n / Nph)
+  const void* consts;         // [2] sqrt(1/2), sqrt(3)/2
+  unsigned* status;
+};
+
+// Instantiations of the register-staged kernel, one per (compensated precision?, FFT length);
+// defined by shell_inst.cu compiled once per pair.
+template <int DFP, int LEN>
+cudaError_t launch_shell_inst(const ShellArgs2& a, int threads, size_t smem, const LaunchIO& io, cudaStream_t s);
+template <int DFP, int LEN>
+cudaError_t set_attr_inst(int bytes);
+#define SPH_DECLARE_SHELL_INST(D, L)                                                                    \
+  template <>                                                                                           \
+  cudaError_t launch_shell_inst<D, L>(const ShellArgs2&, int, size_t, const LaunchIO&, cudaStream_t); \
+  template <>                                                                                           \
+  cudaError_t set_attr_inst<D, L>(int);
+SPH_DECLARE_SHELL_INST(0, 0)
+SPH_DECLARE_SHELL_INST(0, 32)
+SPH_DECLARE_SHELL_INST(0, 64)
+SPH_DECLARE_SHELL_INST(0, 96)
+SPH_DECLARE_SHELL_INST(0, 128)
+SPH_DECLARE_SHELL_INST(0, 192)
+SPH_DECLARE_SHELL_INST(0, 256)
+SPH_DECLARE_SHELL_INST(1, 0)
+SPH_DECLARE_SHELL_INST(1, 32)
+SPH_DECLARE_SHELL_INST(1, 64)
+SPH_DECLARE_SHELL_INST(1, 96)
+SPH_DECLARE_SHELL_INST(1, 128)
+SPH_DECLARE_SHELL_INST(1, 192)
+SPH_DECLARE_SHELL_INST(1, 256)
+#undef SPH_DECLARE_SHELL_INST
+
+size_t shell_smem_bytes(const ShellArgs2& a, int precision);
+int fixed_length(const ShellArgs2& a);
+cudaError_t launch_shell(const ShellArgs2& a, int precision, int threads, size_t smem, const LaunchIO& io,
+                         cudaStream_t s);
+cudaError_t set_shell_smem_attr(int device);
+
 }  // namespace sph
 
 struct sph_filter_plan_s {
@@ -74,6 +126,13 @@ struct sph_filter_plan_s {
   sph::ShellArgs args{};
   size_t smem_bytes = 0;
   int launches = 1;
+
+  // register-staged kernel (used when the shape fits it)
+  bool use_v2 = false;
+  sph::ShellArgs2 args2{};
+  int threads2 = 0;
+  size_t smem2 = 0;
+  void* d_tabs = nullptr;     // one allocation holding every v2 table
 
   double* d_lmax = nullptr;
   double* d_mmax = nullptr;

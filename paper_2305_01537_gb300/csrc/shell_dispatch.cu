@@ -1,0 +1,55 @@
+// Selection among the compiled instantiations of the register-staged shell kernel.
+#include "shell_kernel.cuh"
+
+namespace sph {
+
+int fixed_length(const ShellArgs2& a) {
+  const int L = a.Nph;
+  if (2 * a.Nth != L) return 0;
+  if (L == 32 || L == 64 || L == 96 || L == 128 || L == 192 || L == 256) return L;
+  return 0;
+}
+
+size_t shell_smem_bytes(const ShellArgs2& a, int precision) {
+  return precision == SPH_PREC_F32X2 ? shellk::smem_impl<shellk::DF>(a) : shellk::smem_impl<shellk::F64>(a);
+}
+
+template <int DFP>
+static cudaError_t launch_p(const ShellArgs2& a, int threads, size_t smem, const LaunchIO& io, cudaStream_t s) {
+  switch (fixed_length(a)) {
+    case 32: return launch_shell_inst<DFP, 32>(a, threads, smem, io, s);
+    case 64: return launch_shell_inst<DFP, 64>(a, threads, smem, io, s);
+    case 96: return launch_shell_inst<DFP, 96>(a, threads, smem, io, s);
+    case 128: return launch_shell_inst<DFP, 128>(a, threads, smem, io, s);
+    case 192: return launch_shell_inst<DFP, 192>(a, threads, smem, io, s);
+    case 256: return launch_shell_inst<DFP, 256>(a, threads, smem, io, s);
+    default: return launch_shell_inst<DFP, 0>(a, threads, smem, io, s);
+  }
+}
+
+cudaError_t launch_shell(const ShellArgs2& a, int precision, int threads, size_t smem, const LaunchIO& io,
+                         cudaStream_t s) {
+  if (precision == SPH_PREC_F32X2) return launch_p<1>(a, threads, smem, io, s);
+  return launch_p<0>(a, threads, smem, io, s);
+}
+
+template <int DFP>
+static cudaError_t set_attr_p(int bytes) {
+  cudaError_t e = set_attr_inst<DFP, 0>(bytes);
+  if (e == cudaSuccess) e = set_attr_inst<DFP, 32>(bytes);
+  if (e == cudaSuccess) e = set_attr_inst<DFP, 64>(bytes);
+  if (e == cudaSuccess) e = set_attr_inst<DFP, 96>(bytes);
+  if (e == cudaSuccess) e = set_attr_inst<DFP, 128>(bytes);
+  if (e == cudaSuccess) e = set_attr_inst<DFP, 192>(bytes);
+  if (e == cudaSuccess) e = set_attr_inst<DFP, 256>(bytes);
+  return e;
+}
+
+cudaError_t set_shell_smem_attr(int device) {
+  const int bytes = max_smem_optin(device);
+  cudaError_t e = set_attr_p<0>(bytes);
+  if (e != cudaSuccess) return e;
+  return set_attr_p<1>(bytes);
+}
+
+}  // namespace sph

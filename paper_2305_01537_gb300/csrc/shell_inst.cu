@@ -1,0 +1,32 @@
+// One instantiation of the register-staged shell kernel. The build compiles this file once per
+// (precision, FFT length) pair with -DSPH_SHELL_DF=0|1 -DSPH_SHELL_LEN=0|32|64|96|128|192|256, so
+// the instantiations compile in parallel; shell_dispatch.cu selects one at launch time.
+#include "shell_kernel.cuh"
+
+#ifndef SPH_SHELL_DF
+#define SPH_SHELL_DF 0
+#endif
+#ifndef SPH_SHELL_LEN
+#define SPH_SHELL_LEN 0
+#endif
+
+namespace sph {
+
+#if SPH_SHELL_DF
+using InstPolicy = shellk::DF;
+#else
+using InstPolicy = shellk::F64;
+#endif
+
+template <>
+cudaError_t launch_shell_inst<SPH_SHELL_DF, SPH_SHELL_LEN>(const ShellArgs2& a, int threads, size_t smem,
+                                                         const LaunchIO& io, cudaStream_t s) {
+  return shellk::launch_impl<InstPolicy, SPH_SHELL_LEN>(a, threads, smem, io, s);
+}
+
+template <>
+cudaError_t set_attr_inst<SPH_SHELL_DF, SPH_SHELL_LEN>(int bytes) {
+  return shellk::set_attr_impl<InstPolicy, SPH_SHELL_LEN>(bytes);
+}
+
+}  // namespace sph

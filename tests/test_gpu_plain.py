@@ -1,4 +1,5 @@
-"""Parity of the plain form (SPH_PREC_F64) with the oracle, through the C ABI, on a GB300.
+"""Parity of the plain form with the oracle, through the C ABI, on a GB300, for both arithmetic
+choices of that form: FP64 (SPH_PREC_F64) and compensated FP32 pairs (SPH_PREC_F32X2).
 
 Error measure: per field, max over points |y - y_oracle| / max |y_oracle|. Tolerance 1e-13: the
 oracle's own rounding error is below 2e-15 of the field maximum (checked by its extended-precision
@@ -13,6 +14,7 @@ import oracle
 from paper_2305_01537_gb300 import workloads as W
 
 TOL = 1e-13
+PRECS = [0, 2]  # SPH_PREC_F64, SPH_PREC_F32X2
 
 pytestmark = pytest.mark.gpu
 
@@ -49,17 +51,19 @@ def oracle_of(grid, x, transpose=False):
     return f(x, grid.parity, grid.kind, grid.L, grid.r, grid.dr_min, grid.floor)
 
 
-def test_single_field_workload(torch_cuda):
+@pytest.mark.parametrize("prec", PRECS)
+def test_single_field_workload(torch_cuda, prec):
     wl = W.single_field()
     g = wl.grids[0]
     x = wl.state()
-    y, _ = run_plan(torch_cuda, g, x)
+    y, _ = run_plan(torch_cuda, g, x, precision=prec)
     assert field_errors(y, oracle_of(g, x)).max() <= TOL
 
 
 @pytest.mark.parametrize("Nth,Nph", [(1, 2), (2, 4), (3, 6), (4, 8), (5, 10), (6, 12), (8, 4), (7, 18),
                                      (12, 24), (16, 30)])
-def test_tiny_and_ragged_grids(torch_cuda, Nth, Nph):
+@pytest.mark.parametrize("prec", PRECS)
+def test_tiny_and_ragged_grids(torch_cuda, Nth, Nph, prec):
     """Every kind and parity, radii from the origin (floor) to past the identity threshold, on
     small, odd and prime-factor sizes (radix 2, 3, 5, 7 and 9 stages, single-ring shells)."""
     parity = [0, 1, 0, 1, 0, 1]
@@ -68,29 +72,38 @@ def test_tiny_and_ragged_grids(torch_cuda, Nth, Nph):
     r = np.array([0.0, 0.3, 1.1, 2.6, 7.0, 40.0])
     g = W.Grid(len(r), Nth, Nph, parity, kind, L, r)
     x = W.random_state(g.shape, seed=Nth * 1000 + Nph)
-    y, _ = run_plan(torch_cuda, g, x)
+    from paper_2305_01537_gb300 import SphFilterError
+    try:
+        y, _ = run_plan(torch_cuda, g, x, precision=prec)
+    except SphFilterError as e:
+        # compensated FP32 needs radices 2, 3, 4, 8; other lengths are rejected, not approximated
+        assert prec == 2 and e.status == 4
+        return
     assert field_errors(y, oracle_of(g, x)).max() <= TOL
-    yt, _ = run_plan(torch_cuda, g, x, fn="apply_adjoint")
+    yt, _ = run_plan(torch_cuda, g, x, fn="apply_adjoint", precision=prec)
     assert field_errors(yt, oracle_of(g, x, transpose=True)).max() <= TOL
 
 
-def test_28_field_mix_medium(torch_cuda):
-    """All field classes of the 28-field mix on a grid whose theta transforms need several batches."""
-    g = W.grid_28(10, 24, 48)
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("Nth,Nph", [(24, 48), (32, 64), (16, 48), (12, 36)])
+def test_28_field_mix_medium(torch_cuda, prec, Nth, Nph):
+    """All field classes of the 28-field mix, on compiled lengths (48, 64) and generic ones."""
+    g = W.grid_28(10, Nth, Nph)
     g.r = np.array([0.5, 1.5, 2.5, 3.5, 4.5, 6.5, 9.5, 14.5, 30.5, 100.5])
     x = W.band_limited_state(g, seed=77, mode_max=6, noise=0.05)
-    y, _ = run_plan(torch_cuda, g, x)
+    y, _ = run_plan(torch_cuda, g, x, precision=prec)
     assert field_errors(y, oracle_of(g, x)).max() <= TOL
 
 
-def test_full_state_128x64x128_sampled(torch_cuda):
+@pytest.mark.parametrize("prec", PRECS)
+def test_full_state_128x64x128_sampled(torch_cuda, prec):
     """The 28-field Nr=128, Ntheta=64, Nphi=128 workload at full size, in the launch configuration the
     benchmark times; the oracle checks a sample of shells covering every field class and both
     parities, at radii inside and past the identity thresholds."""
     wl = W.full_state_128x64x128()
     g = wl.grids[0]
     x = wl.state()
-    y, _ = run_plan(torch_cuda, g, x)
+    y, _ = run_plan(torch_cuda, g, x, precision=prec)
     rng = np.random.default_rng(0)
     shells = [(v, int(i)) for v in range(g.nvars) for i in ([0, 1, 5, 10, 11, 127] + list(rng.integers(0, 128, 2)))]
     ref = oracle.filter_shells(x, shells, g.parity, g.kind, g.L, g.r, g.dr_min, g.floor)
@@ -104,19 +117,21 @@ def test_full_state_128x64x128_sampled(torch_cuda):
     assert np.array_equal(y[0, 127, rows], x[0, 127, rows])
 
 
-def test_in_place(torch_cuda):
+@pytest.mark.parametrize("prec", PRECS)
+def test_in_place(torch_cuda, prec):
     from paper_2305_01537_gb300 import Plan
     torch = torch_cuda
     g = W.grid_28(4, 16, 32)
     x = W.band_limited_state(g, seed=5, mode_max=4, noise=0.05)
-    plan = Plan.from_grid(g)
+    plan = Plan.from_grid(g, precision=prec)
     xd = torch.from_numpy(x).cuda()
     plan.apply(xd, out=xd)
     torch.cuda.synchronize()
     assert field_errors(xd.cpu().numpy(), oracle_of(g, x)).max() <= TOL
 
 
-def test_tanh_maps(torch_cuda):
+@pytest.mark.parametrize("prec", PRECS)
+def test_tanh_maps(torch_cuda, prec):
     """F(tanh z) and (1 - tanh(z)^2) F^T g, the fused steps of a filter/tanh chain."""
     from paper_2305_01537_gb300 import Plan
     torch = torch_cuda
@@ -124,7 +139,7 @@ def test_tanh_maps(torch_cuda):
     g = W.Grid(6, 16, 32, wl.grids[0].parity, wl.grids[0].kind, wl.grids[0].L)
     z = W.random_state(g.shape, 3)
     gr = W.random_state(g.shape, 4)
-    plan = Plan.from_grid(g)
+    plan = Plan.from_grid(g, precision=prec)
     zd, gd = torch.from_numpy(z).cuda(), torch.from_numpy(gr).cuda()
     y = plan.apply_tanh(zd).cpu().numpy()
     assert field_errors(y, oracle_of(g, np.tanh(z))).max() <= TOL
@@ -133,16 +148,26 @@ def test_tanh_maps(torch_cuda):
     assert field_errors(d, ref).max() <= TOL
 
 
-def test_fp32_io(torch_cuda):
+@pytest.mark.parametrize("prec", PRECS)
+def test_fp32_io(torch_cuda, prec):
     """FP32 storage: errors are those of rounding the input and the output to FP32."""
     from paper_2305_01537_gb300 import Plan
     torch = torch_cuda
     g = W.grid_28(4, 16, 32)
     x = W.band_limited_state(g, seed=6, mode_max=4, noise=0.05).astype(np.float32)
-    plan = Plan.from_grid(g)
+    plan = Plan.from_grid(g, precision=prec)
     y = plan.apply(torch.from_numpy(x).cuda()).cpu().numpy()
     assert y.dtype == np.float32
     assert field_errors(y.astype(np.float64), oracle_of(g, x.astype(np.float64))).max() <= 2e-6
+
+
+def test_generic_chunked_fallback(torch_cuda):
+    """A length with a prime factor above 3 (Nphi = 2 * 37) runs on the chunked FP64 kernel."""
+    g = W.grid_28(3, 5, 74)
+    g.r = np.array([0.5, 3.5, 20.5])
+    x = W.band_limited_state(g, seed=9, mode_max=3, noise=0.05)
+    y, _ = run_plan(torch_cuda, g, x)
+    assert field_errors(y, oracle_of(g, x)).max() <= TOL
 
 
 def test_host_entry_point(torch_cuda):
