@@ -10,6 +10,12 @@
 
 namespace sph {
 
+int max_smem_per_sm(int device) {
+  int v = 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device) != cudaSuccess) return 0;
+  return v;
+}
+
 int max_smem_optin(int device) {
   int v = 0;
   if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) return 0;
@@ -84,7 +90,7 @@ long double fval(int kind, long double al, long double lmax) {
   return kind == SPH_FILTER_EXP ? expl(-(al - lmax)) : 0.0L;
 }
 
-// Radices the register-staged kernel implements: 8, 4, 2, 3.
+// Radices the staged shell kernel implements: 8, 4, 2, 3.
 bool factorize_v2(int n, Factors* f) {
   f->n = n;
   f->nst = 0;
@@ -115,26 +121,36 @@ struct TabWriter {
   }
 };
 
-// Builds the tables of the register-staged kernel; false if the shape does not fit it.
+// Builds the tables of the staged shell kernel; SPH_EUNSUPPORTED if the shape does not fit it.
 sph_status setup_v2(sph_filter_plan_s* p) {
   ShellArgs2& a = p->args2;
   a.Nr = p->Nr;
   a.Nth = p->Nth;
   a.Nph = p->Nph;
   a.nvars = p->nvars;
-  a.ldS = p->Nph + 1;
+  a.ldS = p->Nph + 2;  // even: value pairs are 16-byte aligned
   if (!factorize_v2(2 * p->Nth, &a.f_th) || !factorize_v2(p->Nph, &a.f_ph)) return SPH_EUNSUPPORTED;
-  int cap = kMaxV;
-  for (int s = 0; s < a.f_th.nst; ++s) cap = std::min(cap, a.f_th.radix[s] * (kMaxV / a.f_th.radix[s]));
-  for (int s = 0; s < a.f_ph.nst; ++s) cap = std::min(cap, a.f_ph.radix[s] * (kMaxV / a.f_ph.radix[s]));
-  const long tot_th = (long)((p->Nph / 2 + 1) / 2) * 2 * p->Nth;
-  const long tot_ph = (long)((p->Nth + 1) / 2) * p->Nph;
-  const long need = (std::max(tot_th, tot_ph) + cap - 1) / cap;
-  int threads = (int)std::max<long>(64, (need + 31) / 32 * 32);
-  if (threads > 512) return SPH_EUNSUPPORTED;
-  a.min_threads = (int)need;
-  const size_t smem = shell_smem_bytes(a, p->precision);
-  if (smem > (size_t)max_smem_optin(p->device)) return SPH_EUNSUPPORTED;
+  // Two CTAs of 256 threads per SM when the shell plus a scratch batch fits half the shared memory
+  // (their copies and barriers then overlap each other's arithmetic); otherwise one CTA of 512.
+  const int nseq = (p->Nph / 2 + 1) / 2, npair = (p->Nth + 1) / 2;
+  const size_t optin = (size_t)max_smem_optin(p->device);
+  const size_t half_sm = (size_t)(max_smem_per_sm(p->device) / 2) - 1024;  // per-CTA reserve
+  int threads = 0;
+  size_t smem = 0;
+  for (int pass = 0; pass < 2 && !threads; ++pass) {
+    const size_t limit = pass == 0 ? std::min(half_sm, optin) : optin;
+    for (int div = 1; div <= 64; div *= 2) {
+      a.batch_th = std::max(1, (nseq + div - 1) / div);
+      a.batch_ph = std::max(1, (npair + div - 1) / div);
+      smem = shell_smem_bytes(a, p->precision);
+      if (smem <= limit) {
+        threads = pass == 0 ? 256 : 512;
+        break;
+      }
+      if (a.batch_th == 1 && a.batch_ph == 1) break;
+    }
+  }
+  if (!threads) return SPH_EUNSUPPORTED;
 
   const bool pair = p->precision == SPH_PREC_F32X2;
   const int Nr = p->Nr, Nth = p->Nth, Nph = p->Nph, nh = Nph / 2 + 1, ncls = p->ncls;
@@ -255,7 +271,7 @@ sph_status launch(sph_filter_plan p, const void* in, const void* aux, void* out,
   int cur = -1;
   if (cudaGetDevice(&cur) != cudaSuccess) return SPH_ECUDA;
   if (cur != p->device && cudaSetDevice(p->device) != cudaSuccess) return SPH_ECUDA;
-  LaunchIO io{in, aux, out, map_in, map_out, transpose, is_f32};
+  LaunchIO io{in, aux, out, map_in, map_out, transpose, is_f32, ((uintptr_t)in % 16) == 0 ? 1 : 0};
   cudaError_t e = p->use_v2 ? launch_shell(p->args2, p->precision, p->threads2, p->smem2, io, (cudaStream_t)stream)
                             : launch_plain(*p, io, (cudaStream_t)stream);
   if (cur != p->device) cudaSetDevice(cur);
@@ -342,7 +358,7 @@ sph_status sph_filter_plan_create(sph_filter_plan* out, int Nr, int Ntheta, int 
     free_plan(p);
     return st;
   }
-  // the register-staged kernel when the shape fits it; otherwise the chunked FP64 kernel
+  // the staged shell kernel when the shape fits it; otherwise the chunked FP64 kernel
   st = setup_v2(p);
   if (st != SPH_OK && st != SPH_EUNSUPPORTED) {
     free_plan(p);

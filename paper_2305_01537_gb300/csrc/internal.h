@@ -12,7 +12,6 @@ namespace sph {
 
 constexpr int kMaxStages = 12;   // radix stages of one FFT length
 constexpr int kThreads = 256;    // threads per CTA of the chunked FP64 kernel
-constexpr int kMaxV = 8;         // complex values a thread of the register-staged kernel holds per stage
 
 // Mixed-radix factorisation of an FFT length, radices in the order the stages run.
 struct Factors {
@@ -57,14 +56,15 @@ struct LaunchIO {
   int map_out;
   int transpose;      // 0: theta then phi; 1: phi then theta
   int is_f32;         // 0: FP64 I/O, 1: FP32 I/O
+  int async_ok;       // input 16-byte aligned: shells may be copied with cp.async
 };
 
-// Arguments of the register-staged shell kernel (filter_shell.cu). Tables hold FP64 values, or
+// Arguments of the staged shell kernel (shell_kernel.cuh). Tables hold FP64 values, or
 // FP32 pairs (hi, lo) for the compensated FP32 precision.
 struct ShellArgs2 {
   int Nr, Nth, Nph, nvars;
   int ldS;                    // row stride of the staged shell (elements)
-  int min_threads;            // threads each CTA needs to hold one stage in registers
+  int batch_th, batch_ph;     // sequences per FFT batch (sizes the scratch buffer)
   Factors f_th, f_ph;         // radices (2, 3, 4, 8) of 2 Ntheta and Nphi
   const double* lmax;         // [ncls][Nr]
   const VarInfo* var;         // [nvars]
@@ -77,7 +77,7 @@ struct ShellArgs2 {
   unsigned* status;
 };
 
-// Instantiations of the register-staged kernel, one per (compensated precision?, FFT length);
+// Instantiations of the staged shell kernel, one per (compensated precision?, FFT length);
 // defined by shell_inst.cu compiled once per pair.
 template <int DFP, int LEN>
 cudaError_t launch_shell_inst(const ShellArgs2& a, int threads, size_t smem, const LaunchIO& io, cudaStream_t s);
@@ -127,7 +127,7 @@ struct sph_filter_plan_s {
   size_t smem_bytes = 0;
   int launches = 1;
 
-  // register-staged kernel (used when the shape fits it)
+  // staged shell kernel (used when the shape fits it)
   bool use_v2 = false;
   sph::ShellArgs2 args2{};
   int threads2 = 0;

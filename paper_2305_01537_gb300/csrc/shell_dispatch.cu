@@ -1,4 +1,4 @@
-// Selection among the compiled instantiations of the register-staged shell kernel.
+// Selection among the compiled instantiations of the staged shell kernel.
 #include "shell_kernel.cuh"
 
 namespace sph {

@@ -1,4 +1,4 @@
-// One instantiation of the register-staged shell kernel. The build compiles this file once per
+// One instantiation of the staged shell kernel. The build compiles this file once per
 // (precision, FFT length) pair with -DSPH_SHELL_DF=0|1 -DSPH_SHELL_LEN=0|32|64|96|128|192|256, so
 // the instantiations compile in parallel; shell_dispatch.cu selects one at launch time.
 #include "shell_kernel.cuh"

@@ -1,11 +1,12 @@
-// Shell kernel of the double FFT filter (arXiv:2305.01537, Sec. II.C), register-staged in-place form.
+// Shell kernel of the double FFT filter (arXiv:2305.01537, Sec. II.C), staged (ping-pong) form.
 // Included by shell_inst.cu, which the build compiles once per (precision, FFT length) pair.
 //
-// One CTA filters one (field, shell) pair. The shell (Ntheta x Nphi values) is staged once in
-// shared memory, which is also the only FFT buffer: every FFT stage loads all of its butterflies'
-// inputs into registers, synchronises, and stores the outputs back into the same memory. All
-// sequences of a pass are transformed in one batch, so each stage holds the whole shell in
-// registers (at most 16 complex values per thread).
+// One CTA filters one (field, shell) pair; two CTAs share an SM where shared memory allows, so that
+// one CTA's copies and barriers overlap the other's arithmetic. The shell (Ntheta x Nphi values) is
+// staged once in shared memory (cp.async, 16-byte pieces). The sequences of a pass are transformed
+// in batches; the FFT stages ping-pong between the shell's own memory (each sequence's slots,
+// below) and a scratch buffer with a linear layout: a thread reads a butterfly's inputs from one,
+// writes its outputs to the other, and needs one barrier per stage.
 //
 //  theta pass (Sec. II.C, first filter equation, double covering): circle k (k < Nphi/2) is
 //    c[q] = x[q][k] for q < Ntheta and (-1)^a x[2 Ntheta-1-q][k+Nphi/2] for q >= Ntheta. Circles
@@ -21,6 +22,12 @@
 //  Identity skipping: exponential and sharp filters keep every mode when l_max >= Ntheta (theta)
 //    or m_max >= Nphi/2 (phi); those shells and rings are not transformed at all.
 //
+// Shared memory is addressed with 32-bit shared-window addresses. The first stage reads and the last
+// stage writes the shell's own row-major layout (row stride Nphi + 2, so value pairs are 16-byte
+// aligned); in between, a sequence's slots in the shell memory have their row (theta) or pair
+// column (phi) index XOR-swizzled within groups of 8, and so does the scratch index, which keeps
+// unit-stride and radix-stride accesses free of bank conflicts.
+//
 // The arithmetic policy is FP64 (F64) or compensated FP32 pairs (DF, about 48-bit significands,
 // with a per-shell power-of-two scale). Multipliers f(|l|)/N and twiddles come from FP64 tables
 // built on the host.
@@ -34,12 +41,12 @@
 namespace sph {
 namespace shellk {
 
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // ------------------------------------------------------------------ arithmetic policies
 
 struct F64 {
   using T = double;
-  using Store = double;
   struct C {
     double re, im;
   };
@@ -49,23 +56,32 @@ struct F64 {
   static __device__ __forceinline__ T neg(T a) { return -a; }
   static __device__ __forceinline__ T half(T a) { return 0.5 * a; }
   static __device__ __forceinline__ T zero() { return 0.0; }
-  static __device__ __forceinline__ T ld(const Store* p) { return *p; }
-  static __device__ __forceinline__ void st(Store* p, T v) { *p = v; }
   static __device__ __forceinline__ T from_tab(const void* tab, size_t i) {
     return __ldg(static_cast<const double*>(tab) + i);
   }
-  static __device__ __forceinline__ C ld_tw(const void* tab, int i) {
-    const double2 w = static_cast<const double2*>(tab)[i];
-    return C{w.x, w.y};
-  }
   static __device__ __forceinline__ C cmul(C a, C w) {
     return C{fma(a.re, w.re, -a.im * w.im), fma(a.re, w.im, a.im * w.re)};
+  }
+  static __device__ __forceinline__ T ld8(uint32_t a) {
+    double v;
+    asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(a));
+    return v;
+  }
+  static __device__ __forceinline__ void st8(uint32_t a, T v) {
+    asm volatile("st.shared.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
+  }
+  static __device__ __forceinline__ C ld16(uint32_t a) {
+    double x, y;
+    asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(x), "=d"(y) : "r"(a));
+    return C{x, y};
+  }
+  static __device__ __forceinline__ void st16(uint32_t a, C v) {
+    asm volatile("st.shared.v2.f64 [%0], {%1, %2};" ::"r"(a), "d"(v.re), "d"(v.im) : "memory");
   }
 };
 
 struct DF {
   using T = df;
-  using Store = float2;
   struct C {
     df re, im;
   };
@@ -89,20 +105,12 @@ struct DF {
   }
   static __device__ __forceinline__ df half(df a) { return df{0.5f * a.hi, 0.5f * a.lo}; }
   static __device__ __forceinline__ df zero() { return df{0.0f, 0.0f}; }
-  static __device__ __forceinline__ df ld(const Store* p) {
-    const float2 v = *p;
-    return df{v.x, v.y};
-  }
-  static __device__ __forceinline__ void st(Store* p, df v) { *p = make_float2(v.hi, v.lo); }
   static __device__ __forceinline__ df from_tab(const void* tab, size_t i) {
     const float2 v = __ldg(static_cast<const float2*>(tab) + i);
     return df{v.x, v.y};
   }
-  static __device__ __forceinline__ C ld_tw(const void* tab, int i) {
-    const float4 w = static_cast<const float4*>(tab)[i];
-    return C{df{w.x, w.y}, df{w.z, w.w}};
-  }
-  // a.hi*b.hi - c.hi*d.hi + (low-order terms), renormalised: one part of a complex product.
+  // a*b - c*d in compensated arithmetic: exact products of the high parts, TwoSum of their
+  // difference, the low-order cross terms accumulated by FMA, one renormalisation.
   static __device__ __forceinline__ df dot2(df a, df b, df c, df d) {
     const float p1 = __fmul_rn(a.hi, b.hi);
     const float e1 = __fmaf_rn(a.hi, b.hi, -p1);
@@ -122,6 +130,24 @@ struct DF {
   static __device__ __forceinline__ C cmul(C a, C w) {
     return C{dot2(a.re, w.re, a.im, w.im), dot2(a.re, w.im, neg(a.im), w.re)};
   }
+  static __device__ __forceinline__ T ld8(uint32_t a) {
+    float x, y;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(x), "=f"(y) : "r"(a));
+    return df{x, y};
+  }
+  static __device__ __forceinline__ void st8(uint32_t a, T v) {
+    asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v.hi), "f"(v.lo) : "memory");
+  }
+  static __device__ __forceinline__ C ld16(uint32_t a) {
+    float x, y, z, w;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(x), "=f"(y), "=f"(z), "=f"(w) : "r"(a));
+    return C{df{x, y}, df{z, w}};
+  }
+  static __device__ __forceinline__ void st16(uint32_t a, C v) {
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.re.hi), "f"(v.re.lo), "f"(v.im.hi),
+                 "f"(v.im.lo)
+                 : "memory");
+  }
 };
 
 template <class P>
@@ -132,22 +158,22 @@ struct Cx {
   static __device__ __forceinline__ C sub(C a, C b) { return C{P::sub(a.re, b.re), P::sub(a.im, b.im)}; }
   static __device__ __forceinline__ C scale(C a, T g) { return C{P::mul(a.re, g), P::mul(a.im, g)}; }
   static __device__ __forceinline__ C neg(C a) { return C{P::neg(a.re), P::neg(a.im)}; }
-  // multiply by DIR * i
-  template <int DIR>
+  template <int DIR>  // multiply by DIR * i
   static __device__ __forceinline__ C mul_i(C v) {
     return DIR < 0 ? C{v.im, P::neg(v.re)} : C{P::neg(v.im), v.re};
   }
-  static __device__ __forceinline__ C conj_tw(C w) { return C{w.re, P::neg(w.im)}; }
+  static __device__ __forceinline__ C conj(C w) { return C{w.re, P::neg(w.im)}; }
 };
 
-// Constants the radix kernels need, in the policy's precision (filled from FP64 host values).
+// Constants of the radix kernels in the policy's precision (from FP64 host values).
 template <class P>
 struct Consts {
-  typename P::T c8;   // sqrt(1/2)
-  typename P::T s3;   // sqrt(3)/2
+  typename P::T c8;  // sqrt(1/2)
+  typename P::T s3;  // sqrt(3)/2
 };
 
 // ------------------------------------------------------------------ in-register DFTs
+// V[u] = sum_r v[r] exp(DIR 2 pi i u r / R), DIR = -1 forward, +1 inverse.
 
 template <class P, int R, int DIR>
 struct Dft;
@@ -215,310 +241,367 @@ struct Dft<P, 3, DIR> {
 
 // ------------------------------------------------------------------ pass accessors
 
+// XOR swizzle of an index within aligned groups of 8 (identity past the last full group).
+__device__ __forceinline__ int swz(int r, int full8) { return r < full8 ? (r ^ ((r >> 3) & 7)) : r; }
+
 template <class P>
 struct ThetaAcc {
   using C = typename P::C;
   using T = typename P::T;
-  typename P::Store* S;
-  C* ov;           // buffer of the lone circle
-  const T* g;      // multipliers f(|l|)/M, l = 0..Ntheta (shared memory)
-  int ld, Nth, h, M, nseq;
-  bool lone;       // Nphi/2 odd: the last sequence holds circle h-1 alone
+  struct Seq {
+    int b;
+    bool lone;
+    bool general;
+  };
+  uint32_t S;    // shell, row stride ld (8-byte elements)
+  uint32_t ov;   // lone-circle slots (16-byte complex)
+  uint32_t lin;  // scratch: sequence b, index n at (b - b0) * M + swizzled n
+  uint32_t g;    // multipliers f(|l|)/M, l = 0..Ntheta
+  int ld, Nth, Nth8, h, M, M8, nseq, b0;
+  bool lone_last;  // Nphi/2 odd: the last sequence holds circle h-1 alone
   bool odd;        // parity a = 1
+  bool hodd;       // h odd: pairs at column 2s+h are only 8-byte aligned
 
-  __device__ __forceinline__ bool is_lone(int b) const { return lone && b == nseq - 1; }
-  // home of complex slot n of sequence b: row and first column of the value pair
-  __device__ __forceinline__ int home(int b, int n) const {
-    return n < Nth ? n * ld + 2 * b : (n - Nth) * ld + 2 * b + h;
+  __device__ __forceinline__ uint32_t el(int row, int col) const { return S + (uint32_t)(row * ld + col) * 8u; }
+  __device__ __forceinline__ Seq seq(int b) const { return Seq{b, lone_last && b == nseq - 1, false}; }
+  __device__ __forceinline__ C pair_ld(uint32_t a, bool split) const {
+    return split ? C{P::ld8(a), P::ld8(a + 8)} : P::ld16(a);
   }
-  __device__ __forceinline__ C slot_ld(int b, int n) const {
-    if (is_lone(b)) return ov[n];
-    const int o = home(b, n);
-    return C{P::ld(S + o), P::ld(S + o + 1)};
+  __device__ __forceinline__ void pair_st(uint32_t a, bool split, C v) const {
+    if (split) {
+      P::st8(a, v.re);
+      P::st8(a + 8, v.im);
+    } else {
+      P::st16(a, v);
+    }
   }
-  __device__ __forceinline__ void slot_st(int b, int n, C v) const {
-    if (is_lone(b)) {
-      ov[n] = v;
+  // intermediate slot n of a sequence: swizzled row, the sequence's column pair
+  __device__ __forceinline__ C slot_ld(const Seq& s, int n) const {
+    if (s.lone) return P::ld16(ov + 16u * n);
+    const bool up = n < Nth;
+    const int r = up ? n : n - Nth;
+    return pair_ld(el(swz(r, Nth8), up ? 2 * s.b : 2 * s.b + h), hodd && !up);
+  }
+  __device__ __forceinline__ void slot_st(const Seq& s, int n, C v) const {
+    if (s.lone) {
+      P::st16(ov + 16u * n, v);
       return;
     }
-    const int o = home(b, n);
-    P::st(S + o, v.re);
-    P::st(S + o + 1, v.im);
+    const bool up = n < Nth;
+    const int r = up ? n : n - Nth;
+    pair_st(el(swz(r, Nth8), up ? 2 * s.b : 2 * s.b + h), hodd && !up, v);
   }
-  // circle sample q of the sequence: slot pi(q) with the parity sign for q >= Ntheta
-  __device__ __forceinline__ C gather(int b, int q) const {
+  // circle sample q, read from the shell's own layout with the parity sign past the pole
+  __device__ __forceinline__ C gather(const Seq& s, int q) const {
     const bool up = q < Nth;
-    const int n = up ? q : 3 * Nth - 1 - q;
-    C v;
-    if (is_lone(b)) {
-      v = C{P::ld(S + home(b, n)), P::zero()};
-    } else {
-      v = slot_ld(b, n);
-    }
+    const uint32_t a = el(up ? q : M - 1 - q, up ? 2 * s.b : 2 * s.b + h);
+    C v = s.lone ? C{P::ld8(a), P::zero()} : pair_ld(a, hodd && !up);
     if (!up && odd) v = Cx<P>::neg(v);
     return v;
   }
-  __device__ __forceinline__ void scatter(int b, int q, C v) const {
+  __device__ __forceinline__ void scatter(const Seq& s, int q, C v) const {
     const bool up = q < Nth;
-    const int n = up ? q : 3 * Nth - 1 - q;
     if (!up && odd) v = Cx<P>::neg(v);
-    if (is_lone(b)) {
-      P::st(S + home(b, n), v.re);
-      return;
-    }
-    const int o = home(b, n);
-    P::st(S + o, v.re);
-    P::st(S + o + 1, v.im);
+    const uint32_t a = el(up ? q : M - 1 - q, up ? 2 * s.b : 2 * s.b + h);
+    if (s.lone) P::st8(a, v.re);
+    else pair_st(a, hodd && !up, v);
   }
-  __device__ __forceinline__ T mult(int, int l) const { return g[l <= Nth ? l : M - l]; }
-  __device__ __forceinline__ bool general(int) const { return false; }
+  __device__ __forceinline__ T mult(const Seq&, int l) const { return P::ld8(g + 8u * (l <= Nth ? l : M - l)); }
+  __device__ __forceinline__ uint32_t lin_at(int b, int n) const {
+    return lin + 16u * (uint32_t)((b - b0) * M + swz(n, M8));
+  }
+  __device__ __forceinline__ C lin_ld(int b, int n) const { return P::ld16(lin_at(b, n)); }
+  __device__ __forceinline__ void lin_st(int b, int n, C v) const { P::st16(lin_at(b, n), v); }
+  // sizes known at compile time for the fixed lengths (2 Ntheta = Nphi = LEN)
+  template <int LEN>
+  __device__ __forceinline__ void fix() {
+    if constexpr (LEN > 0) {
+      Nth = LEN / 2;
+      Nth8 = (LEN / 2) & ~7;
+      ld = LEN + 2;
+      h = LEN / 2;
+      M = LEN;
+      M8 = LEN & ~7;
+      nseq = (LEN / 2 + 1) / 2;
+      lone_last = hodd = ((LEN / 2) & 1) != 0;
+    }
+  }
 };
 
 template <class P>
 struct PhiAcc {
   using C = typename P::C;
   using T = typename P::T;
-  typename P::Store* S;
-  C* ov;            // buffer of the lone middle ring
-  const int2* pairs;  // (j1, j2), j2 < 0 for the lone ring; bit 30 of j1 marks a general pair
+  struct Seq {
+    int j1, j2;  // j2 < 0: lone middle ring
+    bool general;
+  };
+  uint32_t S, ov;
+  uint32_t lin;       // scratch: sequence b, index n at (b - b0) * N + swizzled n
+  const int2* pairs;  // (j1 | general << 30, j2) in shared memory
   const void* gtab;   // multipliers f(|m|)/Nphi of this shell: [Ntheta][Nphi/2+1] (global)
   size_t gbase;
-  int ld, N, hN, nh;
+  int ld, N, N8, hN, hN8, nh, b0;
 
-  __device__ __forceinline__ int j1(int b) const { return pairs[b].x & 0x3fffffff; }
-  __device__ __forceinline__ int j2(int b) const { return pairs[b].y; }
-  __device__ __forceinline__ bool general(int b) const { return (pairs[b].x >> 30) & 1; }
-  __device__ __forceinline__ C slot_ld(int b, int n) const {
-    const int q = j2(b);
-    if (q < 0) return ov[n];
-    const int o = (n < hN ? j1(b) : q) * ld + 2 * (n < hN ? n : n - hN);
-    return C{P::ld(S + o), P::ld(S + o + 1)};
+  __device__ __forceinline__ uint32_t el(int row, int col) const { return S + (uint32_t)(row * ld + col) * 8u; }
+  __device__ __forceinline__ Seq seq(int b) const {
+    const int2 p = pairs[b];
+    return Seq{p.x & 0x3fffffff, p.y, ((p.x >> 30) & 1) != 0};
   }
-  __device__ __forceinline__ void slot_st(int b, int n, C v) const {
-    const int q = j2(b);
-    if (q < 0) {
-      ov[n] = v;
-      return;
-    }
-    const int o = (n < hN ? j1(b) : q) * ld + 2 * (n < hN ? n : n - hN);
-    P::st(S + o, v.re);
-    P::st(S + o + 1, v.im);
+  __device__ __forceinline__ uint32_t slot(const Seq& s, int n) const {
+    const bool lo = n < hN;
+    const int u = lo ? n : n - hN;
+    return el(lo ? s.j1 : s.j2, 2 * swz(u, hN8));
   }
-  __device__ __forceinline__ C gather(int b, int k) const {
-    const int q = j2(b);
-    return C{P::ld(S + j1(b) * ld + k), q >= 0 ? P::ld(S + q * ld + k) : P::zero()};
+  __device__ __forceinline__ C slot_ld(const Seq& s, int n) const {
+    return s.j2 < 0 ? P::ld16(ov + 16u * n) : P::ld16(slot(s, n));
   }
-  __device__ __forceinline__ void scatter(int b, int k, C v) const {
-    const int q = j2(b);
-    P::st(S + j1(b) * ld + k, v.re);
-    if (q >= 0) P::st(S + q * ld + k, v.im);
+  __device__ __forceinline__ void slot_st(const Seq& s, int n, C v) const {
+    if (s.j2 < 0) P::st16(ov + 16u * n, v);
+    else P::st16(slot(s, n), v);
+  }
+  __device__ __forceinline__ C gather(const Seq& s, int k) const {
+    return C{P::ld8(el(s.j1, k)), s.j2 >= 0 ? P::ld8(el(s.j2, k)) : P::zero()};
+  }
+  __device__ __forceinline__ void scatter(const Seq& s, int k, C v) const {
+    P::st8(el(s.j1, k), v.re);
+    if (s.j2 >= 0) P::st8(el(s.j2, k), v.im);
   }
   __device__ __forceinline__ T ring_mult(int j, int m) const {
     return P::from_tab(gtab, gbase + (size_t)j * nh + (m <= hN ? m : N - m));
   }
-  __device__ __forceinline__ T mult(int b, int m) const { return ring_mult(j1(b), m); }
+  __device__ __forceinline__ T mult(const Seq& s, int m) const { return ring_mult(s.j1, m); }
+  __device__ __forceinline__ uint32_t lin_at(int b, int n) const {
+    return lin + 16u * (uint32_t)((b - b0) * N + swz(n, N8));
+  }
+  __device__ __forceinline__ C lin_ld(int b, int n) const { return P::ld16(lin_at(b, n)); }
+  __device__ __forceinline__ void lin_st(int b, int n, C v) const { P::st16(lin_at(b, n), v); }
+  template <int LEN>
+  __device__ __forceinline__ void fix() {
+    if constexpr (LEN > 0) {
+      ld = LEN + 2;
+      N = LEN;
+      N8 = LEN & ~7;
+      hN = LEN / 2;
+      hN8 = (LEN / 2) & ~7;
+      nh = LEN / 2 + 1;
+    }
+  }
 };
 
-// ------------------------------------------------------------------ register-staged stage
+// ------------------------------------------------------------------ FFT stage
 
 enum { kFirst = 1, kLast = 2, kMul = 4 };
 
-template <class P, class Acc, int R, int DIR, int MODE>
-__device__ __forceinline__ void stage(const Acc& A, int N, int B, int Ns, const typename P::C* tw,
-                                      const Consts<P>& k) {
+// One radix-R Stockham stage over all B sequences: from the shell slots to the scratch (FROM_SLOTS)
+// or back. kFirst reads the logical sequence out of the shell layout, kLast writes it back there,
+// kMul multiplies each input by the spectral multiplier.
+template <class P, class Acc, int R, int DIR, int MODE, bool FROM_SLOTS>
+__device__ __forceinline__ void stage(const Acc& A, int N, int B, int Ns, uint32_t tw, const Consts<P>& k) {
   using C = typename P::C;
   using X = Cx<P>;
-  constexpr int MAXI = (kMaxV + R - 1) / R;
   const int NR = N / R;
   const int total = B * NR;
   const int tws = N / (Ns * R);
-  C v[MAXI][R];
+#pragma unroll 1
+  for (int w = threadIdx.x; w < total; w += blockDim.x) {
+    const int bl = w / NR, j = w - bl * NR;
+    const int b = A.b0 + bl;
+    const int kk = j % Ns;
+    const auto sq = A.seq(b);
+    C v[R];
 #pragma unroll
-  for (int u = 0; u < MAXI; ++u) {
-    const int w = threadIdx.x + u * blockDim.x;
-    if (w < total) {
-      const int b = w / NR, j = w - b * NR;
-      const int kk = j % Ns;
-#pragma unroll
-      for (int t = 0; t < R; ++t) {
-        const int n = j + t * NR;
-        C x = (MODE & kFirst) ? A.gather(b, n) : A.slot_ld(b, n);
-        if (MODE & kMul) {
-          if (!A.general(b)) x = X::scale(x, A.mult(b, n));
-        }
-        v[u][t] = x;
-      }
-      if (Ns > 1) {
-#pragma unroll
-        for (int t = 1; t < R; ++t) {
-          C wt = tw[t * kk * tws];
-          if (DIR > 0) wt = X::conj_tw(wt);
-          v[u][t] = P::cmul(v[u][t], wt);
-        }
-      }
-      Dft<P, R, DIR>::run(v[u], k);
+    for (int t = 0; t < R; ++t) {
+      const int n = j + t * NR;
+      C x = (MODE & kFirst) ? A.gather(sq, n) : (FROM_SLOTS ? A.slot_ld(sq, n) : A.lin_ld(b, n));
+      if ((MODE & kMul) && !sq.general) x = X::scale(x, A.mult(sq, n));
+      v[t] = x;
     }
-  }
-  __syncthreads();
+    if (Ns > 1) {
 #pragma unroll
-  for (int u = 0; u < MAXI; ++u) {
-    const int w = threadIdx.x + u * blockDim.x;
-    if (w < total) {
-      const int b = w / NR, j = w - b * NR;
-      const int kk = j % Ns;
-      const int base = (j / Ns) * Ns * R + kk;
-#pragma unroll
-      for (int t = 0; t < R; ++t) {
-        if (MODE & kLast) A.scatter(b, base + t * Ns, v[u][t]);
-        else A.slot_st(b, base + t * Ns, v[u][t]);
+      for (int t = 1; t < R; ++t) {
+        C wt = P::ld16(tw + 16u * (uint32_t)(t * kk * tws));
+        if (DIR > 0) wt = X::conj(wt);
+        v[t] = P::cmul(v[t], wt);
       }
+    }
+    Dft<P, R, DIR>::run(v, k);
+    const int base = (j / Ns) * Ns * R + kk;
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      const int n = base + t * Ns;
+      if (MODE & kLast) A.scatter(sq, n, v[t]);
+      else if (FROM_SLOTS) A.lin_st(b, n, v[t]);
+      else A.slot_st(sq, n, v[t]);
     }
   }
   __syncthreads();
 }
 
-// Generic lengths: each stage is its own function, so the register allocation of one radix does not
+// Generic lengths: each stage is its own function, so one radix's register allocation does not
 // weigh on the others (the call costs a register save and restore per stage).
 template <class P, class Acc, int R, int DIR, int MODE>
-__device__ __noinline__ void stage_ni(const Acc& A, int N, int B, int Ns, const typename P::C* tw,
-                                      const Consts<P>& k) {
-  stage<P, Acc, R, DIR, MODE>(A, N, B, Ns, tw, k);
+__device__ __noinline__ void stage_ni(const Acc A, int N, int B, int Ns, uint32_t tw, const Consts<P> k,
+                                      bool from_slots) {
+  if (from_slots) stage<P, Acc, R, DIR, MODE, true>(A, N, B, Ns, tw, k);
+  else stage<P, Acc, R, DIR, MODE, false>(A, N, B, Ns, tw, k);
 }
 
 template <class P, class Acc, int DIR, int MODE>
-__device__ __forceinline__ void stage_r(int R, const Acc& A, int N, int B, int Ns, const typename P::C* tw,
-                                        const Consts<P>& k) {
+__device__ __forceinline__ void stage_r(int R, const Acc& A, int N, int B, int Ns, uint32_t tw, const Consts<P>& k,
+                                        bool from_slots) {
   switch (R) {
-    case 8: stage_ni<P, Acc, 8, DIR, MODE>(A, N, B, Ns, tw, k); break;
-    case 4: stage_ni<P, Acc, 4, DIR, MODE>(A, N, B, Ns, tw, k); break;
-    case 2: stage_ni<P, Acc, 2, DIR, MODE>(A, N, B, Ns, tw, k); break;
-    default: stage_ni<P, Acc, 3, DIR, MODE>(A, N, B, Ns, tw, k); break;
+    case 8: stage_ni<P, Acc, 8, DIR, MODE>(A, N, B, Ns, tw, k, from_slots); break;
+    case 4: stage_ni<P, Acc, 4, DIR, MODE>(A, N, B, Ns, tw, k, from_slots); break;
+    case 2: stage_ni<P, Acc, 2, DIR, MODE>(A, N, B, Ns, tw, k, from_slots); break;
+    default: stage_ni<P, Acc, 3, DIR, MODE>(A, N, B, Ns, tw, k, from_slots); break;
   }
 }
 
-// Exact two-real-sequence multiply for pairs whose rings have different multipliers:
+// Exact two-real-sequence multiply for ring pairs whose multipliers differ:
 // W_m = (f1+f2)/2 Z_m + (f1-f2)/2 conj(Z_{N-m}), on the spectrum held in the slots.
 template <class P>
-__device__ void general_multiply(const PhiAcc<P>& A, int B) {
+__device__ void general_multiply(const PhiAcc<P>& A, int B, bool in_slots) {
   using C = typename P::C;
   const int nh = A.N / 2 + 1;
-  C zm, zn, wm, wn;
-  int b = -1, m = 0;
-  // at most one (pair, m) per thread per round; pairs needing this are rare
   for (int base = 0; base < B * nh; base += blockDim.x) {
     const int w = base + threadIdx.x;
     bool act = false;
+    int m = 0, mn = 0, bb = 0;
+    typename PhiAcc<P>::Seq sq{0, -1, false};
+    C wm, wn;
     if (w < B * nh) {
-      b = w / nh;
-      m = w - b * nh;
-      act = A.general(b);
+      const int b = A.b0 + w / nh;
+      bb = b;
+      m = w - (w / nh) * nh;
+      sq = A.seq(b);
+      act = sq.general;
       if (act) {
-        const int mn = (A.N - m) % A.N;
-        zm = A.slot_ld(b, m);
-        zn = A.slot_ld(b, mn);
-        const auto f1 = A.ring_mult(A.j1(b), m), f2 = A.ring_mult(A.j2(b), m);
+        mn = (A.N - m) % A.N;
+        const C zm = in_slots ? A.slot_ld(sq, m) : A.lin_ld(b, m);
+        const C zn = in_slots ? A.slot_ld(sq, mn) : A.lin_ld(b, mn);
+        const auto f1 = A.ring_mult(sq.j1, m), f2 = A.ring_mult(sq.j2, m);
         const auto ca = P::half(P::add(f1, f2)), cd = P::half(P::sub(f1, f2));
-        // conj(z) * cd: (re cd, -im cd)
         wm = C{P::add(P::mul(zm.re, ca), P::mul(zn.re, cd)), P::sub(P::mul(zm.im, ca), P::mul(zn.im, cd))};
         wn = C{P::add(P::mul(zn.re, ca), P::mul(zm.re, cd)), P::sub(P::mul(zn.im, ca), P::mul(zm.im, cd))};
       }
     }
     __syncthreads();
     if (act) {
-      const int mn = (A.N - m) % A.N;
-      A.slot_st(b, m, wm);
-      if (mn != m) A.slot_st(b, mn, wn);
+      if (in_slots) {
+        A.slot_st(sq, m, wm);
+        if (mn != m) A.slot_st(sq, mn, wn);
+      } else {
+        A.lin_st(bb, m, wm);
+        if (mn != m) A.lin_st(bb, mn, wn);
+      }
     }
     __syncthreads();
   }
 }
 
 template <class P>
-__device__ __forceinline__ void maybe_general_multiply(const ThetaAcc<P>&, int) {}
+__device__ __forceinline__ void maybe_general_multiply(const ThetaAcc<P>&, int, bool) {}
 template <class P>
-__device__ __forceinline__ void maybe_general_multiply(const PhiAcc<P>& A, int B) {
-  general_multiply<P>(A, B);
+__device__ __forceinline__ void maybe_general_multiply(const PhiAcc<P>& A, int B, bool in_slots) {
+  general_multiply<P>(A, B, in_slots);
 }
 
+// Runtime radix sequence (generic lengths).
 template <class P, class Acc>
-__device__ void filter_pass(const Acc& A, int N, int B, const Factors& f, const typename P::C* tw,
-                            const Consts<P>& k, bool has_general) {
-  // forward transform: first stage gathers the logical sequence
+__device__ void pass_rt(const Acc& A, int N, int B, const Factors& f, uint32_t tw, const Consts<P>& k,
+                        bool has_general) {
+  // stage g (0-based over forward and inverse) reads the slots when g is even
   int Ns = 1;
   for (int s = 0; s < f.nst; ++s) {
     const int R = f.radix[s];
-    if (s == 0) stage_r<P, Acc, -1, kFirst>(R, A, N, B, Ns, tw, k);
-    else stage_r<P, Acc, -1, 0>(R, A, N, B, Ns, tw, k);
+    if (s == 0) stage_r<P, Acc, -1, kFirst>(R, A, N, B, Ns, tw, k, true);
+    else stage_r<P, Acc, -1, 0>(R, A, N, B, Ns, tw, k, (s & 1) == 0);
     Ns *= R;
   }
-  if (has_general) maybe_general_multiply<P>(A, B);
-  // inverse transform: first stage multiplies, last stage scatters
+  if (has_general) maybe_general_multiply<P>(A, B, (f.nst & 1) == 0);
   Ns = 1;
   for (int s = 0; s < f.nst; ++s) {
     const int R = f.radix[s];
     const bool first = s == 0, last = s == f.nst - 1;
-    if (first && last) stage_r<P, Acc, 1, kMul | kLast>(R, A, N, B, Ns, tw, k);
-    else if (first) stage_r<P, Acc, 1, kMul>(R, A, N, B, Ns, tw, k);
-    else if (last) stage_r<P, Acc, 1, kLast>(R, A, N, B, Ns, tw, k);
-    else stage_r<P, Acc, 1, 0>(R, A, N, B, Ns, tw, k);
+    const bool from_slots = ((f.nst + s) & 1) == 0;
+    if (first && last) stage_r<P, Acc, 1, kMul | kLast>(R, A, N, B, Ns, tw, k, from_slots);
+    else if (first) stage_r<P, Acc, 1, kMul>(R, A, N, B, Ns, tw, k, from_slots);
+    else if (last) stage_r<P, Acc, 1, kLast>(R, A, N, B, Ns, tw, k, from_slots);
+    else stage_r<P, Acc, 1, 0>(R, A, N, B, Ns, tw, k, from_slots);
     Ns *= R;
   }
 }
 
-// Fixed lengths: the radix sequence is known at compile time and every stage is inlined.
-template <class P, class Acc, int DIR, int MODE0, int R0, int... Rs>
-__device__ __forceinline__ void run_stages(const Acc& A, int N, int B, int Ns, const typename P::C* tw,
-                                           const Consts<P>& k) {
+// Compile-time radix sequence (fixed lengths): every stage inlined.
+template <class P, class Acc, int DIR, int MODE0, bool FROM_SLOTS, int R0, int... Rs>
+__device__ __forceinline__ void run_stages(const Acc& A, int N, int B, int Ns, uint32_t tw, const Consts<P>& k) {
   constexpr bool last = sizeof...(Rs) == 0;
   constexpr int MODE = MODE0 | ((DIR > 0 && last) ? kLast : 0);
-  stage<P, Acc, R0, DIR, MODE>(A, N, B, Ns, tw, k);
-  if constexpr (!last) run_stages<P, Acc, DIR, 0, Rs...>(A, N, B, Ns * R0, tw, k);
+  stage<P, Acc, R0, DIR, MODE, FROM_SLOTS>(A, N, B, Ns, tw, k);
+  if constexpr (!last) run_stages<P, Acc, DIR, 0, !FROM_SLOTS, Rs...>(A, N, B, Ns * R0, tw, k);
 }
 
 template <class P, class Acc, int... Rs>
-__device__ __forceinline__ void pass_ct(const Acc& A, int N, int B, const typename P::C* tw, const Consts<P>& k,
+__device__ __forceinline__ void pass_ct(const Acc& A, int N, int B, uint32_t tw, const Consts<P>& k,
                                         bool has_general) {
-  run_stages<P, Acc, -1, kFirst, Rs...>(A, N, B, 1, tw, k);
-  if (has_general) maybe_general_multiply<P>(A, B);
-  run_stages<P, Acc, 1, kMul, Rs...>(A, N, B, 1, tw, k);
+  constexpr bool even = (sizeof...(Rs) % 2) == 0;  // the spectrum lands in the slots
+  run_stages<P, Acc, -1, kFirst, true, Rs...>(A, N, B, 1, tw, k);
+  if (has_general) maybe_general_multiply<P>(A, B, even);
+  run_stages<P, Acc, 1, kMul, even, Rs...>(A, N, B, 1, tw, k);
 }
 
 // Lengths with a compiled radix sequence (theta circles of 2 Ntheta = Nphi = LEN).
-template <int LEN>
-struct FixedLen {
-  static constexpr bool ok = LEN == 32 || LEN == 64 || LEN == 96 || LEN == 128 || LEN == 192 || LEN == 256;
-};
-
 template <class P, class Acc, int LEN>
-__device__ __forceinline__ void pass_fixed(const Acc& A, int B, const typename P::C* tw, const Consts<P>& k,
-                                           bool g) {
+__device__ __forceinline__ void run_pass(const Acc& A, int N, int B, const Factors& f, uint32_t tw,
+                                         const Consts<P>& k, bool g) {
   if constexpr (LEN == 32) pass_ct<P, Acc, 8, 4>(A, LEN, B, tw, k, g);
   else if constexpr (LEN == 64) pass_ct<P, Acc, 8, 8>(A, LEN, B, tw, k, g);
   else if constexpr (LEN == 96) pass_ct<P, Acc, 8, 4, 3>(A, LEN, B, tw, k, g);
   else if constexpr (LEN == 128) pass_ct<P, Acc, 8, 8, 2>(A, LEN, B, tw, k, g);
   else if constexpr (LEN == 192) pass_ct<P, Acc, 8, 8, 3>(A, LEN, B, tw, k, g);
   else if constexpr (LEN == 256) pass_ct<P, Acc, 8, 8, 4>(A, LEN, B, tw, k, g);
+  else pass_rt<P, Acc>(A, N, B, f, tw, k, g);
 }
 
-template <class P, class Acc, int LEN>
-__device__ __forceinline__ void run_pass(const Acc& A, int N, int B, const Factors& f, const typename P::C* tw,
-                                         const Consts<P>& k, bool g) {
-  if constexpr (LEN != 0) pass_fixed<P, Acc, LEN>(A, B, tw, k, g);
-  else filter_pass<P>(A, N, B, f, tw, k, g);
+// Each pass is its own function: its registers are allocated apart from the load/store code.
+template <class P, int LEN>
+__device__ __noinline__ void theta_pass_fn(ThetaAcc<P> TA, Factors f, uint32_t tw, Consts<P> K, int batch) {
+  TA.template fix<LEN>();
+  for (int b0 = 0; b0 < TA.nseq; b0 += batch) {
+    TA.b0 = b0;
+    run_pass<P, ThetaAcc<P>, LEN>(TA, TA.M, min(batch, TA.nseq - b0), f, tw, K, false);
+  }
+}
+
+template <class P, int LEN>
+__device__ __noinline__ void phi_pass_fn(PhiAcc<P> PA, int npairs, bool has_general, Factors f, uint32_t tw,
+                                         Consts<P> K, int batch) {
+  PA.template fix<LEN>();
+  for (int b0 = 0; b0 < npairs; b0 += batch) {
+    PA.b0 = b0;
+    run_pass<P, PhiAcc<P>, LEN>(PA, PA.N, min(batch, npairs - b0), f, tw, K, has_general);
+  }
 }
 
 // ------------------------------------------------------------------ kernel
 
 template <class P>
 struct Layout {
-  typename P::Store* S;
-  typename P::C* ov;
-  typename P::C* tw_th;
-  typename P::C* tw_ph;
-  typename P::T* g_th;
+  unsigned char* buf;  // the shell
+  uint32_t lin;        // FFT scratch
+  uint32_t ov, tw_th, tw_ph, g_th;
   int2* pairs;
   int* misc;  // [0] pair count, [1] general flag, [2] block max exponent
 };
+
+// Scratch for one batch: batch_th theta sequences (2 Ntheta slots each) or batch_ph phi pairs
+// (Nphi slots each).
+__host__ __device__ __forceinline__ size_t scratch_bytes(const ShellArgs2& A) {
+  const size_t th = (size_t)A.batch_th * 2 * A.Nth;
+  const size_t ph = (size_t)A.batch_ph * A.Nph;
+  return 16 * (th > ph ? th : ph);
+}
 
 template <class P>
 __device__ Layout<P> carve(const ShellArgs2& A, unsigned char* base) {
@@ -529,11 +612,13 @@ __device__ Layout<P> carve(const ShellArgs2& A, unsigned char* base) {
     off = (off + bytes + 15) / 16 * 16;
     return p;
   };
-  L.S = reinterpret_cast<typename P::Store*>(take(sizeof(typename P::Store) * (size_t)A.Nth * A.ldS));
-  L.ov = reinterpret_cast<typename P::C*>(take(sizeof(typename P::C) * (size_t)max(2 * A.Nth, A.Nph)));
-  L.tw_th = reinterpret_cast<typename P::C*>(take(sizeof(typename P::C) * 2 * (size_t)A.Nth));
-  L.tw_ph = reinterpret_cast<typename P::C*>(take(sizeof(typename P::C) * (size_t)A.Nph));
-  L.g_th = reinterpret_cast<typename P::T*>(take(sizeof(typename P::T) * (size_t)(A.Nth + 1)));
+  const size_t shell_bytes = 8 * (size_t)A.Nth * A.ldS;
+  L.buf = take(shell_bytes);
+  L.lin = saddr(take(scratch_bytes(A)));
+  L.ov = saddr(take(16 * (size_t)max(2 * A.Nth, A.Nph)));
+  L.tw_th = saddr(take(16 * 2 * (size_t)A.Nth));
+  L.tw_ph = saddr(take(16 * (size_t)A.Nph));
+  L.g_th = saddr(take(8 * (size_t)(A.Nth + 1)));
   L.pairs = reinterpret_cast<int2*>(take(sizeof(int2) * (size_t)(A.Nth / 2 + 1)));
   L.misc = reinterpret_cast<int*>(take(sizeof(int) * 4));
   return L;
@@ -553,46 +638,71 @@ __device__ __forceinline__ double from_real<F64>(double x, int) { return x; }
 template <>
 __device__ __forceinline__ double from_real<DF>(df x, int E) { return df_to_double(x, E); }
 
+// Shell s in i-major order (the fields of one radius run together, so their multiplier rows stay in
+// L2); returns the element offset of the shell in the [var][shell] state layout.
+__device__ __forceinline__ size_t shell_offset(const ShellArgs2& A, int s, int* v, int* i) {
+  *i = s / A.nvars;
+  *v = s - *i * A.nvars;
+  return ((size_t)*v * A.Nr + *i) * (size_t)A.Nth * A.Nph;
+}
+
+// Start the asynchronous copy of shell s into a buffer (16-byte pieces into the padded rows).
+__device__ __forceinline__ void issue_load(const ShellArgs2& A, const double* in, int s, unsigned char* buf) {
+  int v, i;
+  const double* src = in + shell_offset(A, s, &v, &i);
+  const int half = A.Nph / 2, total = A.Nth * half;
+  const uint32_t dst = saddr(buf);
+  for (int c = threadIdx.x; c < total; c += blockDim.x) {
+    const int row = c / half, k2 = c - row * half;
+    const uint32_t d = dst + (uint32_t)(row * A.ldS + 2 * k2) * 8u;
+    const double* g = src + (size_t)row * A.Nph + 2 * k2;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(g) : "memory");
+  }
+}
+
 template <class P, int LEN>
-__global__ void __launch_bounds__(512, 1) shell_kernel(ShellArgs2 A, LaunchIO io) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  using T = typename P::T;
-  using C = typename P::C;
-  const Layout<P> L = carve<P>(A, smem_raw);
-  // i-major order: the fields of one radius run together, so their multiplier rows stay in L2
-  const int i = blockIdx.x / A.nvars, v = blockIdx.x - i * A.nvars;
-  const int shell = v * A.Nr + i;
+__device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layout<P>& L, unsigned char* buf, int s,
+                             const Consts<P>& K) {
+  constexpr bool dfp = std::is_same<P, DF>::value;
+  int v, i;
+  const size_t off = shell_offset(A, s, &v, &i);
   const VarInfo vi = A.var[v];
   const int Nth = A.Nth, Nph = A.Nph, ld = A.ldS;
   const int npts = Nth * Nph;
-  constexpr bool dfp = std::is_same<P, DF>::value;
+  double* Sd = reinterpret_cast<double*>(buf);
 
-  // every stage must fit the registers: B * N <= blockDim * (R * floor(16 / R)) for each radix
-  if (threadIdx.x == 0 && (int)blockDim.x < A.min_threads) atomicCAS(A.status, 0u, (unsigned)SPH_EDEVICE);
-  if ((int)blockDim.x < A.min_threads) return;
-
-  // twiddles, constants, theta multipliers
-  const C* twth_g = static_cast<const C*>(A.tw_th);
-  const C* twph_g = static_cast<const C*>(A.tw_ph);
-  for (int n = threadIdx.x; n < 2 * Nth; n += blockDim.x) L.tw_th[n] = twth_g[n];
-  for (int n = threadIdx.x; n < Nph; n += blockDim.x) L.tw_ph[n] = twph_g[n];
-  const size_t gth_base = ((size_t)vi.cls * A.Nr + i) * (Nth + 1);
-  for (int n = threadIdx.x; n <= Nth; n += blockDim.x) L.g_th[n] = P::from_tab(A.g_th, gth_base + n);
-  Consts<P> K;
-  K.c8 = P::from_tab(A.consts, 0);
-  K.s3 = P::from_tab(A.consts, 1);
-
-  // load the shell (raw FP64 first, so the compensated form can pick its scale)
-  const double* srcd = static_cast<const double*>(io.in) + (size_t)shell * npts;
-  const float* srcf = static_cast<const float*>(io.in) + (size_t)shell * npts;
-  double* Sd = reinterpret_cast<double*>(L.S);
+  // FP32 or unaligned input: synchronous load (8 loads in flight per thread), as FP64 in the buffer
+  if (io.is_f32 || !io.async_ok) {
+    const float* srcf = static_cast<const float*>(io.in) + off;
+    const double* srcd = static_cast<const double*>(io.in) + off;
+    constexpr int kBatch = 8;
+    for (int n0 = 0; n0 < npts; n0 += kBatch * blockDim.x) {
+      double xv[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const int n = n0 + u * blockDim.x + threadIdx.x;
+        xv[u] = n < npts ? (io.is_f32 ? (double)__ldcs(srcf + n) : __ldcs(srcd + n)) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const int n = n0 + u * blockDim.x + threadIdx.x;
+        if (n < npts) Sd[(n / Nph) * ld + n % Nph] = xv[u];
+      }
+    }
+    __syncthreads();
+  }
+  // input map, block exponent, conversion to the working precision (in place)
   unsigned emax = 0;
-  for (int n = threadIdx.x; n < npts; n += blockDim.x) {
-    const int j = n / Nph, k = n - j * Nph;
-    double x = io.is_f32 ? (double)srcf[n] : srcd[n];
-    if (io.map_in == kMapTanh) x = tanh(x);
-    Sd[j * ld + k] = x;
-    if (dfp) emax = max(emax, (unsigned)df_exp_field(x));
+  if (io.map_in == kMapTanh || dfp) {
+    for (int n = threadIdx.x; n < npts; n += blockDim.x) {
+      const int o = (n / Nph) * ld + n % Nph;
+      double x = Sd[o];
+      if (io.map_in == kMapTanh) {
+        x = tanh(x);
+        Sd[o] = x;
+      }
+      if (dfp) emax = max(emax, (unsigned)df_exp_field(x));
+    }
   }
   int E = 0;
   if (dfp) {
@@ -602,30 +712,19 @@ __global__ void __launch_bounds__(512, 1) shell_kernel(ShellArgs2 A, LaunchIO io
     if ((threadIdx.x & 31) == 0) atomicMax(&L.misc[2], (int)emax);
     __syncthreads();
     E = L.misc[2] - 1023;
+    const uint32_t sb = saddr(buf);
     for (int n = threadIdx.x; n < npts; n += blockDim.x) {
-      const int j = n / Nph, k = n - j * Nph;
-      P::st(L.S + j * ld + k, to_real<P>(Sd[j * ld + k], E));
+      const int o = (n / Nph) * ld + n % Nph;
+      P::st8(sb + 8u * o, to_real<P>(Sd[o], E));
     }
   }
-  __syncthreads();
 
+  // per-shell tables: theta multipliers, phi ring pairs
   const double lmax = A.lmax[vi.cls * A.Nr + i];
   const bool gauss = vi.kind == SPH_FILTER_GAUSS;
   const bool theta_on = gauss || lmax < (double)Nth;
-
-  ThetaAcc<P> TA;
-  TA.S = L.S;
-  TA.ov = L.ov;
-  TA.g = L.g_th;
-  TA.ld = ld;
-  TA.Nth = Nth;
-  TA.h = Nph / 2;
-  TA.M = 2 * Nth;
-  TA.nseq = (Nph / 2 + 1) / 2;
-  TA.lone = (Nph / 2) & 1;
-  TA.odd = vi.parity != 0;
-
-  // phi pairs: rings j and Ntheta-1-j, active unless both keep every mode
+  const size_t gth_base = ((size_t)vi.cls * A.Nr + i) * (Nth + 1);
+  for (int n = threadIdx.x; n <= Nth; n += blockDim.x) P::st8(L.g_th + 8u * n, P::from_tab(A.g_th, gth_base + n));
   const uint8_t* ring_info = A.ring_info + ((size_t)vi.cls * A.Nr + i) * Nth;
   if (threadIdx.x == 0) {
     int np = 0, gen = 0;
@@ -644,53 +743,100 @@ __global__ void __launch_bounds__(512, 1) shell_kernel(ShellArgs2 A, LaunchIO io
     L.misc[0] = np;
     L.misc[1] = gen;
   }
+  __syncthreads();
+  const int npairs = L.misc[0];
+  const bool has_general = L.misc[1] != 0;
+
+  ThetaAcc<P> TA;
+  TA.S = saddr(buf);
+  TA.ov = L.ov;
+  TA.lin = L.lin;
+  TA.g = L.g_th;
+  TA.ld = ld;
+  TA.Nth = Nth;
+  TA.Nth8 = Nth & ~7;
+  TA.h = Nph / 2;
+  TA.M = 2 * Nth;
+  TA.M8 = (2 * Nth) & ~7;
+  TA.nseq = (Nph / 2 + 1) / 2;
+  TA.lone_last = (Nph / 2) & 1;
+  TA.odd = vi.parity != 0;
+  TA.hodd = (Nph / 2) & 1;
+  TA.b0 = 0;
+
   PhiAcc<P> PA;
-  PA.S = L.S;
+  PA.S = saddr(buf);
   PA.ov = L.ov;
+  PA.lin = L.lin;
   PA.pairs = L.pairs;
   PA.gtab = A.g_ph;
   PA.gbase = ((size_t)vi.cls * A.Nr + i) * (size_t)Nth * (Nph / 2 + 1);
   PA.ld = ld;
   PA.N = Nph;
+  PA.N8 = Nph & ~7;
   PA.hN = Nph / 2;
+  PA.hN8 = (Nph / 2) & ~7;
   PA.nh = Nph / 2 + 1;
-  __syncthreads();
-  const int npairs = L.misc[0];
-  const bool has_general = L.misc[1] != 0;
+  PA.b0 = 0;
 
-  // filter: theta pass then phi pass, or the reverse order for the transpose
+  // the filter: theta pass then phi pass, or the reverse order for the transpose
   for (int step = 0; step < 2; ++step) {
     if ((step == 0) != (io.transpose != 0)) {
-      if (theta_on) run_pass<P, ThetaAcc<P>, LEN>(TA, 2 * Nth, TA.nseq, A.f_th, L.tw_th, K, false);
+      if (theta_on) theta_pass_fn<P, LEN>(TA, A.f_th, L.tw_th, K, A.batch_th);
     } else {
-      if (npairs) run_pass<P, PhiAcc<P>, LEN>(PA, Nph, npairs, A.f_ph, L.tw_ph, K, has_general);
+      if (npairs) phi_pass_fn<P, LEN>(PA, npairs, has_general, A.f_ph, L.tw_ph, K, A.batch_ph);
     }
   }
 
-  const size_t off = (size_t)shell * npts;
+  // store (streaming), with the output map
+  const uint32_t sb = saddr(buf);
   for (int n = threadIdx.x; n < npts; n += blockDim.x) {
-    const int j = n / Nph, k = n - j * Nph;
-    double y = from_real<P>(P::ld(L.S + j * ld + k), E);
+    const int o = (n / Nph) * ld + n % Nph;
+    double y = from_real<P>(P::ld8(sb + 8u * o), E);
     if (io.map_out == kOutTanhGrad) {
       const double z = io.is_f32 ? (double)static_cast<const float*>(io.aux)[off + n]
                                  : static_cast<const double*>(io.aux)[off + n];
       const double t = tanh(z);
       y *= (1.0 - t * t);
     }
-    if (io.is_f32) static_cast<float*>(io.out)[off + n] = (float)y;
-    else static_cast<double*>(io.out)[off + n] = y;
+    if (io.is_f32) __stcs(static_cast<float*>(io.out) + off + n, (float)y);
+    else __stcs(static_cast<double*>(io.out) + off + n, y);
   }
+}
+
+template <class P, int LEN>
+__global__ void __launch_bounds__(512) shell_kernel(ShellArgs2 A, LaunchIO io) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Layout<P> L = carve<P>(A, smem_raw);
+
+  // twiddles and radix constants, once per CTA
+  const typename P::C* twth_g = static_cast<const typename P::C*>(A.tw_th);
+  const typename P::C* twph_g = static_cast<const typename P::C*>(A.tw_ph);
+  for (int n = threadIdx.x; n < 2 * A.Nth; n += blockDim.x) P::st16(L.tw_th + 16u * n, twth_g[n]);
+  for (int n = threadIdx.x; n < A.Nph; n += blockDim.x) P::st16(L.tw_ph + 16u * n, twph_g[n]);
+  Consts<P> K;
+  K.c8 = P::from_tab(A.consts, 0);
+  K.s3 = P::from_tab(A.consts, 1);
+
+  const int sidx = blockIdx.x;
+  if (!io.is_f32 && io.async_ok) {
+    issue_load(A, static_cast<const double*>(io.in), sidx, L.buf);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+  }
+  __syncthreads();
+  filter_shell<P, LEN>(A, io, L, L.buf, sidx, K);
 }
 
 template <class P>
 size_t shell_smem(const ShellArgs2& a) {
   auto up = [](size_t x) { return (x + 15) / 16 * 16; };
-  const size_t cs = 2 * sizeof(typename P::T);
-  size_t s = up(sizeof(typename P::Store) * (size_t)a.Nth * a.ldS);
-  s += up(cs * (size_t)std::max(2 * a.Nth, a.Nph));
-  s += up(cs * 2 * (size_t)a.Nth);
-  s += up(cs * (size_t)a.Nph);
-  s += up(sizeof(typename P::T) * (size_t)(a.Nth + 1));
+  size_t s = up(8 * (size_t)a.Nth * a.ldS);
+  s += up(scratch_bytes(a));
+  s += up(16 * (size_t)std::max(2 * a.Nth, a.Nph));
+  s += up(16 * 2 * (size_t)a.Nth);
+  s += up(16 * (size_t)a.Nph);
+  s += up(8 * (size_t)(a.Nth + 1));
   s += up(sizeof(int2) * (size_t)(a.Nth / 2 + 1));
   s += up(sizeof(int) * 4);
   return s;
