@@ -104,7 +104,9 @@ sph_status sph_filter_apply_tanh(sph_filter_plan plan, const double* z, double* 
 sph_status sph_filter_apply_adjoint_tanh(sph_filter_plan plan, const double* g, const double* z,
                                          double* out, sph_stream_t stream);
 
-/* FP32 input/output variants of the four calls above (FP32 arithmetic inside). */
+/* FP32 storage variants of the four calls above: in, out, z and g are FP32 device states; the
+ * values are widened on load and rounded once on store, and the arithmetic in between is the
+ * plan's precision. */
 sph_status sph_filter_apply_f32(sph_filter_plan plan, const float* in, float* out, sph_stream_t stream);
 sph_status sph_filter_apply_adjoint_f32(sph_filter_plan plan, const float* in, float* out,
                                         sph_stream_t stream);

@@ -150,6 +150,22 @@ sph_status setup_v2(sph_filter_plan_s* p) {
       if (a.batch_th == 1 && a.batch_ph == 1) break;
     }
   }
+  if (!threads && p->Nth % 4 == 0 && p->Nph % 8 == 0) {
+    // a cluster pair per shell: each CTA holds half of the columns (theta) or a quarter of the rings
+    // (phi) and the halves are exchanged through distributed shared memory
+    const int nseq_cl = (p->Nph / 4 + 1) / 2, npair_cl = p->Nth / 4;
+    for (int div = 1; div <= 64; div *= 2) {
+      a.batch_th = std::max(1, (nseq_cl + div - 1) / div);
+      a.batch_ph = std::max(1, (npair_cl + div - 1) / div);
+      smem = shell_smem_cl_bytes(a, p->precision);
+      if (smem <= optin) {
+        threads = 512;
+        p->cluster = true;
+        break;
+      }
+      if (a.batch_th == 1 && a.batch_ph == 1) break;
+    }
+  }
   if (!threads) return SPH_EUNSUPPORTED;
 
   const bool pair = p->precision == SPH_PREC_F32X2;
@@ -272,8 +288,9 @@ sph_status launch(sph_filter_plan p, const void* in, const void* aux, void* out,
   if (cudaGetDevice(&cur) != cudaSuccess) return SPH_ECUDA;
   if (cur != p->device && cudaSetDevice(p->device) != cudaSuccess) return SPH_ECUDA;
   LaunchIO io{in, aux, out, map_in, map_out, transpose, is_f32, ((uintptr_t)in % 16) == 0 ? 1 : 0};
-  cudaError_t e = p->use_v2 ? launch_shell(p->args2, p->precision, p->threads2, p->smem2, io, (cudaStream_t)stream)
-                            : launch_plain(*p, io, (cudaStream_t)stream);
+  cudaError_t e = !p->use_v2 ? launch_plain(*p, io, (cudaStream_t)stream)
+                  : p->cluster ? launch_shell_cl(p->args2, p->precision, p->threads2, p->smem2, io, (cudaStream_t)stream)
+                               : launch_shell(p->args2, p->precision, p->threads2, p->smem2, io, (cudaStream_t)stream);
   if (cur != p->device) cudaSetDevice(cur);
   return e == cudaSuccess ? SPH_OK : SPH_ECUDA;
 }

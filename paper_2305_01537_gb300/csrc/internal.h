@@ -103,6 +103,24 @@ SPH_DECLARE_SHELL_INST(1, 128)
 SPH_DECLARE_SHELL_INST(1, 192)
 SPH_DECLARE_SHELL_INST(1, 256)
 #undef SPH_DECLARE_SHELL_INST
+// Cluster-pair instantiations for shells too large for one CTA (lengths 256 and generic).
+template <int DFP, int LEN>
+cudaError_t launch_shell_cl_inst(const ShellArgs2& a, int threads, size_t smem, const LaunchIO& io, cudaStream_t s);
+template <int DFP, int LEN>
+cudaError_t set_attr_cl_inst(int bytes);
+#define SPH_DECLARE_SHELL_CL_INST(D, L)                                                                    \
+  template <>                                                                                              \
+  cudaError_t launch_shell_cl_inst<D, L>(const ShellArgs2&, int, size_t, const LaunchIO&, cudaStream_t); \
+  template <>                                                                                              \
+  cudaError_t set_attr_cl_inst<D, L>(int);
+SPH_DECLARE_SHELL_CL_INST(0, 0)
+SPH_DECLARE_SHELL_CL_INST(0, 256)
+SPH_DECLARE_SHELL_CL_INST(1, 0)
+SPH_DECLARE_SHELL_CL_INST(1, 256)
+#undef SPH_DECLARE_SHELL_CL_INST
+size_t shell_smem_cl_bytes(const ShellArgs2& a, int precision);
+cudaError_t launch_shell_cl(const ShellArgs2& a, int precision, int threads, size_t smem, const LaunchIO& io,
+                            cudaStream_t s);
 
 size_t shell_smem_bytes(const ShellArgs2& a, int precision);
 int fixed_length(const ShellArgs2& a);
@@ -129,6 +147,7 @@ struct sph_filter_plan_s {
 
   // staged shell kernel (used when the shape fits it)
   bool use_v2 = false;
+  bool cluster = false;       // a 2-CTA cluster filters each shell
   sph::ShellArgs2 args2{};
   int threads2 = 0;
   size_t smem2 = 0;

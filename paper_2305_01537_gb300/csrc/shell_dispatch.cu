@@ -33,6 +33,18 @@ cudaError_t launch_shell(const ShellArgs2& a, int precision, int threads, size_t
   return launch_p<0>(a, threads, smem, io, s);
 }
 
+size_t shell_smem_cl_bytes(const ShellArgs2& a, int precision) {
+  return precision == SPH_PREC_F32X2 ? shellk::shell_smem_cl<shellk::DF>(a) : shellk::shell_smem_cl<shellk::F64>(a);
+}
+
+cudaError_t launch_shell_cl(const ShellArgs2& a, int precision, int threads, size_t smem, const LaunchIO& io,
+                            cudaStream_t s) {
+  const bool fixed = fixed_length(a) == 256;
+  if (precision == SPH_PREC_F32X2)
+    return fixed ? launch_shell_cl_inst<1, 256>(a, threads, smem, io, s) : launch_shell_cl_inst<1, 0>(a, threads, smem, io, s);
+  return fixed ? launch_shell_cl_inst<0, 256>(a, threads, smem, io, s) : launch_shell_cl_inst<0, 0>(a, threads, smem, io, s);
+}
+
 template <int DFP>
 static cudaError_t set_attr_p(int bytes) {
   cudaError_t e = set_attr_inst<DFP, 0>(bytes);
@@ -42,6 +54,8 @@ static cudaError_t set_attr_p(int bytes) {
   if (e == cudaSuccess) e = set_attr_inst<DFP, 128>(bytes);
   if (e == cudaSuccess) e = set_attr_inst<DFP, 192>(bytes);
   if (e == cudaSuccess) e = set_attr_inst<DFP, 256>(bytes);
+  if (e == cudaSuccess) e = set_attr_cl_inst<DFP, 0>(bytes);
+  if (e == cudaSuccess) e = set_attr_cl_inst<DFP, 256>(bytes);
   return e;
 }
 

@@ -29,4 +29,17 @@ cudaError_t set_attr_inst<SPH_SHELL_DF, SPH_SHELL_LEN>(int bytes) {
   return shellk::set_attr_impl<InstPolicy, SPH_SHELL_LEN>(bytes);
 }
 
+#if SPH_SHELL_LEN == 0 || SPH_SHELL_LEN == 256
+template <>
+cudaError_t launch_shell_cl_inst<SPH_SHELL_DF, SPH_SHELL_LEN>(const ShellArgs2& a, int threads, size_t smem,
+                                                            const LaunchIO& io, cudaStream_t s) {
+  return shellk::launch_cl_impl<InstPolicy, SPH_SHELL_LEN>(a, threads, smem, io, s);
+}
+
+template <>
+cudaError_t set_attr_cl_inst<SPH_SHELL_DF, SPH_SHELL_LEN>(int bytes) {
+  return shellk::set_attr_cl_impl<InstPolicy, SPH_SHELL_LEN>(bytes);
+}
+#endif
+
 }  // namespace sph

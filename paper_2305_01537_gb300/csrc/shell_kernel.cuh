@@ -312,18 +312,20 @@ struct ThetaAcc {
   }
   __device__ __forceinline__ C lin_ld(int b, int n) const { return P::ld16(lin_at(b, n)); }
   __device__ __forceinline__ void lin_st(int b, int n, C v) const { P::st16(lin_at(b, n), v); }
-  // sizes known at compile time for the fixed lengths (2 Ntheta = Nphi = LEN)
-  template <int LEN>
+  // sizes known at compile time for the fixed lengths (2 Ntheta = Nphi = LEN); SPLIT: the CTA
+  // holds half of the meridians (a cluster pair shares the shell), i.e. a shell of Nphi/2 columns
+  template <int LEN, bool SPLIT = false>
   __device__ __forceinline__ void fix() {
     if constexpr (LEN > 0) {
+      constexpr int W = SPLIT ? LEN / 2 : LEN;  // columns held
       Nth = LEN / 2;
       Nth8 = (LEN / 2) & ~7;
-      ld = LEN + 2;
-      h = LEN / 2;
+      ld = W + 2;
+      h = W / 2;
       M = LEN;
       M8 = LEN & ~7;
-      nseq = (LEN / 2 + 1) / 2;
-      lone_last = hodd = ((LEN / 2) & 1) != 0;
+      nseq = (W / 2 + 1) / 2;
+      lone_last = hodd = ((W / 2) & 1) != 0;
     }
   }
 };
@@ -384,6 +386,75 @@ struct PhiAcc {
       N8 = LEN & ~7;
       hN = LEN / 2;
       hN8 = (LEN / 2) & ~7;
+      nh = LEN / 2 + 1;
+    }
+  }
+};
+
+// Phi pass of a CTA that shares its shell with a cluster peer. The CTA of rank r owns the ring
+// pairs (j, Ntheta-1-j) with j in [r Ntheta/4, (r+1) Ntheta/4). Its buffer A holds every row for
+// the meridian blocks {r, r+2} (blocks of Nphi/4 columns), buffer B holds its own rows for the
+// peer's blocks {1-r, 3-r}; inside each, a block pair sits at local columns [0, Nphi/2).
+template <class P>
+struct PhiSplitAcc {
+  using C = typename P::C;
+  using T = typename P::T;
+  using Seq = typename PhiAcc<P>::Seq;
+  uint32_t A, Bm, lin;
+  const int2* pairs;
+  const void* gtab;
+  size_t gbase;
+  int ld, N, N8, QB, QB8, Nth, r, hN, nh, b0;
+
+  __device__ __forceinline__ int brow(int j) const {
+    const int q = Nth / 4;
+    return j < Nth / 2 ? j - q * r : q + (j - (Nth - (r + 1) * q));
+  }
+  __device__ __forceinline__ uint32_t el(int j, int c) const {
+    const int blk = c / QB;
+    const int lc = (c - blk * QB) + (blk >= 2 ? QB : 0);
+    const bool mine = blk == r || blk == 2 + r;
+    return mine ? A + (uint32_t)(j * ld + lc) * 8u : Bm + (uint32_t)(brow(j) * ld + lc) * 8u;
+  }
+  __device__ __forceinline__ Seq seq(int b) const {
+    const int2 p = pairs[b];
+    return Seq{p.x & 0x3fffffff, p.y, ((p.x >> 30) & 1) != 0};
+  }
+  // slots: segments of Nphi/4 complex in A row j1, B row j1, A row j2, B row j2
+  __device__ __forceinline__ uint32_t slot(const Seq& s, int n) const {
+    const int seg = n / QB, u = n - seg * QB;
+    const int j = seg < 2 ? s.j1 : s.j2;
+    const int col = 2 * swz(u, QB8);
+    return (seg & 1) ? Bm + (uint32_t)(brow(j) * ld + col) * 8u : A + (uint32_t)(j * ld + col) * 8u;
+  }
+  __device__ __forceinline__ C slot_ld(const Seq& s, int n) const { return P::ld16(slot(s, n)); }
+  __device__ __forceinline__ void slot_st(const Seq& s, int n, C v) const { P::st16(slot(s, n), v); }
+  __device__ __forceinline__ C gather(const Seq& s, int k) const {
+    return C{P::ld8(el(s.j1, k)), P::ld8(el(s.j2, k))};
+  }
+  __device__ __forceinline__ void scatter(const Seq& s, int k, C v) const {
+    P::st8(el(s.j1, k), v.re);
+    P::st8(el(s.j2, k), v.im);
+  }
+  __device__ __forceinline__ T ring_mult(int j, int m) const {
+    return P::from_tab(gtab, gbase + (size_t)j * nh + (m <= hN ? m : N - m));
+  }
+  __device__ __forceinline__ T mult(const Seq& s, int m) const { return ring_mult(s.j1, m); }
+  __device__ __forceinline__ uint32_t lin_at(int b, int n) const {
+    return lin + 16u * (uint32_t)((b - b0) * N + swz(n, N8));
+  }
+  __device__ __forceinline__ C lin_ld(int b, int n) const { return P::ld16(lin_at(b, n)); }
+  __device__ __forceinline__ void lin_st(int b, int n, C v) const { P::st16(lin_at(b, n), v); }
+  template <int LEN>
+  __device__ __forceinline__ void fix() {
+    if constexpr (LEN > 0) {
+      ld = LEN / 2 + 2;
+      N = LEN;
+      N8 = LEN & ~7;
+      QB = LEN / 4;
+      QB8 = (LEN / 4) & ~7;
+      Nth = LEN / 2;
+      hN = LEN / 2;
       nh = LEN / 2 + 1;
     }
   }
@@ -502,6 +573,46 @@ __device__ void general_multiply(const PhiAcc<P>& A, int B, bool in_slots) {
 
 template <class P>
 __device__ __forceinline__ void maybe_general_multiply(const ThetaAcc<P>&, int, bool) {}
+
+// Split-shell pairs whose multipliers differ: same exact split as general_multiply.
+template <class P>
+__device__ void maybe_general_multiply(const PhiSplitAcc<P>& A, int B, bool in_slots) {
+  using C = typename P::C;
+  const int nh = A.N / 2 + 1;
+  for (int base = 0; base < B * nh; base += blockDim.x) {
+    const int w = base + threadIdx.x;
+    bool act = false;
+    int m = 0, mn = 0, bb = 0;
+    typename PhiAcc<P>::Seq sq{0, -1, false};
+    C wm, wn;
+    if (w < B * nh) {
+      bb = A.b0 + w / nh;
+      m = w - (w / nh) * nh;
+      sq = A.seq(bb);
+      act = sq.general;
+      if (act) {
+        mn = (A.N - m) % A.N;
+        const C zm = in_slots ? A.slot_ld(sq, m) : A.lin_ld(bb, m);
+        const C zn = in_slots ? A.slot_ld(sq, mn) : A.lin_ld(bb, mn);
+        const auto f1 = A.ring_mult(sq.j1, m), f2 = A.ring_mult(sq.j2, m);
+        const auto ca = P::half(P::add(f1, f2)), cd = P::half(P::sub(f1, f2));
+        wm = C{P::add(P::mul(zm.re, ca), P::mul(zn.re, cd)), P::sub(P::mul(zm.im, ca), P::mul(zn.im, cd))};
+        wn = C{P::add(P::mul(zn.re, ca), P::mul(zm.re, cd)), P::sub(P::mul(zn.im, ca), P::mul(zm.im, cd))};
+      }
+    }
+    __syncthreads();
+    if (act) {
+      if (in_slots) {
+        A.slot_st(sq, m, wm);
+        if (mn != m) A.slot_st(sq, mn, wn);
+      } else {
+        A.lin_st(bb, m, wm);
+        if (mn != m) A.lin_st(bb, mn, wn);
+      }
+    }
+    __syncthreads();
+  }
+}
 template <class P>
 __device__ __forceinline__ void maybe_general_multiply(const PhiAcc<P>& A, int B, bool in_slots) {
   general_multiply<P>(A, B, in_slots);
@@ -565,9 +676,9 @@ __device__ __forceinline__ void run_pass(const Acc& A, int N, int B, const Facto
 }
 
 // Each pass is its own function: its registers are allocated apart from the load/store code.
-template <class P, int LEN>
+template <class P, int LEN, bool SPLIT = false>
 __device__ __noinline__ void theta_pass_fn(ThetaAcc<P> TA, Factors f, uint32_t tw, Consts<P> K, int batch) {
-  TA.template fix<LEN>();
+  TA.template fix<LEN, SPLIT>();
   for (int b0 = 0; b0 < TA.nseq; b0 += batch) {
     TA.b0 = b0;
     run_pass<P, ThetaAcc<P>, LEN>(TA, TA.M, min(batch, TA.nseq - b0), f, tw, K, false);
@@ -581,6 +692,16 @@ __device__ __noinline__ void phi_pass_fn(PhiAcc<P> PA, int npairs, bool has_gene
   for (int b0 = 0; b0 < npairs; b0 += batch) {
     PA.b0 = b0;
     run_pass<P, PhiAcc<P>, LEN>(PA, PA.N, min(batch, npairs - b0), f, tw, K, has_general);
+  }
+}
+
+template <class P, int LEN>
+__device__ __noinline__ void phi_split_pass_fn(PhiSplitAcc<P> PA, int npairs, bool has_general, Factors f,
+                                               uint32_t tw, Consts<P> K, int batch) {
+  PA.template fix<LEN>();
+  for (int b0 = 0; b0 < npairs; b0 += batch) {
+    PA.b0 = b0;
+    run_pass<P, PhiSplitAcc<P>, LEN>(PA, PA.N, min(batch, npairs - b0), f, tw, K, has_general);
   }
 }
 
@@ -826,6 +947,283 @@ __global__ void __launch_bounds__(512) shell_kernel(ShellArgs2 A, LaunchIO io) {
   }
   __syncthreads();
   filter_shell<P, LEN>(A, io, L, L.buf, sidx, K);
+}
+
+
+// ------------------------------------------------------------------ cluster-pair kernel (large shells)
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t peer_addr(uint32_t a, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ uint4 ld_peer16(uint32_t a) {
+  uint4 v;
+  asm volatile("ld.shared::cluster.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void st_local16(uint32_t a, uint4 v) {
+  asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w) : "memory");
+}
+
+template <class P>
+struct LayoutCl {
+  uint32_t A, B, lin, ov, tw_th, tw_ph, g_th;
+  int2* pairs;
+  int* misc;
+};
+
+// Shared memory of one CTA of a pair: A (all rows, half the columns), B (a quarter of the rows, the
+// other half of the columns), FFT scratch, tables.
+__host__ __device__ __forceinline__ size_t cl_ld(const ShellArgs2& A) { return (size_t)A.Nph / 2 + 2; }
+
+template <class P>
+__device__ LayoutCl<P> carve_cl(const ShellArgs2& A, unsigned char* base) {
+  LayoutCl<P> L;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    unsigned char* p = base + off;
+    off = (off + bytes + 15) / 16 * 16;
+    return p;
+  };
+  L.A = saddr(take(8 * (size_t)A.Nth * cl_ld(A)));
+  L.B = saddr(take(8 * (size_t)(A.Nth / 2) * cl_ld(A)));
+  L.lin = saddr(take(scratch_bytes(A)));
+  L.ov = saddr(take(16 * (size_t)max(2 * A.Nth, A.Nph)));
+  L.tw_th = saddr(take(16 * 2 * (size_t)A.Nth));
+  L.tw_ph = saddr(take(16 * (size_t)A.Nph));
+  L.g_th = saddr(take(8 * (size_t)(A.Nth + 1)));
+  L.pairs = reinterpret_cast<int2*>(take(sizeof(int2) * (size_t)(A.Nth / 2 + 1)));
+  L.misc = reinterpret_cast<int*>(take(sizeof(int) * 4));
+  return L;
+}
+
+template <class P>
+size_t shell_smem_cl(const ShellArgs2& a) {
+  auto up = [](size_t x) { return (x + 15) / 16 * 16; };
+  size_t s = up(8 * (size_t)a.Nth * cl_ld(a));
+  s += up(8 * (size_t)(a.Nth / 2) * cl_ld(a));
+  s += up(scratch_bytes(a));
+  s += up(16 * (size_t)std::max(2 * a.Nth, a.Nph));
+  s += up(16 * 2 * (size_t)a.Nth);
+  s += up(16 * (size_t)a.Nph);
+  s += up(8 * (size_t)(a.Nth + 1));
+  s += up(sizeof(int2) * (size_t)(a.Nth / 2 + 1));
+  s += up(sizeof(int) * 4);
+  return s;
+}
+
+// Global column c of a shell row -> (is it in this rank's blocks {r, r+2}, local column).
+__device__ __forceinline__ bool cl_mine(int c, int QB, int r, int* lc) {
+  const int blk = c / QB;
+  *lc = (c - blk * QB) + (blk >= 2 ? QB : 0);
+  return blk == r || blk == 2 + r;
+}
+__device__ __forceinline__ int cl_brow(int j, int Nth, int r) {
+  const int q = Nth / 4;
+  return j < Nth / 2 ? j - q * r : q + (j - (Nth - (r + 1) * q));
+}
+__device__ __forceinline__ bool cl_own_row(int j, int Nth, int r) {
+  const int q = Nth / 4;
+  return (j >= q * r && j < q * (r + 1)) || (j >= Nth - (r + 1) * q && j < Nth - r * q);
+}
+
+// One shell per cluster pair; Ntheta % 4 == 0, Nphi % 8 == 0.
+template <class P, int LEN>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512) shell_kernel_cl(ShellArgs2 A, LaunchIO io) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr bool dfp = std::is_same<P, DF>::value;
+  const LayoutCl<P> L = carve_cl<P>(A, smem_raw);
+  const int r = (int)cluster_rank();
+  const int sidx = blockIdx.x / 2;
+  int v, i;
+  const size_t off = shell_offset(A, sidx, &v, &i);
+  const VarInfo vi = A.var[v];
+  const int Nth = A.Nth, Nph = A.Nph, QB = Nph / 4, ldc = (int)cl_ld(A);
+  const bool fwd = io.transpose == 0;
+
+  for (int n = threadIdx.x; n < 2 * Nth; n += blockDim.x)
+    P::st16(L.tw_th + 16u * n, static_cast<const typename P::C*>(A.tw_th)[n]);
+  for (int n = threadIdx.x; n < Nph; n += blockDim.x)
+    P::st16(L.tw_ph + 16u * n, static_cast<const typename P::C*>(A.tw_ph)[n]);
+  Consts<P> K;
+  K.c8 = P::from_tab(A.consts, 0);
+  K.s3 = P::from_tab(A.consts, 1);
+
+  // load: forward order takes every row of blocks {r, r+2} into A; the transpose order takes this
+  // rank's rows, blocks {r, r+2} into A and the others into B. Raw FP64 first.
+  const double* srcd = static_cast<const double*>(io.in) + off;
+  const float* srcf = static_cast<const float*>(io.in) + off;
+  const int rows = fwd ? Nth : Nth / 2;
+  unsigned emax = 0;
+  for (int e = threadIdx.x; e < rows * Nph; e += blockDim.x) {
+    const int jr = e / Nph, c = e - jr * Nph;
+    int j = jr;
+    if (!fwd) j = jr < Nth / 4 ? r * (Nth / 4) + jr : Nth - (r + 1) * (Nth / 4) + (jr - Nth / 4);
+    int lc;
+    const bool mine = cl_mine(c, QB, r, &lc);
+    if (fwd && !mine) continue;
+    double x = io.is_f32 ? (double)__ldcs(srcf + (size_t)j * Nph + c) : __ldcs(srcd + (size_t)j * Nph + c);
+    if (io.map_in == kMapTanh) x = tanh(x);
+    if (dfp) emax = max(emax, (unsigned)df_exp_field(x));
+    const uint32_t a = mine ? L.A + (uint32_t)(j * ldc + lc) * 8u : L.B + (uint32_t)(cl_brow(j, Nth, r) * ldc + lc) * 8u;
+    F64::st8(a, x);
+  }
+  int E = 0;
+  if (dfp) {
+    emax = __reduce_max_sync(0xffffffffu, emax);
+    if (threadIdx.x == 0) L.misc[2] = 0;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) atomicMax(&L.misc[2], (int)emax);
+    cluster_sync();  // both halves' maxima are in place
+    const uint32_t mine = saddr(&L.misc[2]);
+    unsigned other;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(other) : "r"(peer_addr(mine, 1 - r)));
+    E = max(L.misc[2], (int)other) - 1023;
+    for (int e = threadIdx.x; e < rows * Nph; e += blockDim.x) {
+      const int jr = e / Nph, c = e - jr * Nph;
+      int j = jr;
+      if (!fwd) j = jr < Nth / 4 ? r * (Nth / 4) + jr : Nth - (r + 1) * (Nth / 4) + (jr - Nth / 4);
+      int lc;
+      const bool mine_c = cl_mine(c, QB, r, &lc);
+      if (fwd && !mine_c) continue;
+      const uint32_t a = mine_c ? L.A + (uint32_t)(j * ldc + lc) * 8u : L.B + (uint32_t)(cl_brow(j, Nth, r) * ldc + lc) * 8u;
+      P::st8(a, to_real<P>(F64::ld8(a), E));
+    }
+  }
+
+  // per-shell tables
+  const double lmax = A.lmax[vi.cls * A.Nr + i];
+  const bool theta_on = vi.kind == SPH_FILTER_GAUSS || lmax < (double)Nth;
+  const size_t gth_base = ((size_t)vi.cls * A.Nr + i) * (Nth + 1);
+  for (int n = threadIdx.x; n <= Nth; n += blockDim.x) P::st8(L.g_th + 8u * n, P::from_tab(A.g_th, gth_base + n));
+  const uint8_t* ring_info = A.ring_info + ((size_t)vi.cls * A.Nr + i) * Nth;
+  if (threadIdx.x == 0) {
+    int np = 0, gen = 0;
+    const int q = Nth / 4;
+    for (int j = q * r; j < q * (r + 1); ++j) {
+      const int jj = Nth - 1 - j;
+      const uint8_t a = ring_info[j], b = ring_info[jj];
+      if (!((a | b) & 1)) continue;
+      const int g = (a >> 1) & 1;
+      gen |= g;
+      L.pairs[np++] = make_int2(j | (g << 30), jj);
+    }
+    L.misc[0] = np;
+    L.misc[1] = gen;
+  }
+  __syncthreads();
+  const int npairs = L.misc[0];
+  const bool has_general = L.misc[1] != 0;
+
+  ThetaAcc<P> TA;
+  TA.S = L.A;
+  TA.ov = L.ov;
+  TA.lin = L.lin;
+  TA.g = L.g_th;
+  TA.ld = ldc;
+  TA.Nth = Nth;
+  TA.Nth8 = Nth & ~7;
+  TA.h = Nph / 4;
+  TA.M = 2 * Nth;
+  TA.M8 = (2 * Nth) & ~7;
+  TA.nseq = (Nph / 4 + 1) / 2;
+  TA.lone_last = (Nph / 4) & 1;
+  TA.odd = vi.parity != 0;
+  TA.hodd = (Nph / 4) & 1;
+  TA.b0 = 0;
+
+  PhiSplitAcc<P> PA;
+  PA.A = L.A;
+  PA.Bm = L.B;
+  PA.lin = L.lin;
+  PA.pairs = L.pairs;
+  PA.gtab = A.g_ph;
+  PA.gbase = ((size_t)vi.cls * A.Nr + i) * (size_t)Nth * (Nph / 2 + 1);
+  PA.ld = ldc;
+  PA.N = Nph;
+  PA.N8 = Nph & ~7;
+  PA.QB = QB;
+  PA.QB8 = QB & ~7;
+  PA.Nth = Nth;
+  PA.r = r;
+  PA.hN = Nph / 2;
+  PA.nh = Nph / 2 + 1;
+  PA.b0 = 0;
+
+  // exchange through the peer's shared memory: forward, this rank's rows of the peer's blocks (the
+  // peer's A -> our B); transpose, the peer's rows of our blocks (the peer's B -> our A)
+  auto exchange = [&]() {
+    cluster_sync();  // the peer's first pass is complete
+    const int half = Nph / 2;  // local columns of a row
+    const int q = Nth / 4;
+    for (int e = threadIdx.x; e < (Nth / 2) * (half / 2); e += blockDim.x) {
+      const int jr = e / (half / 2), c2 = 2 * (e - jr * (half / 2));
+      if (fwd) {
+        const int j = jr < q ? r * q + jr : Nth - (r + 1) * q + (jr - q);
+        const uint4 val = ld_peer16(peer_addr(L.A + (uint32_t)(j * ldc + c2) * 8u, 1 - r));
+        st_local16(L.B + (uint32_t)(cl_brow(j, Nth, r) * ldc + c2) * 8u, val);
+      } else {
+        const int ro = 1 - r;
+        const int j = jr < q ? ro * q + jr : Nth - (ro + 1) * q + (jr - q);
+        const uint4 val = ld_peer16(peer_addr(L.B + (uint32_t)(cl_brow(j, Nth, ro) * ldc + c2) * 8u, ro));
+        st_local16(L.A + (uint32_t)(j * ldc + c2) * 8u, val);
+      }
+    }
+    cluster_sync();  // both reads are done before either side writes the rows the peer read
+  };
+
+  if (fwd) {
+    if (theta_on) theta_pass_fn<P, LEN, true>(TA, A.f_th, L.tw_th, K, A.batch_th);
+    exchange();
+    if (npairs) phi_split_pass_fn<P, LEN>(PA, npairs, has_general, A.f_ph, L.tw_ph, K, A.batch_ph);
+  } else {
+    if (npairs) phi_split_pass_fn<P, LEN>(PA, npairs, has_general, A.f_ph, L.tw_ph, K, A.batch_ph);
+    exchange();
+    if (theta_on) theta_pass_fn<P, LEN, true>(TA, A.f_th, L.tw_th, K, A.batch_th);
+  }
+  __syncthreads();
+
+  // store: forward, this rank's rows (A and B); transpose, every row of blocks {r, r+2} (A)
+  const int store_rows = fwd ? Nth / 2 : Nth;
+  for (int e = threadIdx.x; e < store_rows * Nph; e += blockDim.x) {
+    const int jr = e / Nph, c = e - jr * Nph;
+    int j = jr;
+    if (fwd) j = jr < Nth / 4 ? r * (Nth / 4) + jr : Nth - (r + 1) * (Nth / 4) + (jr - Nth / 4);
+    int lc;
+    const bool mine = cl_mine(c, QB, r, &lc);
+    if (!fwd && !mine) continue;
+    const uint32_t a = mine ? L.A + (uint32_t)(j * ldc + lc) * 8u : L.B + (uint32_t)(cl_brow(j, Nth, r) * ldc + lc) * 8u;
+    double y = from_real<P>(P::ld8(a), E);
+    const size_t o = off + (size_t)j * Nph + c;
+    if (io.map_out == kOutTanhGrad) {
+      const double z = io.is_f32 ? (double)static_cast<const float*>(io.aux)[o] : static_cast<const double*>(io.aux)[o];
+      const double t = tanh(z);
+      y *= (1.0 - t * t);
+    }
+    if (io.is_f32) __stcs(static_cast<float*>(io.out) + o, (float)y);
+    else __stcs(static_cast<double*>(io.out) + o, y);
+  }
+}
+
+template <class P, int LEN>
+cudaError_t launch_cl_impl(const ShellArgs2& a, int threads, size_t smem, const LaunchIO& io, cudaStream_t s) {
+  const dim3 grid((unsigned)(2 * a.nvars * a.Nr));
+  shell_kernel_cl<P, LEN><<<grid, threads, smem, s>>>(a, io);
+  return cudaGetLastError();
+}
+
+template <class P, int LEN>
+cudaError_t set_attr_cl_impl(int bytes) {
+  return cudaFuncSetAttribute(shell_kernel_cl<P, LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 template <class P>
