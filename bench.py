@@ -35,6 +35,11 @@ from paper_2305_01537_gb300 import workloads as W  # noqa: E402
 
 HBM_FALLBACK_GBS = 6800.0
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+# Compensated FP32 pairs: FP32 instruction rate (152 SMs x 128 lanes x 2.07 GHz) divided by the FP32
+# instructions one FP64-equivalent flop of the radix-8 butterfly costs (866 / 98 = 8.8)
+F32_INSTR_PER_S = 152 * 128 * 2.07e9
+DF_INSTR_PER_FLOP = 866.0 / 98.0
+DF_PEAK_TFLOPS = F32_INSTR_PER_S / DF_INSTR_PER_FLOP / 1e12
 
 
 def measured_peaks():
@@ -128,12 +133,12 @@ def dist_setup():
     return world, rank, local
 
 
-def cpu_baseline(grid, x, seconds_target=10.0):
+def cpu_baseline(grid, x, seconds_target=10.0, stride0=16):
     """The oracle as it stands, on all host cores, over a stratified sample of shells (every s-th
     radial shell of every field), grown until it has run for about `seconds_target` seconds."""
     import oracle
     threads = oracle.max_threads()
-    stride = 16
+    stride = stride0
     total_pts, total_t = 0, 0.0
     sample_shells = 0
     while True:
@@ -186,19 +191,110 @@ def run_reference(args):
     return 0
 
 
+def _timed(fn, steps, warmup, stream):
+    """Run fn warmup times, then time `steps` calls with CUDA events on `stream` (ms total)."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_batch(args):
+    """Six uneven grids (28 fields each) filtered three times per step (one filter per RK3 substep),
+    replayed as one CUDA graph per step; every plan autotuned first."""
+    import torch
+    from paper_2305_01537_gb300 import Batch, Plan, SPH_PREC_F64, SPH_PREC_F32X2
+    prec = SPH_PREC_F32X2 if args.precision == "f32x2" else SPH_PREC_F64
+    wl = W.batched_six_grids()
+    xs, outs, plans = [], [], []
+    for n, g in enumerate(wl.grids):
+        xs.append(torch.from_numpy(wl.state(n)).cuda())
+        outs.append(torch.empty_like(xs[-1]))
+        plans.append(Plan.from_grid(g, precision=prec))
+        plans[-1].autotune(xs[-1], outs[-1])
+    b = Batch(plans)
+    stream = torch.cuda.current_stream()
+    b.capture(xs, outs, 3, stream)
+    with ClockSampler(0) as clk:
+        t0 = time.time()
+        ms = _timed(lambda: b.launch(stream), args.steps, args.warmup, stream)
+        clk.mark(t0, time.time())
+    points = wl.points * 3
+    value = points * args.steps / (ms * 1e-3) / 1e9
+    peaks, src = measured_peaks()
+    gbs = 16.0 * points * args.steps / (ms * 1e-3) / 1e9
+    print(json.dumps({
+        "metric": "filtered Gpoints/s (theta+phi double FFT filter, FP64 I/O)", "value": value, "unit": "Gpoints/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": wl.name, "grids": [[g.Nr, g.Ntheta, g.Nphi, g.nvars] for g in wl.grids],
+                   "applications_per_step": 3, "precision": args.precision,
+                   "launch": "one CUDA graph per step (per-grid kernels on parallel branches)"},
+        "hbm": {"achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"], "frac": gbs / peaks["hbm_gbs"], "peak_source": src},
+        "gpu_launches": args.steps * 3 * sum(p.launches for p in plans), "clocks": clk.summary()}), flush=True)
+    return 0
+
+
+def run_chain(args):
+    """loss = sum w (F o tanh o ... o F x)^2 over 8 filters on the 8-field 128x64x128 state; one step
+    is the forward chain and its gradient (8 fused adjoint launches)."""
+    import torch
+    from paper_2305_01537_gb300 import Plan, SPH_PREC_F64, SPH_PREC_F32X2
+    from paper_2305_01537_gb300.autograd import chain_loss
+    prec = SPH_PREC_F32X2 if args.precision == "f32x2" else SPH_PREC_F64
+    wl = W.chain_8field()
+    g = wl.grids[0]
+    x = torch.from_numpy(wl.state() * 0.1).cuda()
+    w = torch.from_numpy(W.chain_weights(g)).cuda()
+    plan = Plan.from_grid(g, precision=prec)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        xd = x.detach().requires_grad_(True)
+        chain_loss(xd, plan, w, 8).backward()
+
+    with ClockSampler(0) as clk:
+        t0 = time.time()
+        ms = _timed(step, args.steps, args.warmup, stream)
+        clk.mark(t0, time.time())
+    points = g.points * 16  # 8 forward + 8 adjoint filter applications
+    value = points * args.steps / (ms * 1e-3) / 1e9
+    print(json.dumps({
+        "metric": "filtered Gpoints/s (theta+phi double FFT filter, FP64 I/O)", "value": value, "unit": "Gpoints/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": wl.name, "filters": 8, "step": "forward chain + backward", "precision": args.precision},
+        "gpu_launches": args.steps * 16 * plan.launches, "clocks": clk.summary()}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="f64", choices=["f64", "f32x2", "tc"])
+    ap.add_argument("--precision", default="f32x2", choices=["f64", "f32x2", "tc"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="state28_128x64x128",
+                    choices=["state28_128x64x128", "state28_256x128x256", "batch6_uneven", "chain8_128x64x128"])
+    ap.add_argument("--autotune", action="store_true", help="autotune the plan's launch shape before timing")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch6_uneven":
+        return run_batch(args)
+    if args.workload == "chain8_128x64x128":
+        return run_chain(args)
 
     import torch
     import torch.distributed as dist
@@ -210,12 +306,14 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     prec = {"f64": SPH_PREC_F64, "f32x2": SPH_PREC_F32X2, "tc": SPH_PREC_SPLIT_TC}[args.precision]
 
-    wl = W.full_state_128x64x128()
+    wl = W.full_state_128x64x128() if args.workload == "state28_128x64x128" else W.full_state_256x128x256()
     g = wl.grids[0]
     x_host = torch.from_numpy(wl.state()).pin_memory()
     x = x_host.cuda()
     y = torch.empty_like(x)
     plan = Plan.from_grid(g, precision=prec)
+    if args.autotune:
+        plan.autotune(x, y)
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -290,7 +388,13 @@ def main():
             roof = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
                     "peak_source": "FP64 FMA: 152 SMs x 2/clk x 2 flop x 2.07 GHz (recipe's 1.25 TFLOP/s)",
-                    "kernel": "plain_shell_kernel<double>", "flops_per_launch": flops}
+                    "kernel": "shell_kernel<F64>", "flops_per_launch": flops}
+        elif args.precision == "f32x2":
+            roof = {"bound": "alu", "achieved": tflops, "peak": DF_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": tflops / DF_PEAK_TFLOPS, "traffic": traffic,
+                    "peak_source": "FP64-equivalent rate of compensated FP32 pairs: 152 SMs x 128 FP32 lanes x "
+                                   "2.07 GHz / 8.8 FP32 instructions per FP64-equivalent flop",
+                    "kernel": "shell_kernel<DF>", "flops_per_launch": flops}
         else:
             roof = {"bound": "hbm", "achieved": hbm_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": hbm_gbs / peaks["hbm_gbs"], "traffic": traffic,
@@ -299,9 +403,11 @@ def main():
             "metric": "filtered Gpoints/s (theta+phi double FFT filter, FP64 I/O)",
             "value": value, "unit": "Gpoints/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": {"f64": "f64", "f32x2": "f32x2", "tc": "bf16x_split"}[args.precision],
+            "data": "synthetic",
             "config": {"workload": wl.name, "Nr": g.Nr, "Ntheta": g.Ntheta, "Nphi": g.Nphi, "nvars": g.nvars,
-                       "precision": args.precision, "l2": "inputs (235 MB) larger than L2; no flush",
+                       "precision": args.precision,
+                       "l2": f"inputs ({8 * points / 1e6:.0f} MB) larger than L2; no flush",
                        "parallelism": f"independent shards x{world}"},
             "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": peaks["hbm_gbs"], "frac": hbm_gbs / peaks["hbm_gbs"],
                     "peak_source": src, "bytes_per_point": 16},
@@ -312,7 +418,7 @@ def main():
             "clocks": clk.summary(),
         }
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(g, x_host.numpy())
+            line["cpu_baseline"] = cpu_baseline(g, x_host.numpy(), stride0=16 if g.Nr <= 128 else 64)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

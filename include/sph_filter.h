@@ -136,6 +136,43 @@ int sph_filter_plan_launches(sph_filter_plan plan);
 /* Static description of a status code. */
 const char* sph_filter_status_string(sph_status status);
 
+/* ---- several grids at once (uneven shapes, e.g. the levels of a multi-grid evolution) ---- */
+
+/* Opaque batch of plans, one per grid; owned by the library until destroyed. */
+typedef struct sph_filter_batch_s* sph_filter_batch;
+
+/* Group nplans plans (created on the same device) so that one call filters all their grids. The
+ * kernels of different grids run concurrently on internal streams forked from the caller's
+ * stream and joined back into it. The plans must outlive the batch. *out is NULL on failure.
+ * Errors: SPH_EINVAL (nplans < 1, NULL plan, plans on different devices), SPH_ENOMEM, SPH_ECUDA. */
+sph_status sph_filter_batch_create(sph_filter_batch* out, int nplans, const sph_filter_plan* plans);
+
+/* Release the batch (its streams, events and graph). Synchronises first. NULL is a no-op. */
+void sph_filter_batch_destroy(sph_filter_batch batch);
+
+/* out[g] = F_g in[g] for every grid g (Sec. II.C double filter): in and out are host arrays of
+ * nplans device pointers to FP64 states of the plans' shapes. Asynchronous on `stream`. Errors as
+ * sph_filter_apply. */
+sph_status sph_filter_batch_apply(sph_filter_batch batch, const double* const* in, double* const* out,
+                                  sph_stream_t stream);
+
+/* Record napply consecutive applications into a CUDA graph kept by the batch: the first filters
+ * in -> out, the others filter out in place (one filter application per Runge-Kutta substep).
+ * The pointers are baked into the graph; capture again to change them. Must not be called while
+ * `stream` is itself being captured. Errors: SPH_EINVAL (napply < 1), SPH_ECUDA. */
+sph_status sph_filter_batch_capture(sph_filter_batch batch, const double* const* in, double* const* out,
+                                    int napply, sph_stream_t stream);
+
+/* Replay the captured graph on `stream` (one graph launch). SPH_EINVAL if nothing was captured. */
+sph_status sph_filter_batch_launch(sph_filter_batch batch, sph_stream_t stream);
+
+/* Autotuner: time every valid choice of threads per CTA and FFT batch size for this plan on the
+ * caller's in/out device buffers (FP64, the plan's shape; out is overwritten) and keep the
+ * fastest. Synchronous. Must not run concurrently with other calls on the same plan. *best_ms
+ * (may be NULL) receives the fastest time of one application. */
+sph_status sph_filter_plan_autotune(sph_filter_plan plan, const double* in, double* out, sph_stream_t stream,
+                                    double* best_ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,7 +26,9 @@ EXPORTED = (
     "sph_filter_apply_tanh", "sph_filter_apply_adjoint_tanh", "sph_filter_apply_f32",
     "sph_filter_apply_adjoint_f32", "sph_filter_apply_tanh_f32", "sph_filter_apply_adjoint_tanh_f32",
     "sph_filter_apply_host", "sph_filter_plan_sync_status", "sph_filter_plan_points",
-    "sph_filter_plan_launches", "sph_filter_status_string",
+    "sph_filter_plan_launches", "sph_filter_status_string", "sph_filter_batch_create",
+    "sph_filter_batch_destroy", "sph_filter_batch_apply", "sph_filter_batch_capture", "sph_filter_batch_launch",
+    "sph_filter_plan_autotune",
 )
 
 
@@ -69,6 +71,12 @@ def load() -> ctypes.CDLL:
         "sph_filter_plan_points": ([P], LL),
         "sph_filter_plan_launches": ([P], I),
         "sph_filter_status_string": ([I], ctypes.c_char_p),
+        "sph_filter_batch_create": ([ctypes.POINTER(P), I, P], I),
+        "sph_filter_batch_destroy": ([P], None),
+        "sph_filter_batch_apply": ([P, P, P, P], I),
+        "sph_filter_batch_capture": ([P, P, P, I, P], I),
+        "sph_filter_batch_launch": ([P, P], I),
+        "sph_filter_plan_autotune": ([P, P, P, P, ctypes.POINTER(ctypes.c_double)], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -198,6 +206,61 @@ class Plan:
 
     def sync_status(self) -> int:
         return int(load().sph_filter_plan_sync_status(self._h))
+
+    def autotune(self, x, out, stream=None) -> float:
+        """sph_filter_plan_autotune on the given FP64 device buffers; returns the best time (ms)."""
+        import torch
+        self._io(x, out, torch.float64)
+        best = ctypes.c_double(0.0)
+        _check(load().sph_filter_plan_autotune(self._h, x.data_ptr(), out.data_ptr(), _stream_handle(stream),
+                                               ctypes.byref(best)), "sph_filter_plan_autotune")
+        return best.value
+
+
+class Batch:
+    """sph_filter_batch: several plans (grids) filtered by one call, or replayed as a CUDA graph."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p._h.value for p in self.plans])
+        h = ctypes.c_void_p()
+        _check(load().sph_filter_batch_create(ctypes.byref(h), len(self.plans), arr), "sph_filter_batch_create")
+        self._h = h
+
+    def _ptrs(self, xs, outs):
+        import torch
+        if len(xs) != len(self.plans) or len(outs) != len(self.plans):
+            raise ValueError("one input and one output per plan")
+        for p, x, o in zip(self.plans, xs, outs):
+            p._io(x, o, torch.float64)
+        ins = (ctypes.c_void_p * len(xs))(*[x.data_ptr() for x in xs])
+        ous = (ctypes.c_void_p * len(outs))(*[o.data_ptr() for o in outs])
+        return ins, ous
+
+    def apply(self, xs, outs, stream=None):
+        ins, ous = self._ptrs(xs, outs)
+        _check(load().sph_filter_batch_apply(self._h, ins, ous, _stream_handle(stream)), "sph_filter_batch_apply")
+        return outs
+
+    def capture(self, xs, outs, napply: int, stream=None):
+        ins, ous = self._ptrs(xs, outs)
+        self._keep = (xs, outs)
+        _check(load().sph_filter_batch_capture(self._h, ins, ous, int(napply), _stream_handle(stream)),
+               "sph_filter_batch_capture")
+
+    def launch(self, stream=None):
+        _check(load().sph_filter_batch_launch(self._h, _stream_handle(stream)), "sph_filter_batch_launch")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sph_filter_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _is_f32(t) -> bool:

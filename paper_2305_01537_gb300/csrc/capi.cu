@@ -274,8 +274,10 @@ sph_status check_io(const sph_filter_plan_s* p, const void* in, const void* out,
   return SPH_OK;
 }
 
-sph_status launch(sph_filter_plan p, const void* in, const void* aux, void* out, int map_in, int map_out,
-                  int transpose, int is_f32, sph_stream_t stream) {
+}  // namespace
+
+sph_status launch_plan(sph_filter_plan_s* p, const void* in, const void* aux, void* out, int map_in, int map_out,
+                       int transpose, int is_f32, cudaStream_t stream) {
   sph_status st = check_io(p, in, out, is_f32 ? sizeof(float) : sizeof(double));
   if (st != SPH_OK) return st;
   if (map_out == kOutTanhGrad) {
@@ -295,6 +297,11 @@ sph_status launch(sph_filter_plan p, const void* in, const void* aux, void* out,
   return e == cudaSuccess ? SPH_OK : SPH_ECUDA;
 }
 
+namespace {
+sph_status launch(sph_filter_plan p, const void* in, const void* aux, void* out, int map_in, int map_out,
+                  int transpose, int is_f32, sph_stream_t stream) {
+  return launch_plan(p, in, aux, out, map_in, map_out, transpose, is_f32, (cudaStream_t)stream);
+}
 }  // namespace
 }  // namespace sph
 

@@ -166,6 +166,9 @@ struct sph_filter_plan_s {
 };
 
 namespace sph {
+// Enqueue one filter application of a plan (validates pointers; see sph_filter_apply).
+sph_status launch_plan(sph_filter_plan_s* p, const void* in, const void* aux, void* out, int map_in, int map_out,
+                       int transpose, int is_f32, cudaStream_t stream);
 // Shared-memory bytes the plain shell kernel needs for this plan's shape (0 if it cannot fit).
 size_t plain_smem_bytes(const ShellArgs& a, int* chunk_th, int* chunk_ph);
 // Enqueue the plain FP64 shell kernel.
