@@ -58,16 +58,20 @@ struct Shape {
 // Launch shapes of the staged kernel that fit the device: threads per CTA and sequences per FFT batch.
 std::vector<Shape> candidates(sph_filter_plan_s* p) {
   std::vector<Shape> out;
+  if (p->cluster) {  // the cluster kernel's batches are set by the free buffer memory
+    out.push_back(Shape{p->threads2, p->args2.batch_th, p->args2.batch_ph, p->smem2});
+    return out;
+  }
   const size_t optin = (size_t)sph::max_smem_optin(p->device);
   sph::ShellArgs2 a = p->args2;
-  const int nseq = p->cluster ? (p->Nph / 4 + 1) / 2 : (p->Nph / 2 + 1) / 2;
-  const int npair = p->cluster ? p->Nth / 4 : (p->Nth + 1) / 2;
+  const int nseq = (p->Nph / 2 + 1) / 2;
+  const int npair = (p->Nth + 1) / 2;
   const int thr[2] = {256, 512};
-  for (int ti = p->cluster ? 1 : 0; ti < 2; ++ti) {
+  for (int ti = 0; ti < 2; ++ti) {
     for (int div = 1; div <= 64; div *= 2) {
       a.batch_th = std::max(1, (nseq + div - 1) / div);
       a.batch_ph = std::max(1, (npair + div - 1) / div);
-      const size_t smem = p->cluster ? sph::shell_smem_cl_bytes(a, p->precision) : sph::shell_smem_bytes(a, p->precision);
+      const size_t smem = sph::shell_smem_bytes(a, p->precision);
       if (smem <= optin) {
         bool dup = false;
         for (const Shape& s : out) dup |= s.threads == thr[ti] && s.batch_th == a.batch_th && s.batch_ph == a.batch_ph;

@@ -151,19 +151,19 @@ sph_status setup_v2(sph_filter_plan_s* p) {
     }
   }
   if (!threads && p->Nth % 4 == 0 && p->Nph % 8 == 0) {
-    // a cluster pair per shell: each CTA holds half of the columns (theta) or a quarter of the rings
-    // (phi) and the halves are exchanged through distributed shared memory
+    // a cluster pair per shell: each CTA holds half of the columns (theta) or half of the rings
+    // (phi); the halves are exchanged through distributed shared memory. The FFT scratch reuses
+    // buffer memory that is free during each pass (see the kernel), which sets the batch sizes.
+    const size_t ldc = (size_t)p->Nph / 2 + 2;
     const int nseq_cl = (p->Nph / 4 + 1) / 2, npair_cl = p->Nth / 4;
-    for (int div = 1; div <= 64; div *= 2) {
-      a.batch_th = std::max(1, (nseq_cl + div - 1) / div);
-      a.batch_ph = std::max(1, (npair_cl + div - 1) / div);
-      smem = shell_smem_cl_bytes(a, p->precision);
-      if (smem <= optin) {
-        threads = 512;
-        p->cluster = true;
-        break;
-      }
-      if (a.batch_th == 1 && a.batch_ph == 1) break;
+    const int cap_th = (int)((8 * (size_t)(p->Nth / 2) * ldc) / (16 * 2 * (size_t)p->Nth));
+    const int cap_ph = (int)((8 * (size_t)(p->Nth / 4) * ldc) / (16 * (size_t)p->Nph));
+    a.batch_th = std::min(nseq_cl, cap_th);
+    a.batch_ph = std::min(npair_cl, 2 * cap_ph);
+    smem = shell_smem_cl_bytes(a, p->precision);
+    if (a.batch_th >= 1 && cap_ph >= 1 && smem <= optin) {
+      threads = 512;
+      p->cluster = true;
     }
   }
   if (!threads) return SPH_EUNSUPPORTED;

@@ -400,7 +400,9 @@ struct PhiSplitAcc {
   using C = typename P::C;
   using T = typename P::T;
   using Seq = typename PhiAcc<P>::Seq;
-  uint32_t A, Bm, lin;
+  uint32_t A, Bm;
+  uint32_t lin0, lin1;  // scratch: the peer's rows of A (two blocks of `cap` sequences each)
+  int cap;
   const int2* pairs;
   const void* gtab;
   size_t gbase;
@@ -441,7 +443,9 @@ struct PhiSplitAcc {
   }
   __device__ __forceinline__ T mult(const Seq& s, int m) const { return ring_mult(s.j1, m); }
   __device__ __forceinline__ uint32_t lin_at(int b, int n) const {
-    return lin + 16u * (uint32_t)((b - b0) * N + swz(n, N8));
+    const int bl = b - b0;
+    const bool second = bl >= cap;
+    return (second ? lin1 : lin0) + 16u * (uint32_t)((second ? bl - cap : bl) * N + swz(n, N8));
   }
   __device__ __forceinline__ C lin_ld(int b, int n) const { return P::ld16(lin_at(b, n)); }
   __device__ __forceinline__ void lin_st(int b, int n, C v) const { P::st16(lin_at(b, n), v); }
@@ -981,8 +985,9 @@ struct LayoutCl {
   int* misc;
 };
 
-// Shared memory of one CTA of a pair: A (all rows, half the columns), B (a quarter of the rows, the
-// other half of the columns), FFT scratch, tables.
+// Shared memory of one CTA of a pair: A (all rows, half the columns), B (half of the rows, the other
+// half of the columns), tables. The FFT scratch of the theta pass is B (not yet filled, or already
+// read by the peer); that of the phi pass is the peer's rows of A (not yet filled, or already read).
 __host__ __device__ __forceinline__ size_t cl_ld(const ShellArgs2& A) { return (size_t)A.Nph / 2 + 2; }
 
 template <class P>
@@ -996,7 +1001,7 @@ __device__ LayoutCl<P> carve_cl(const ShellArgs2& A, unsigned char* base) {
   };
   L.A = saddr(take(8 * (size_t)A.Nth * cl_ld(A)));
   L.B = saddr(take(8 * (size_t)(A.Nth / 2) * cl_ld(A)));
-  L.lin = saddr(take(scratch_bytes(A)));
+  L.lin = 0;
   L.ov = saddr(take(16 * (size_t)max(2 * A.Nth, A.Nph)));
   L.tw_th = saddr(take(16 * 2 * (size_t)A.Nth));
   L.tw_ph = saddr(take(16 * (size_t)A.Nph));
@@ -1011,7 +1016,6 @@ size_t shell_smem_cl(const ShellArgs2& a) {
   auto up = [](size_t x) { return (x + 15) / 16 * 16; };
   size_t s = up(8 * (size_t)a.Nth * cl_ld(a));
   s += up(8 * (size_t)(a.Nth / 2) * cl_ld(a));
-  s += up(scratch_bytes(a));
   s += up(16 * (size_t)std::max(2 * a.Nth, a.Nph));
   s += up(16 * 2 * (size_t)a.Nth);
   s += up(16 * (size_t)a.Nph);
@@ -1059,23 +1063,55 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512) shell_kernel_cl
   K.s3 = P::from_tab(A.consts, 1);
 
   // load: forward order takes every row of blocks {r, r+2} into A; the transpose order takes this
-  // rank's rows, blocks {r, r+2} into A and the others into B. Raw FP64 first.
+  // rank's rows, blocks {r, r+2} into A and the others into B. Raw FP64 first (cp.async, 16-byte
+  // pieces, when the input is FP64 and 16-byte aligned).
   const double* srcd = static_cast<const double*>(io.in) + off;
   const float* srcf = static_cast<const float*>(io.in) + off;
   const int rows = fwd ? Nth : Nth / 2;
-  unsigned emax = 0;
-  for (int e = threadIdx.x; e < rows * Nph; e += blockDim.x) {
-    const int jr = e / Nph, c = e - jr * Nph;
-    int j = jr;
-    if (!fwd) j = jr < Nth / 4 ? r * (Nth / 4) + jr : Nth - (r + 1) * (Nth / 4) + (jr - Nth / 4);
+  auto row_of = [&](int jr) {
+    return fwd ? jr : (jr < Nth / 4 ? r * (Nth / 4) + jr : Nth - (r + 1) * (Nth / 4) + (jr - Nth / 4));
+  };
+  auto addr_of = [&](int j, int c) {
     int lc;
     const bool mine = cl_mine(c, QB, r, &lc);
-    if (fwd && !mine) continue;
-    double x = io.is_f32 ? (double)__ldcs(srcf + (size_t)j * Nph + c) : __ldcs(srcd + (size_t)j * Nph + c);
-    if (io.map_in == kMapTanh) x = tanh(x);
-    if (dfp) emax = max(emax, (unsigned)df_exp_field(x));
-    const uint32_t a = mine ? L.A + (uint32_t)(j * ldc + lc) * 8u : L.B + (uint32_t)(cl_brow(j, Nth, r) * ldc + lc) * 8u;
-    F64::st8(a, x);
+    return mine ? L.A + (uint32_t)(j * ldc + lc) * 8u : L.B + (uint32_t)(cl_brow(j, Nth, r) * ldc + lc) * 8u;
+  };
+  const int cols = fwd ? Nph / 2 : Nph;  // columns loaded per row
+  auto col_of = [&](int cc) {            // cc-th loaded column of a row
+    if (!fwd) return cc;
+    return cc < QB ? r * QB + cc : (2 + r) * QB + (cc - QB);
+  };
+  if (!io.is_f32 && io.async_ok) {
+    for (int e = threadIdx.x; e < rows * (cols / 2); e += blockDim.x) {
+      const int jr = e / (cols / 2), c = col_of(2 * (e - jr * (cols / 2)));
+      const int j = row_of(jr);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(addr_of(j, c)), "l"(srcd + (size_t)j * Nph + c)
+                   : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+  } else {
+    for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
+      const int jr = e / cols, c = col_of(e - jr * cols);
+      const int j = row_of(jr);
+      const double x = io.is_f32 ? (double)__ldcs(srcf + (size_t)j * Nph + c) : __ldcs(srcd + (size_t)j * Nph + c);
+      F64::st8(addr_of(j, c), x);
+    }
+    __syncthreads();
+  }
+  unsigned emax = 0;
+  if (io.map_in == kMapTanh || dfp) {
+    for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
+      const int jr = e / cols, c = col_of(e - jr * cols);
+      const uint32_t a = addr_of(row_of(jr), c);
+      double x = F64::ld8(a);
+      if (io.map_in == kMapTanh) {
+        x = tanh(x);
+        F64::st8(a, x);
+      }
+      if (dfp) emax = max(emax, (unsigned)df_exp_field(x));
+    }
   }
   int E = 0;
   if (dfp) {
@@ -1088,14 +1124,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512) shell_kernel_cl
     unsigned other;
     asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(other) : "r"(peer_addr(mine, 1 - r)));
     E = max(L.misc[2], (int)other) - 1023;
-    for (int e = threadIdx.x; e < rows * Nph; e += blockDim.x) {
-      const int jr = e / Nph, c = e - jr * Nph;
-      int j = jr;
-      if (!fwd) j = jr < Nth / 4 ? r * (Nth / 4) + jr : Nth - (r + 1) * (Nth / 4) + (jr - Nth / 4);
-      int lc;
-      const bool mine_c = cl_mine(c, QB, r, &lc);
-      if (fwd && !mine_c) continue;
-      const uint32_t a = mine_c ? L.A + (uint32_t)(j * ldc + lc) * 8u : L.B + (uint32_t)(cl_brow(j, Nth, r) * ldc + lc) * 8u;
+    for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
+      const int jr = e / cols, c = col_of(e - jr * cols);
+      const uint32_t a = addr_of(row_of(jr), c);
       P::st8(a, to_real<P>(F64::ld8(a), E));
     }
   }
@@ -1127,7 +1158,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512) shell_kernel_cl
   ThetaAcc<P> TA;
   TA.S = L.A;
   TA.ov = L.ov;
-  TA.lin = L.lin;
+  TA.lin = L.B;
   TA.g = L.g_th;
   TA.ld = ldc;
   TA.Nth = Nth;
@@ -1144,7 +1175,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512) shell_kernel_cl
   PhiSplitAcc<P> PA;
   PA.A = L.A;
   PA.Bm = L.B;
-  PA.lin = L.lin;
+  {
+    const int q = Nth / 4, ro = 1 - r;
+    PA.lin0 = L.A + (uint32_t)(q * ro * ldc) * 8u;
+    PA.lin1 = L.A + (uint32_t)((Nth - (ro + 1) * q) * ldc) * 8u;
+    PA.cap = (q * ldc * 8) / (16 * Nph);
+  }
   PA.pairs = L.pairs;
   PA.gtab = A.g_ph;
   PA.gbase = ((size_t)vi.cls * A.Nr + i) * (size_t)Nth * (Nph / 2 + 1);
