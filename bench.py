@@ -42,6 +42,21 @@ DF_INSTR_PER_FLOP = 866.0 / 98.0
 DF_PEAK_TFLOPS = F32_INSTR_PER_S / DF_INSTR_PER_FLOP / 1e12
 
 
+def kernel_sources_hash() -> str:
+    """Hash of the CUDA sources, to tell whether recorded ncu counters still describe the kernel."""
+    import glob
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2305_01537_gb300", "csrc")
+    files = sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))
+                   + glob.glob(os.path.join(csrc, "*.h")))
+    h = hashlib.sha256()
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -124,6 +139,21 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows),
                 "power_w_max": max(float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit())
                 if any(r[2].replace(".", "").isdigit() for r in self.rows) else None}
+
+
+def combine_ranks(times_ms, units_per_rank: float, steps: int, device=None):
+    """Max over ranks of each timed region (ms) and the whole-job rate of each: every rank
+    processes `units_per_rank` units per step (independent shards, weak scaling), so the job's
+    rate is world * units * steps / slowest time. Uses the default process group if initialised."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    t = torch.tensor([float(x) for x in times_ms], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    slow = [float(x) for x in t.cpu()]
+    rates = [world * units_per_rank * steps / (ms * 1e-3) for ms in slow]
+    return slow, rates
 
 
 def dist_setup():
@@ -364,14 +394,10 @@ def main():
     barrier()
     e2e_ms = e0.elapsed_time(e1)
 
-    if world > 1:
-        t = torch.tensor([elapsed_ms, e2e_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms, e2e_ms = float(t[0]), float(t[1])
-
     points = g.points
-    value = world * points * args.steps / (elapsed_ms * 1e-3) / 1e9
-    e2e_value = world * points * args.steps / (e2e_ms * 1e-3) / 1e9
+    (elapsed_ms, e2e_ms), (rate, e2e_rate) = combine_ranks([elapsed_ms, e2e_ms], points, args.steps, device="cuda")
+    value = rate / 1e9
+    e2e_value = e2e_rate / 1e9
     if rank == 0:
         peaks, src = measured_peaks()
         avg_kernel_s = statistics.mean(kernel_ms) * 1e-3
@@ -383,7 +409,9 @@ def main():
         tp = os.path.join(ROOT, "profiles", "traffic.json")
         if os.path.exists(tp):
             with open(tp) as f:
-                traffic = json.load(f).get(f"{args.precision}:{wl.name}")
+                rec = json.load(f)
+            if rec.get("kernel_sources_sha256_16") == kernel_sources_hash():
+                traffic = rec.get(f"{args.precision}:{wl.name}")
         if args.precision == "f64":
             roof = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
