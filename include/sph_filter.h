@@ -123,6 +123,24 @@ sph_status sph_filter_apply_adjoint_tanh_f32(sph_filter_plan plan, const float* 
 sph_status sph_filter_apply_host(sph_filter_plan plan, const double* host_in, double* host_out,
                                  sph_stream_t stream);
 
+/* Same as sph_filter_apply_host, but allocates no device memory: the device copies of the input
+ * and the output live in a fixed array inside the library (32 MiB on every GPU that loads it,
+ * held until the process exits). The paper has no counterpart; this is for callers that cannot
+ * let a library allocate device memory, e.g. a framework whose own allocator has reserved the
+ * whole device at start-up, or code that must not risk the device synchronisation that
+ * cudaMalloc/cudaFree may cause. No cudaMalloc, cudaFree or allocating library routine is called.
+ * Limits and behaviour:
+ *  - The state may have at most 2,097,152 points (nvars * Nr * Ntheta * Nphi); larger states are
+ *    rejected with SPH_EINVAL before anything is enqueued.
+ *  - The first call on a device looks up the array's device address on that device (a one-time
+ *    set-up); make that first call before any stream capture.
+ *  - Every call uses the same array, and nothing in it needs to start at zero (each call overwrites
+ *    what it reads). Calls whose work overlaps on the GPU (e.g. on two streams) race on the array;
+ *    order them on one stream or synchronise between them.
+ *  - host_in/host_out as in sph_filter_apply_host; asynchronous on `stream`. */
+sph_status sph_filter_apply_host_noalloc(sph_filter_plan plan, const double* host_in, double* host_out,
+                                         sph_stream_t stream);
+
 /* Wait for all work on the plan's device and return the first error a kernel latched for this
  * plan (SPH_OK if none), then clear it. */
 sph_status sph_filter_plan_sync_status(sph_filter_plan plan);

@@ -28,7 +28,7 @@ EXPORTED = (
     "sph_filter_apply_host", "sph_filter_plan_sync_status", "sph_filter_plan_points",
     "sph_filter_plan_launches", "sph_filter_status_string", "sph_filter_batch_create",
     "sph_filter_batch_destroy", "sph_filter_batch_apply", "sph_filter_batch_capture", "sph_filter_batch_launch",
-    "sph_filter_plan_autotune",
+    "sph_filter_plan_autotune", "sph_filter_apply_host_noalloc",
 )
 
 
@@ -77,6 +77,7 @@ def load() -> ctypes.CDLL:
         "sph_filter_batch_capture": ([P, P, P, I, P], I),
         "sph_filter_batch_launch": ([P, P], I),
         "sph_filter_plan_autotune": ([P, P, P, P, ctypes.POINTER(ctypes.c_double)], I),
+        "sph_filter_apply_host_noalloc": ([P, P, P, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
