@@ -51,6 +51,9 @@ struct F64 {
     double re, im;
   };
   static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+  static __device__ __forceinline__ T add_nr(T a, T b) { return a + b; }
+  static __device__ __forceinline__ T sub_nr(T a, T b) { return a - b; }
+  static __device__ __forceinline__ T norm(T a) { return a; }
   static __device__ __forceinline__ T sub(T a, T b) { return a - b; }
   static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
   static __device__ __forceinline__ T neg(T a) { return -a; }
@@ -95,13 +98,27 @@ struct DF {
   }
   static __device__ __forceinline__ df neg(df a) { return df{-a.hi, -a.lo}; }
   static __device__ __forceinline__ df sub(df a, df b) { return add(a, neg(b)); }
+  // Sum without the final renormalisation: hi is the rounded sum of the high parts, lo collects
+  // its exact rounding error and the low parts. Chains of these stay accurate to about 2^-46 as
+  // long as each butterfly's outputs are renormalised (norm) before they are stored.
+  static __device__ __forceinline__ df add_nr(df a, df b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    return df{s, __fadd_rn(e, __fadd_rn(a.lo, b.lo))};
+  }
+  static __device__ __forceinline__ df sub_nr(df a, df b) { return add_nr(a, neg(b)); }
+  static __device__ __forceinline__ df norm(df a) {
+    const float h = __fadd_rn(a.hi, a.lo);
+    return df{h, __fsub_rn(a.lo, __fsub_rn(h, a.hi))};
+  }
+  // Product (exact high product plus the cross terms), not renormalised.
   static __device__ __forceinline__ df mul(df a, df b) {
     const float p = __fmul_rn(a.hi, b.hi);
     float e = __fmaf_rn(a.hi, b.hi, -p);
     e = __fmaf_rn(a.hi, b.lo, e);
     e = __fmaf_rn(a.lo, b.hi, e);
-    const float h = __fadd_rn(p, e);
-    return df{h, __fsub_rn(e, __fsub_rn(h, p))};
+    return df{p, e};
   }
   static __device__ __forceinline__ df half(df a) { return df{0.5f * a.hi, 0.5f * a.lo}; }
   static __device__ __forceinline__ df zero() { return df{0.0f, 0.0f}; }
@@ -110,7 +127,7 @@ struct DF {
     return df{v.x, v.y};
   }
   // a*b - c*d in compensated arithmetic: exact products of the high parts, TwoSum of their
-  // difference, the low-order cross terms accumulated by FMA, one renormalisation.
+  // difference, the low-order cross terms accumulated by FMA (not renormalised).
   static __device__ __forceinline__ df dot2(df a, df b, df c, df d) {
     const float p1 = __fmul_rn(a.hi, b.hi);
     const float e1 = __fmaf_rn(a.hi, b.hi, -p1);
@@ -124,8 +141,7 @@ struct DF {
     t = __fmaf_rn(a.lo, b.hi, t);
     t = __fmaf_rn(-c.hi, d.lo, t);
     t = __fmaf_rn(-c.lo, d.hi, t);
-    const float h = __fadd_rn(s, t);
-    return df{h, __fsub_rn(t, __fsub_rn(h, s))};
+    return df{s, t};
   }
   static __device__ __forceinline__ C cmul(C a, C w) {
     return C{dot2(a.re, w.re, a.im, w.im), dot2(a.re, w.im, neg(a.im), w.re)};
@@ -154,8 +170,9 @@ template <class P>
 struct Cx {
   using C = typename P::C;
   using T = typename P::T;
-  static __device__ __forceinline__ C add(C a, C b) { return C{P::add(a.re, b.re), P::add(a.im, b.im)}; }
-  static __device__ __forceinline__ C sub(C a, C b) { return C{P::sub(a.re, b.re), P::sub(a.im, b.im)}; }
+  static __device__ __forceinline__ C add(C a, C b) { return C{P::add_nr(a.re, b.re), P::add_nr(a.im, b.im)}; }
+  static __device__ __forceinline__ C sub(C a, C b) { return C{P::sub_nr(a.re, b.re), P::sub_nr(a.im, b.im)}; }
+  static __device__ __forceinline__ C norm(C a) { return C{P::norm(a.re), P::norm(a.im)}; }
   static __device__ __forceinline__ C scale(C a, T g) { return C{P::mul(a.re, g), P::mul(a.im, g)}; }
   static __device__ __forceinline__ C neg(C a) { return C{P::neg(a.re), P::neg(a.im)}; }
   template <int DIR>  // multiply by DIR * i
@@ -231,7 +248,7 @@ struct Dft<P, 3, DIR> {
   static __device__ __forceinline__ void run(typename P::C* v, const Consts<P>& k) {
     const auto t = X::add(v[1], v[2]);
     const auto s = X::sub(v[1], v[2]);
-    const typename P::C m{P::sub(v[0].re, P::half(t.re)), P::sub(v[0].im, P::half(t.im))};
+    const typename P::C m{P::sub_nr(v[0].re, P::half(t.re)), P::sub_nr(v[0].im, P::half(t.im))};
     const auto w = X::template mul_i<DIR>(X::scale(s, k.s3));
     v[0] = X::add(v[0], t);
     v[1] = X::add(m, w);
@@ -505,6 +522,7 @@ __device__ __forceinline__ void stage(const Acc& A, int N, int B, int Ns, uint32
 #pragma unroll
     for (int t = 0; t < R; ++t) {
       const int n = base + t * Ns;
+      v[t] = X::norm(v[t]);
       if (MODE & kLast) A.scatter(sq, n, v[t]);
       else if (FROM_SLOTS) A.lin_st(b, n, v[t]);
       else A.slot_st(sq, n, v[t]);
@@ -717,7 +735,8 @@ struct Layout {
   uint32_t lin;        // FFT scratch
   uint32_t ov, tw_th, tw_ph, g_th;
   int2* pairs;
-  int* misc;  // [0] pair count, [1] general flag, [2] block max exponent
+  int* misc;               // [0] pair count, [1] general flag, [2] block max exponent
+  unsigned char* rowact;   // rows that are transformed (1) or passed through unchanged (0)
 };
 
 // Scratch for one batch: batch_th theta sequences (2 Ntheta slots each) or batch_ph phi pairs
@@ -746,6 +765,7 @@ __device__ Layout<P> carve(const ShellArgs2& A, unsigned char* base) {
   L.g_th = saddr(take(8 * (size_t)(A.Nth + 1)));
   L.pairs = reinterpret_cast<int2*>(take(sizeof(int2) * (size_t)(A.Nth / 2 + 1)));
   L.misc = reinterpret_cast<int*>(take(sizeof(int) * 4));
+  L.rowact = take((size_t)A.Nth);
   return L;
 }
 
@@ -816,17 +836,48 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
     }
     __syncthreads();
   }
-  // input map, block exponent, conversion to the working precision (in place)
+  // per-shell tables: theta multipliers, phi ring pairs, rows that will be transformed
+  const double lmax = A.lmax[vi.cls * A.Nr + i];
+  const bool gauss = vi.kind == SPH_FILTER_GAUSS;
+  const bool theta_on = gauss || lmax < (double)Nth;
+  const size_t gth_base = ((size_t)vi.cls * A.Nr + i) * (Nth + 1);
+  for (int n = threadIdx.x; n <= Nth; n += blockDim.x) P::st8(L.g_th + 8u * n, P::from_tab(A.g_th, gth_base + n));
+  for (int j = threadIdx.x; j < Nth; j += blockDim.x) L.rowact[j] = theta_on ? 1 : 0;
+  const uint8_t* ring_info = A.ring_info + ((size_t)vi.cls * A.Nr + i) * Nth;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int np = 0, gen = 0;
+    for (int j = 0; j < (Nth + 1) / 2; ++j) {
+      const int jj = Nth - 1 - j;
+      const uint8_t a = ring_info[j], b = ring_info[jj];
+      if (!((a | b) & 1)) continue;  // bit 0: ring active
+      L.rowact[j] = L.rowact[jj] = 1;
+      if (jj == j) {
+        L.pairs[np++] = make_int2(j, -1);
+      } else {
+        const int g = (a >> 1) & 1;  // bit 1: multipliers of j and its mirror differ
+        gen |= g;
+        L.pairs[np++] = make_int2(j | (g << 30), jj);
+      }
+    }
+    L.misc[0] = np;
+    L.misc[1] = gen;
+  }
+  __syncthreads();
+
+  // input map on every value; block exponent and conversion to the working precision (in place)
+  // only on the rows that are transformed: the others are stored back as they were loaded
   unsigned emax = 0;
   if (io.map_in == kMapTanh || dfp) {
     for (int n = threadIdx.x; n < npts; n += blockDim.x) {
-      const int o = (n / Nph) * ld + n % Nph;
+      const int jrow = n / Nph;
+      const int o = jrow * ld + n % Nph;
       double x = Sd[o];
       if (io.map_in == kMapTanh) {
         x = tanh(x);
         Sd[o] = x;
       }
-      if (dfp) emax = max(emax, (unsigned)df_exp_field(x));
+      if (dfp && L.rowact[jrow]) emax = max(emax, (unsigned)df_exp_field(x));
     }
   }
   int E = 0;
@@ -839,34 +890,11 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
     E = L.misc[2] - 1023;
     const uint32_t sb = saddr(buf);
     for (int n = threadIdx.x; n < npts; n += blockDim.x) {
-      const int o = (n / Nph) * ld + n % Nph;
+      const int jrow = n / Nph;
+      if (!L.rowact[jrow]) continue;
+      const int o = jrow * ld + n % Nph;
       P::st8(sb + 8u * o, to_real<P>(Sd[o], E));
     }
-  }
-
-  // per-shell tables: theta multipliers, phi ring pairs
-  const double lmax = A.lmax[vi.cls * A.Nr + i];
-  const bool gauss = vi.kind == SPH_FILTER_GAUSS;
-  const bool theta_on = gauss || lmax < (double)Nth;
-  const size_t gth_base = ((size_t)vi.cls * A.Nr + i) * (Nth + 1);
-  for (int n = threadIdx.x; n <= Nth; n += blockDim.x) P::st8(L.g_th + 8u * n, P::from_tab(A.g_th, gth_base + n));
-  const uint8_t* ring_info = A.ring_info + ((size_t)vi.cls * A.Nr + i) * Nth;
-  if (threadIdx.x == 0) {
-    int np = 0, gen = 0;
-    for (int j = 0; j < (Nth + 1) / 2; ++j) {
-      const int jj = Nth - 1 - j;
-      const uint8_t a = ring_info[j], b = ring_info[jj];
-      if (!((a | b) & 1)) continue;  // bit 0: ring active
-      if (jj == j) {
-        L.pairs[np++] = make_int2(j, -1);
-      } else {
-        const int g = (a >> 1) & 1;  // bit 1: multipliers of j and its mirror differ
-        gen |= g;
-        L.pairs[np++] = make_int2(j | (g << 30), jj);
-      }
-    }
-    L.misc[0] = np;
-    L.misc[1] = gen;
   }
   __syncthreads();
   const int npairs = L.misc[0];
@@ -913,11 +941,12 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
     }
   }
 
-  // store (streaming), with the output map
+  // store (streaming), with the output map; untransformed rows are still FP64
   const uint32_t sb = saddr(buf);
   for (int n = threadIdx.x; n < npts; n += blockDim.x) {
-    const int o = (n / Nph) * ld + n % Nph;
-    double y = from_real<P>(P::ld8(sb + 8u * o), E);
+    const int jrow = n / Nph;
+    const int o = jrow * ld + n % Nph;
+    double y = (dfp && !L.rowact[jrow]) ? Sd[o] : from_real<P>(P::ld8(sb + 8u * o), E);
     if (io.map_out == kOutTanhGrad) {
       const double z = io.is_f32 ? (double)static_cast<const float*>(io.aux)[off + n]
                                  : static_cast<const double*>(io.aux)[off + n];
@@ -1273,6 +1302,7 @@ size_t shell_smem(const ShellArgs2& a) {
   s += up(8 * (size_t)(a.Nth + 1));
   s += up(sizeof(int2) * (size_t)(a.Nth / 2 + 1));
   s += up(sizeof(int) * 4);
+  s += up((size_t)a.Nth);
   return s;
 }
 

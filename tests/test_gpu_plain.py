@@ -111,13 +111,10 @@ def test_full_state_128x64x128_sampled(torch_cuda, prec):
     err = np.array([np.abs(got[n] - ref[n]).max() / np.abs(ref[n]).max() for n in range(len(shells))])
     assert err.max() <= TOL, shells[int(err.argmax())]
     # rings the exponential filter leaves alone (theta-identity shell, m_max >= Nphi/2) are not
-    # transformed: copied bit for bit in FP64, rounded once to the 48-bit pair form otherwise
+    # transformed and come back bit for bit, in both precisions
     rows = [j for j in range(g.Ntheta) if oracle.mmax(g.r[127], g.dr_min, g.L[0], j, g.Ntheta) >= g.Nphi / 2]
     assert len(rows) > g.Ntheta // 2
-    if prec == 0:
-        assert np.array_equal(y[0, 127, rows], x[0, 127, rows])
-    else:
-        assert np.abs(y[0, 127, rows] - x[0, 127, rows]).max() <= 2.0 ** -47 * np.abs(x[0, 127, rows]).max()
+    assert np.array_equal(y[0, 127, rows], x[0, 127, rows])
 
 
 @pytest.mark.parametrize("prec", PRECS)
