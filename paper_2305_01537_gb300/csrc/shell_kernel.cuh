@@ -791,16 +791,19 @@ __device__ __forceinline__ size_t shell_offset(const ShellArgs2& A, int s, int* 
   return ((size_t)*v * A.Nr + *i) * (size_t)A.Nth * A.Nph;
 }
 
-// Start the asynchronous copy of shell s into a buffer (16-byte pieces into the padded rows).
+// Start the asynchronous copy of shell s into a buffer (16-byte pieces into the padded rows). The
+// sizes are compile-time constants for the fixed lengths.
+template <int LEN>
 __device__ __forceinline__ void issue_load(const ShellArgs2& A, const double* in, int s, unsigned char* buf) {
   int v, i;
   const double* src = in + shell_offset(A, s, &v, &i);
-  const int half = A.Nph / 2, total = A.Nth * half;
+  const int Nth = LEN ? LEN / 2 : A.Nth, Nph = LEN ? LEN : A.Nph, ldS = LEN ? LEN + 2 : A.ldS;
+  const int half = Nph / 2, total = Nth * half;
   const uint32_t dst = saddr(buf);
   for (int c = threadIdx.x; c < total; c += blockDim.x) {
     const int row = c / half, k2 = c - row * half;
-    const uint32_t d = dst + (uint32_t)(row * A.ldS + 2 * k2) * 8u;
-    const double* g = src + (size_t)row * A.Nph + 2 * k2;
+    const uint32_t d = dst + (uint32_t)(row * ldS + 2 * k2) * 8u;
+    const double* g = src + (size_t)row * Nph + 2 * k2;
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(g) : "memory");
   }
 }
@@ -812,7 +815,8 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
   int v, i;
   const size_t off = shell_offset(A, s, &v, &i);
   const VarInfo vi = A.var[v];
-  const int Nth = A.Nth, Nph = A.Nph, ld = A.ldS;
+  // compile-time sizes for the fixed lengths (divisions by Nphi become shifts or multiplies)
+  const int Nth = LEN ? LEN / 2 : A.Nth, Nph = LEN ? LEN : A.Nph, ld = LEN ? LEN + 2 : A.ldS;
   const int npts = Nth * Nph;
   double* Sd = reinterpret_cast<double*>(buf);
 
@@ -974,7 +978,7 @@ __global__ void __launch_bounds__(512) shell_kernel(ShellArgs2 A, LaunchIO io) {
 
   const int sidx = blockIdx.x;
   if (!io.is_f32 && io.async_ok) {
-    issue_load(A, static_cast<const double*>(io.in), sidx, L.buf);
+    issue_load<LEN>(A, static_cast<const double*>(io.in), sidx, L.buf);
     asm volatile("cp.async.commit_group;" ::: "memory");
     asm volatile("cp.async.wait_group 0;" ::: "memory");
   }
