@@ -264,6 +264,10 @@ void free_plan(sph_filter_plan_s* p) {
   cudaFree(p->d_tabs);
   cudaFree(p->d_stage_in);
   cudaFree(p->d_stage_out);
+  for (cudaStream_t s : p->pipe)
+    if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t e : p->pipe_ev)
+    if (e) cudaEventDestroy(e);
   delete p;
 }
 
@@ -278,6 +282,14 @@ sph_status check_io(const sph_filter_plan_s* p, const void* in, const void* out,
 
 sph_status launch_plan(sph_filter_plan_s* p, const void* in, const void* aux, void* out, int map_in, int map_out,
                        int transpose, int is_f32, cudaStream_t stream) {
+  if (!p) return SPH_EINVAL;
+  return launch_plan_vars(p, in, aux, out, map_in, map_out, transpose, is_f32, 0, p->nvars, stream);
+}
+
+sph_status launch_plan_vars(sph_filter_plan_s* p, const void* in, const void* aux, void* out, int map_in,
+                            int map_out, int transpose, int is_f32, int var_begin, int var_count,
+                            cudaStream_t stream) {
+  if (!p || var_begin < 0 || var_count < 1 || var_begin + var_count > p->nvars) return SPH_EINVAL;
   sph_status st = check_io(p, in, out, is_f32 ? sizeof(float) : sizeof(double));
   if (st != SPH_OK) return st;
   if (map_out == kOutTanhGrad) {
@@ -289,7 +301,8 @@ sph_status launch_plan(sph_filter_plan_s* p, const void* in, const void* aux, vo
   int cur = -1;
   if (cudaGetDevice(&cur) != cudaSuccess) return SPH_ECUDA;
   if (cur != p->device && cudaSetDevice(p->device) != cudaSuccess) return SPH_ECUDA;
-  LaunchIO io{in, aux, out, map_in, map_out, transpose, is_f32, ((uintptr_t)in % 16) == 0 ? 1 : 0};
+  LaunchIO io{in,        aux,    out, map_in, map_out, transpose, is_f32, ((uintptr_t)in % 16) == 0 ? 1 : 0,
+              var_begin, var_count};
   cudaError_t e = !p->use_v2 ? launch_plain(*p, io, (cudaStream_t)stream)
                   : p->cluster ? launch_shell_cl(p->args2, p->precision, p->threads2, p->smem2, io, (cudaStream_t)stream)
                                : launch_shell(p->args2, p->precision, p->threads2, p->smem2, io, (cudaStream_t)stream);
@@ -476,7 +489,8 @@ sph_status sph_filter_apply_adjoint_tanh_f32(sph_filter_plan plan, const float* 
 sph_status sph_filter_apply_host(sph_filter_plan plan, const double* host_in, double* host_out,
                                  sph_stream_t stream) {
   if (!plan || !host_in || !host_out) return SPH_EINVAL;
-  const size_t n = (size_t)plan->nvars * plan->Nr * plan->Nth * plan->Nph;
+  const size_t field = (size_t)plan->Nr * plan->Nth * plan->Nph;  // values per field
+  const size_t n = field * plan->nvars;
   if (!plan->d_stage_in) {
     if (cudaMalloc((void**)&plan->d_stage_in, sizeof(double) * n) != cudaSuccess) return SPH_ENOMEM;
     if (cudaMalloc((void**)&plan->d_stage_out, sizeof(double) * n) != cudaSuccess) {
@@ -485,13 +499,41 @@ sph_status sph_filter_apply_host(sph_filter_plan plan, const double* host_in, do
       return SPH_ENOMEM;
     }
   }
+  if (!plan->pipe[0]) {
+    for (cudaStream_t& s : plan->pipe)
+      if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return SPH_ECUDA;
+    for (cudaEvent_t& e : plan->pipe_ev)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return SPH_ECUDA;
+  }
+  // Pipeline over chunks of whole fields on three streams: the copy in of one chunk, the filter of
+  // another and the copy out of a third overlap (both directions of the host link are in use).
   cudaStream_t s = (cudaStream_t)stream;
-  if (cudaMemcpyAsync(plan->d_stage_in, host_in, sizeof(double) * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
-    return SPH_ECUDA;
-  sph_status st = sph_filter_apply(plan, plan->d_stage_in, plan->d_stage_out, stream);
-  if (st != SPH_OK) return st;
-  if (cudaMemcpyAsync(host_out, plan->d_stage_out, sizeof(double) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-    return SPH_ECUDA;
+  // chunks of about 16 MiB: small enough that filling and draining the pipeline costs little, large
+  // enough that each copy runs at the link's full rate
+  const size_t field_bytes = sizeof(double) * field;
+  const int chunk = (int)std::min<size_t>(plan->nvars, std::max<size_t>(1, ((16u << 20) + field_bytes / 2) / field_bytes));
+  if (cudaEventRecord(plan->pipe_ev[3], s) != cudaSuccess) return SPH_ECUDA;
+  for (cudaStream_t ps : plan->pipe)
+    if (cudaStreamWaitEvent(ps, plan->pipe_ev[3], 0) != cudaSuccess) return SPH_ECUDA;
+  int k = 0;
+  for (int v0 = 0; v0 < plan->nvars; v0 += chunk, ++k) {
+    const int nv = std::min(chunk, plan->nvars - v0);
+    cudaStream_t ps = plan->pipe[k % 3];
+    const size_t off = field * v0, cnt = field * nv;
+    if (cudaMemcpyAsync(plan->d_stage_in + off, host_in + off, sizeof(double) * cnt, cudaMemcpyHostToDevice, ps) !=
+        cudaSuccess)
+      return SPH_ECUDA;
+    const sph_status st = launch_plan_vars(plan, plan->d_stage_in, nullptr, plan->d_stage_out, kMapNone, kOutNone, 0,
+                                           0, v0, nv, ps);
+    if (st != SPH_OK) return st;
+    if (cudaMemcpyAsync(host_out + off, plan->d_stage_out + off, sizeof(double) * cnt, cudaMemcpyDeviceToHost, ps) !=
+        cudaSuccess)
+      return SPH_ECUDA;
+  }
+  for (int q = 0; q < 3; ++q) {
+    if (cudaEventRecord(plan->pipe_ev[q], plan->pipe[q]) != cudaSuccess) return SPH_ECUDA;
+    if (cudaStreamWaitEvent(s, plan->pipe_ev[q], 0) != cudaSuccess) return SPH_ECUDA;
+  }
   return SPH_OK;
 }
 

@@ -340,7 +340,7 @@ template <typename IO>
 __global__ void __launch_bounds__(kThreads, 1) plain_shell_kernel(ShellArgs A, LaunchIO io) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Smem m = carve(A, smem_raw);
-  const int shell = blockIdx.x;
+  const int shell = io.var_begin * A.Nr + blockIdx.x;
   const int v = shell / A.Nr, i = shell - v * A.Nr;
   const VarInfo vi = A.var[v];
   const int Nth = A.Nth, Nph = A.Nph, ld = A.ldS;
@@ -406,7 +406,7 @@ size_t plain_smem_bytes(const ShellArgs& a, int* chunk_th, int* chunk_ph) {
 }
 
 cudaError_t launch_plain(const sph_filter_plan_s& p, const LaunchIO& io, cudaStream_t s) {
-  const dim3 grid((unsigned)(p.nvars * p.Nr));
+  const dim3 grid((unsigned)(io.var_count * p.Nr));
   if (io.is_f32) {
     plain_shell_kernel<float><<<grid, kThreads, p.smem_bytes, s>>>(p.args, io);
   } else {

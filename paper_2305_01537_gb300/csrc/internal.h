@@ -57,6 +57,8 @@ struct LaunchIO {
   int transpose;      // 0: theta then phi; 1: phi then theta
   int is_f32;         // 0: FP64 I/O, 1: FP32 I/O
   int async_ok;       // input 16-byte aligned: shells may be copied with cp.async
+  int var_begin;      // fields [var_begin, var_begin + var_count) are filtered (pointers are to
+  int var_count;      // the whole state)
 };
 
 // Arguments of the staged shell kernel (shell_kernel.cuh). Tables hold FP64 values, or
@@ -160,15 +162,21 @@ struct sph_filter_plan_s {
   double2* d_tw_ph = nullptr;
   unsigned* d_status = nullptr;
 
-  // staging buffers of sph_filter_apply_host (allocated on first use)
+  // staging buffers and pipeline streams of sph_filter_apply_host (created on first use)
   double* d_stage_in = nullptr;
   double* d_stage_out = nullptr;
+  cudaStream_t pipe[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t pipe_ev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace sph {
 // Enqueue one filter application of a plan (validates pointers; see sph_filter_apply).
 sph_status launch_plan(sph_filter_plan_s* p, const void* in, const void* aux, void* out, int map_in, int map_out,
                        int transpose, int is_f32, cudaStream_t stream);
+// The same for the fields [var_begin, var_begin + var_count) only.
+sph_status launch_plan_vars(sph_filter_plan_s* p, const void* in, const void* aux, void* out, int map_in,
+                            int map_out, int transpose, int is_f32, int var_begin, int var_count,
+                            cudaStream_t stream);
 // Shared-memory bytes the plain shell kernel needs for this plan's shape (0 if it cannot fit).
 size_t plain_smem_bytes(const ShellArgs& a, int* chunk_th, int* chunk_ph);
 // Enqueue the plain FP64 shell kernel.

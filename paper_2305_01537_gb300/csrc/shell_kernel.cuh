@@ -783,20 +783,21 @@ __device__ __forceinline__ double from_real<F64>(double x, int) { return x; }
 template <>
 __device__ __forceinline__ double from_real<DF>(df x, int E) { return df_to_double(x, E); }
 
-// Shell s in i-major order (the fields of one radius run together, so their multiplier rows stay in
-// L2); returns the element offset of the shell in the [var][shell] state layout.
-__device__ __forceinline__ size_t shell_offset(const ShellArgs2& A, int s, int* v, int* i) {
-  *i = s / A.nvars;
-  *v = s - *i * A.nvars;
+// Shell s of the launch in i-major order over the launched fields (the fields of one radius run
+// together, so their multiplier rows stay in L2); returns the element offset of the shell in the
+// [var][shell] layout of the whole state.
+__device__ __forceinline__ size_t shell_offset(const ShellArgs2& A, const LaunchIO& io, int s, int* v, int* i) {
+  *i = s / io.var_count;
+  *v = io.var_begin + (s - *i * io.var_count);
   return ((size_t)*v * A.Nr + *i) * (size_t)A.Nth * A.Nph;
 }
 
 // Start the asynchronous copy of shell s into a buffer (16-byte pieces into the padded rows). The
 // sizes are compile-time constants for the fixed lengths.
 template <int LEN>
-__device__ __forceinline__ void issue_load(const ShellArgs2& A, const double* in, int s, unsigned char* buf) {
+__device__ __forceinline__ void issue_load(const ShellArgs2& A, const LaunchIO& io, int s, unsigned char* buf) {
   int v, i;
-  const double* src = in + shell_offset(A, s, &v, &i);
+  const double* src = static_cast<const double*>(io.in) + shell_offset(A, io, s, &v, &i);
   const int Nth = LEN ? LEN / 2 : A.Nth, Nph = LEN ? LEN : A.Nph, ldS = LEN ? LEN + 2 : A.ldS;
   const int half = Nph / 2, total = Nth * half;
   const uint32_t dst = saddr(buf);
@@ -813,7 +814,7 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
                              const Consts<P>& K) {
   constexpr bool dfp = std::is_same<P, DF>::value;
   int v, i;
-  const size_t off = shell_offset(A, s, &v, &i);
+  const size_t off = shell_offset(A, io, s, &v, &i);
   const VarInfo vi = A.var[v];
   // compile-time sizes for the fixed lengths (divisions by Nphi become shifts or multiplies)
   const int Nth = LEN ? LEN / 2 : A.Nth, Nph = LEN ? LEN : A.Nph, ld = LEN ? LEN + 2 : A.ldS;
@@ -978,7 +979,7 @@ __global__ void __launch_bounds__(512) shell_kernel(ShellArgs2 A, LaunchIO io) {
 
   const int sidx = blockIdx.x;
   if (!io.is_f32 && io.async_ok) {
-    issue_load<LEN>(A, static_cast<const double*>(io.in), sidx, L.buf);
+    issue_load<LEN>(A, io, sidx, L.buf);
     asm volatile("cp.async.commit_group;" ::: "memory");
     asm volatile("cp.async.wait_group 0;" ::: "memory");
   }
@@ -1082,7 +1083,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512) shell_kernel_cl
   const int r = (int)cluster_rank();
   const int sidx = blockIdx.x / 2;
   int v, i;
-  const size_t off = shell_offset(A, sidx, &v, &i);
+  const size_t off = shell_offset(A, io, sidx, &v, &i);
   const VarInfo vi = A.var[v];
   const int Nth = A.Nth, Nph = A.Nph, QB = Nph / 4, ldc = (int)cl_ld(A);
   const bool fwd = io.transpose == 0;
@@ -1285,7 +1286,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512) shell_kernel_cl
 
 template <class P, int LEN>
 cudaError_t launch_cl_impl(const ShellArgs2& a, int threads, size_t smem, const LaunchIO& io, cudaStream_t s) {
-  const dim3 grid((unsigned)(2 * a.nvars * a.Nr));
+  const dim3 grid((unsigned)(2 * io.var_count * a.Nr));
   shell_kernel_cl<P, LEN><<<grid, threads, smem, s>>>(a, io);
   return cudaGetLastError();
 }
@@ -1312,7 +1313,7 @@ size_t shell_smem(const ShellArgs2& a) {
 
 template <class P, int LEN>
 cudaError_t launch_impl(const ShellArgs2& a, int threads, size_t smem, const LaunchIO& io, cudaStream_t s) {
-  const dim3 grid((unsigned)(a.nvars * a.Nr));
+  const dim3 grid((unsigned)(io.var_count * a.Nr));
   shell_kernel<P, LEN><<<grid, threads, smem, s>>>(a, io);
   return cudaGetLastError();
 }

@@ -170,16 +170,39 @@ def test_generic_chunked_fallback(torch_cuda):
     assert field_errors(y, oracle_of(g, x)).max() <= TOL
 
 
-def test_host_entry_point(torch_cuda):
+# sph_filter_apply_host moves chunks of whole fields of about 16 MiB; the sizes below give several
+# chunks and a shorter last one for each kernel (field bytes -> fields per chunk -> chunks).
+@pytest.mark.parametrize("nvars,Nr,Nth,Nph,prec", [
+    (28, 3, 8, 16, 0),        # 3 KB fields: one chunk
+    (28, 10, 64, 128, 0),     # staged kernel: 640 KiB fields, chunks of 26 + 2
+    (28, 10, 64, 128, 2),
+    (11, 40, 64, 128, 2),     # 2.5 MiB fields: chunks of 6 + 5
+    (9, 1500, 5, 74, 0),      # chunked fallback kernel: 4.2 MiB fields, chunks of 4 + 4 + 1
+    (5, 34, 128, 256, 2),     # cluster kernel: 8.5 MiB fields, chunks of 2 + 2 + 1
+])
+def test_host_entry_point(torch_cuda, nvars, Nr, Nth, Nph, prec):
+    """sph_filter_apply_host pipelines chunks of whole fields over three streams; every field must
+    come back as the device-buffer call filters it (bit for bit: the same kernels on the same
+    shells), and sampled shells as the oracle filters them."""
     from paper_2305_01537_gb300 import Plan
     torch = torch_cuda
-    g = W.grid_28(3, 8, 16)
-    x = torch.from_numpy(W.band_limited_state(g, seed=8, mode_max=2, noise=0.05)).pin_memory()
-    out = torch.empty_like(x).pin_memory()
-    plan = Plan.from_grid(g)
-    plan.apply_host(x, out)
-    torch.cuda.synchronize()
-    assert field_errors(out.numpy(), oracle_of(g, x.numpy())).max() <= TOL
+    g = W.grid_28(Nr, Nth, Nph)
+    sel = [(v * 5) % 28 for v in range(nvars)] if nvars < 28 else list(range(28))
+    g = W.Grid(Nr, Nth, Nph, [g.parity[v] for v in sel], [g.kind[v] for v in sel], [g.L[v] for v in sel], g.r)
+    xn = W.band_limited_state(g, seed=8, mode_max=2, noise=0.05)
+    x = torch.from_numpy(xn).pin_memory()
+    out = torch.full_like(x, np.nan).pin_memory()
+    plan = Plan.from_grid(g, precision=prec)
+    want = plan.apply(x.cuda()).cpu().numpy()
+    shells = sorted({(v, i) for v in (0, nvars // 2, nvars - 1) for i in (0, Nr // 2, Nr - 1)})
+    ref = oracle.filter_shells(xn, shells, g.parity, g.kind, g.L, g.r, g.dr_min, g.floor)
+    got = np.stack([want[v, i] for (v, i) in shells])
+    assert field_errors(got, ref).max() <= TOL
+    for _ in range(2):
+        plan.apply_host(x, out)
+        torch.cuda.synchronize()
+        assert plan.sync_status() == 0
+        assert np.array_equal(out.numpy(), want)
 
 
 def test_alias_and_errors(torch_cuda):
