@@ -62,7 +62,7 @@ def measured_peaks():
     if os.path.exists(path):
         with open(path) as f:
             return json.load(f), "measured"
-    return {"hbm_gbs": HBM_FALLBACK_GBS}, "fallback"
+    return {"hbm_gbs": HBM_FALLBACK_GBS, "bf16_tflops": 1900.0}, "fallback"
 
 
 def algorithmic_flops(grid) -> float:
@@ -80,6 +80,33 @@ def algorithmic_flops(grid) -> float:
             mm = np.maximum(grid.floor, 2 * grid.r[i] / grid.dr_min * np.sin(th) * grid.L[v])
             nact = grid.Ntheta if gauss else int((mm < grid.Nphi / 2).sum())
             flops += nact * grid.Nphi * (5 * math.log2(grid.Nphi) + 1)
+    return flops
+
+
+def tc_slice_products(L: int) -> float:
+    """Flops of the tensor-core form's four GEMMs for one vector of length L (unpadded sizes): with
+    H = L/2, cos forward H x (H+1), sin forward (H-1) x (H-1), and the same two inverse, each run
+    for the 21 slice pairs a + b <= 5 of six-slice operands, 2 flops per multiply-add."""
+    H = L // 2
+    return 21 * 2.0 * (2 * H * (H + 1) + 2 * (H - 1) ** 2)
+
+
+def tc_tensor_flops(grid) -> float:
+    """Tensor-core flops of one application of the split-precision form: every active theta shell
+    contributes Nphi/2 doubled circles of length 2 Ntheta, every active ring one vector of length
+    Nphi (the same activity rule as the FFT form)."""
+    flops = 0.0
+    th = (np.arange(grid.Ntheta) + 0.5) * math.pi / grid.Ntheta
+    f_th, f_ph = tc_slice_products(2 * grid.Ntheta), tc_slice_products(grid.Nphi)
+    for v in range(grid.nvars):
+        for i in range(grid.Nr):
+            lm = max(grid.floor, 2 * grid.r[i] / grid.dr_min * grid.L[v])
+            gauss = grid.kind[v] == W.GAUSS
+            if gauss or lm < grid.Ntheta:
+                flops += grid.Nphi // 2 * f_th
+            mm = np.maximum(grid.floor, 2 * grid.r[i] / grid.dr_min * np.sin(th) * grid.L[v])
+            nact = grid.Ntheta if gauss else int((mm < grid.Nphi / 2).sum())
+            flops += nact * f_ph
     return flops
 
 
@@ -424,9 +451,15 @@ def main():
                                    "2.07 GHz / 8.8 FP32 instructions per FP64-equivalent flop",
                     "kernel": "shell_kernel<DF>", "flops_per_launch": flops}
         else:
-            roof = {"bound": "hbm", "achieved": hbm_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": hbm_gbs / peaks["hbm_gbs"], "traffic": traffic,
-                    "peak_source": f"hbm_gbs of {src}", "bytes_per_launch": bytes_per_launch}
+            tc_flops = tc_tensor_flops(g)
+            tc_tflops = tc_flops / avg_kernel_s / 1e12
+            peak = peaks["bf16_tflops"]
+            roof = {"bound": "tensor", "achieved": tc_tflops, "peak": peak, "unit": "TFLOP/s",
+                    "frac": tc_tflops / peak, "traffic": traffic,
+                    "peak_source": f"bf16_tflops (burst) of {src}",
+                    "kernel": "tc_pass_kernel (theta and phi launches of one application, with the copies "
+                              "of identity shells)",
+                    "flops_per_launch": tc_flops}
         line = {
             "metric": "filtered Gpoints/s (theta+phi double FFT filter, FP64 I/O)",
             "value": value, "unit": "Gpoints/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

@@ -262,6 +262,7 @@ void free_plan(sph_filter_plan_s* p) {
   cudaFree(p->d_tw_ph);
   cudaFree(p->d_status);
   cudaFree(p->d_tabs);
+  tc_free(p);
   cudaFree(p->d_stage_in);
   cudaFree(p->d_stage_out);
   for (cudaStream_t s : p->pipe)
@@ -279,6 +280,8 @@ sph_status check_io(const sph_filter_plan_s* p, const void* in, const void* out,
 }
 
 }  // namespace
+
+long double filter_value(int kind, long double al, long double lmax) { return fval(kind, al, lmax); }
 
 sph_status launch_plan(sph_filter_plan_s* p, const void* in, const void* aux, void* out, int map_in, int map_out,
                        int transpose, int is_f32, cudaStream_t stream) {
@@ -301,6 +304,17 @@ sph_status launch_plan_vars(sph_filter_plan_s* p, const void* in, const void* au
   int cur = -1;
   if (cudaGetDevice(&cur) != cudaSuccess) return SPH_ECUDA;
   if (cur != p->device && cudaSetDevice(p->device) != cudaSuccess) return SPH_ECUDA;
+  if (p->tc) {
+    // the tensor-core form implements the plain FP64 filter and its transpose only
+    if (map_in != kMapNone || map_out != kOutNone || is_f32) {
+      if (cur != p->device) cudaSetDevice(cur);
+      return SPH_EUNSUPPORTED;
+    }
+    const cudaError_t e = tc_launch(p, static_cast<const double*>(in), static_cast<double*>(out), transpose,
+                                    var_begin, var_count, (cudaStream_t)stream);
+    if (cur != p->device) cudaSetDevice(cur);
+    return e == cudaSuccess ? SPH_OK : SPH_ECUDA;
+  }
   LaunchIO io{in,        aux,    out, map_in, map_out, transpose, is_f32, ((uintptr_t)in % 16) == 0 ? 1 : 0,
               var_begin, var_count};
   cudaError_t e = !p->use_v2 ? launch_plain(*p, io, (cudaStream_t)stream)
@@ -339,7 +353,6 @@ sph_status sph_filter_plan_create(sph_filter_plan* out, int Nr, int Ntheta, int 
   }
   for (int i = 0; i < Nr; ++i)
     if (!(prm->r[i] >= 0) || !std::isfinite(prm->r[i])) return SPH_EINVAL;
-  if (prm->precision == SPH_PREC_SPLIT_TC) return SPH_EUNSUPPORTED;
 
   sph_filter_plan_s* p = new (std::nothrow) sph_filter_plan_s();
   if (!p) return SPH_ENOMEM;
@@ -394,6 +407,16 @@ sph_status sph_filter_plan_create(sph_filter_plan* out, int Nr, int Ntheta, int 
   if (st != SPH_OK) {
     free_plan(p);
     return st;
+  }
+  if (p->precision == SPH_PREC_SPLIT_TC) {
+    st = tc_setup(p);
+    if (st != SPH_OK) {
+      free_plan(p);
+      return st;
+    }
+    p->launches = 2;
+    *out = p;
+    return SPH_OK;
   }
   // the staged shell kernel when the shape fits it; otherwise the chunked FP64 kernel
   st = setup_v2(p);

@@ -132,6 +132,10 @@ cudaError_t set_shell_smem_attr(int device);
 
 }  // namespace sph
 
+namespace sph {
+struct TcPlan;
+}
+
 struct sph_filter_plan_s {
   int device = 0;
   int Nr = 0, Nth = 0, Nph = 0, nvars = 0, precision = 0;
@@ -162,6 +166,9 @@ struct sph_filter_plan_s {
   double2* d_tw_ph = nullptr;
   unsigned* d_status = nullptr;
 
+  // split-precision tensor-core form (SPH_PREC_SPLIT_TC)
+  sph::TcPlan* tc = nullptr;
+
   // staging buffers and pipeline streams of sph_filter_apply_host (created on first use)
   double* d_stage_in = nullptr;
   double* d_stage_out = nullptr;
@@ -170,6 +177,17 @@ struct sph_filter_plan_s {
 };
 
 namespace sph {
+// Filter function f(|l|, l_max) of Sec. II.C in extended precision.
+long double filter_value(int kind, long double al, long double lmax);
+
+// Split-precision tensor-core form (tc.cu): tables at plan creation, release, and one application
+// (theta then phi pass, or the reverse for the transpose) of the fields [var_begin, var_begin +
+// var_count) from in to out (in == out allowed).
+sph_status tc_setup(sph_filter_plan_s* p);
+void tc_free(sph_filter_plan_s* p);
+cudaError_t tc_launch(sph_filter_plan_s* p, const double* in, double* out, int transpose, int var_begin,
+                      int var_count, cudaStream_t s);
+
 // Enqueue one filter application of a plan (validates pointers; see sph_filter_apply).
 sph_status launch_plan(sph_filter_plan_s* p, const void* in, const void* aux, void* out, int map_in, int map_out,
                        int transpose, int is_f32, cudaStream_t stream);

@@ -1,0 +1,153 @@
+"""Parity of the split-precision tensor-core form (SPH_PREC_SPLIT_TC) with the oracle, through the C
+ABI (GPU). The form computes only the removed part H x = x - F x from exact BF16 slice products
+(six slices per operand) and subtracts it in FP64; its target is 1e-11 in the per-field
+normalised max norm (max |y - y_ref| / max |y_ref|), against 1e-13 for the plain form."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2305_01537_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-11
+TC = 1  # SPH_PREC_SPLIT_TC
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2305_01537_gb300 import build as B
+    B.build()
+    return torch
+
+
+def field_errors(y, ref):
+    return np.array([np.abs(y[v] - ref[v]).max() / max(np.abs(ref[v]).max(), 1e-300) for v in range(ref.shape[0])])
+
+
+def oracle_of(g, x, transpose=False):
+    f = oracle.filter_T if transpose else oracle.filter
+    return f(x, g.parity, g.kind, g.L, g.r, g.dr_min, g.floor)
+
+
+def sampled_errors(y_of, ref, shells):
+    """Sampled shells against the oracle, each normalised by the largest reference value among its
+    field's sampled shells (at most the field maximum the full-field measure divides by)."""
+    fmax = {v: max(np.abs(ref[n]).max() for n, s in enumerate(shells) if s[0] == v) for v, _ in shells}
+    return np.array([np.abs(y_of(v, i) - ref[n]).max() / fmax[v] for n, (v, i) in enumerate(shells)])
+
+
+@pytest.mark.parametrize("Nr,Nth,Nph", [(3, 4, 8), (4, 8, 16), (3, 16, 32), (2, 12, 40), (3, 32, 24), (2, 5, 74),
+                                        (2, 48, 200)])
+def test_tiny_and_ragged_grids(torch_cuda, Nr, Nth, Nph):
+    """Every field class of the 28-field mix; lengths that are not powers of two, ragged GEMM tiles
+    (fewer than 128 vectors, padded K and N) and outputs split over two passes (Nphi = 200)."""
+    torch = torch_cuda
+    from paper_2305_01537_gb300 import Plan
+    g = W.grid_28(Nr, Nth, Nph)
+    x = W.band_limited_state(g, seed=Nr * 100 + Nth, mode_max=3, noise=0.05)
+    plan = Plan.from_grid(g, precision=TC)
+    xd = torch.from_numpy(x).cuda()
+    y = plan.apply(xd).cpu().numpy()
+    yt = plan.apply_adjoint(xd).cpu().numpy()
+    assert plan.sync_status() == 0
+    assert field_errors(y, oracle_of(g, x)).max() <= TOL
+    assert field_errors(yt, oracle_of(g, x, True)).max() <= TOL
+
+
+@pytest.mark.parametrize("Nth,Nph", [(64, 128), (128, 256)])
+def test_28_field_mix_headline_shapes(torch_cuda, Nth, Nph):
+    """The shell shapes of the 128 x 64 x 128 and 256 x 128 x 256 workloads at radii inside and
+    past the cutoff thresholds (many tiles; two shells per tile for Nphi = 128)."""
+    torch = torch_cuda
+    from paper_2305_01537_gb300 import Plan
+    g = W.grid_28(3, Nth, Nph)
+    g.r = np.array([0.5, 7.5, 40.5])
+    x = W.band_limited_state(g, seed=77, mode_max=Nph // 8, noise=0.05)
+    plan = Plan.from_grid(g, precision=TC)
+    xd = torch.from_numpy(x).cuda()
+    y = plan.apply(xd).cpu().numpy()
+    yt = plan.apply_adjoint(xd).cpu().numpy()
+    assert plan.sync_status() == 0
+    err = field_errors(y, oracle_of(g, x))
+    assert err.max() <= TOL, err
+    assert field_errors(yt, oracle_of(g, x, True)).max() <= TOL
+
+
+def test_in_place_and_random_input(torch_cuda):
+    torch = torch_cuda
+    from paper_2305_01537_gb300 import Plan
+    g = W.grid_28(4, 16, 32)
+    x = W.random_state(g.shape, 12)
+    plan = Plan.from_grid(g, precision=TC)
+    xd = torch.from_numpy(x).cuda()
+    plan.apply(xd, out=xd)
+    assert plan.sync_status() == 0
+    assert field_errors(xd.cpu().numpy(), oracle_of(g, x)).max() <= TOL
+
+
+def test_host_entry_and_scaled_fields(torch_cuda):
+    """Fields of very different magnitudes (1e-30 .. 1e30): the slicing scale is per vector."""
+    torch = torch_cuda
+    from paper_2305_01537_gb300 import Plan
+    g = W.grid_28(3, 8, 16)
+    x = W.band_limited_state(g, seed=5, mode_max=3, noise=0.05)
+    x *= np.logspace(-30, 30, 28)[:, None, None, None]
+    plan = Plan.from_grid(g, precision=TC)
+    xh = torch.from_numpy(x).pin_memory()
+    out = torch.empty_like(xh).pin_memory()
+    plan.apply_host(xh, out)
+    torch.cuda.synchronize()
+    assert plan.sync_status() == 0
+    assert field_errors(out.numpy(), oracle_of(g, x)).max() <= TOL
+
+
+def test_unsupported_calls(torch_cuda):
+    torch = torch_cuda
+    from paper_2305_01537_gb300 import Plan, SphFilterError
+    g = W.grid_28(2, 8, 16)
+    plan = Plan.from_grid(g, precision=TC)
+    z = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+    with pytest.raises(SphFilterError):
+        plan.apply_tanh(z)
+    with pytest.raises(SphFilterError):
+        plan.apply(z.float())
+    with pytest.raises(SphFilterError):  # vectors longer than 256
+        Plan.from_grid(W.grid_28(2, 8, 512), precision=TC)
+
+
+def test_full_state_256x128x256_sampled(torch_cuda):
+    """The 28-field Nr=256, Ntheta=128, Nphi=256 workload at full size, in the launch configuration
+    the benchmark times; the oracle checks sampled shells of every field class."""
+    torch = torch_cuda
+    from paper_2305_01537_gb300 import Plan
+    wl = W.full_state_256x128x256()
+    g = wl.grids[0]
+    x = wl.state()
+    plan = Plan.from_grid(g, precision=TC)
+    xd = torch.from_numpy(x).cuda()
+    y = plan.apply(xd)
+    torch.cuda.synchronize()
+    assert plan.sync_status() == 0
+    del xd
+    shells = [(v, i) for v in (0, 14, 18, 20, 24, 26) for i in (0, 5, 21, 255)]
+    ref = oracle.filter_shells(x, shells, g.parity, g.kind, g.L, g.r, g.dr_min, g.floor)
+    err = sampled_errors(lambda v, i: y[v, i].cpu().numpy(), ref, shells)
+    assert err.max() <= TOL, shells[int(err.argmax())]
+
+
+def test_full_state_128x64x128_sampled(torch_cuda):
+    torch = torch_cuda
+    from paper_2305_01537_gb300 import Plan
+    wl = W.full_state_128x64x128()
+    g = wl.grids[0]
+    x = wl.state()
+    plan = Plan.from_grid(g, precision=TC)
+    y = plan.apply(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert plan.sync_status() == 0
+    shells = [(v, i) for v in (0, 13, 14, 19, 23, 25, 27) for i in (0, 3, 17, 127)]
+    ref = oracle.filter_shells(x, shells, g.parity, g.kind, g.L, g.r, g.dr_min, g.floor)
+    err = sampled_errors(lambda v, i: y[v, i], ref, shells)
+    assert err.max() <= TOL, shells[int(err.argmax())]
