@@ -49,7 +49,7 @@ constexpr int kMaxL = 256;
 constexpr uint32_t kStageA = kS * kM * kKC * 2;       // 49152 bytes
 constexpr uint32_t kStageB = kS * kMaxNPh * kKC * 2;  // 30720 bytes
 constexpr uint32_t kStage = kStageA + kStageB;        // 79872 bytes (a multiple of 1024)
-constexpr int kThr = 256;          // threads per CTA
+constexpr int kThr = 512;          // threads per CTA (4 warps per tensor-memory lane quarter)
 constexpr long long kWaitLimit = 1LL << 20;           // bounded mbarrier polls (seconds at most)
 
 enum Op { kCF = 0, kSF = 1, kCI = 2, kSI = 3 };
@@ -76,7 +76,7 @@ struct TcArgs {
   double* dst;              // state written (may equal src); only active vectors are written
   const int* list;          // theta: active shells v*Nr+i; phi: active rings (v*Nr+i)*Nth+j
   long long nvec;           // theta: entries * Nph/2; phi: entries
-  const double* h;          // 1 - f: theta [ncls][Nr][Nth+1]; phi [ncls][Nr][Nth][Nph/2+1]
+  const float2* h;          // 1 - f as FP32 pairs: theta [ncls][Nr][Nth+1]; phi [ncls][Nr][Nth][Nph/2+1]
   const VarInfo* var;
   OpTab op[4];
   int Ef, Ei;               // operator scales: forward (CF, SF) = 2^Ef * slices, inverse 2^Ei
@@ -86,7 +86,7 @@ struct TcArgs {
 
 struct Row {
   size_t base;              // offset of element 0 of the vector in the state
-  const double* h;          // multipliers of the vector's modes 0 .. H
+  const float2* h;          // multipliers of the vector's modes 0 .. H
   int neg;                  // theta: second half carries the parity sign -1
   int ex;                   // input scale exponent
   int ey;                   // spectrum scale exponent
@@ -222,12 +222,19 @@ __device__ __forceinline__ size_t elem(const TcArgs& A, size_t base, int q) {
     return q < A.Nth ? base + (size_t)q * A.Nph : base + (size_t)(2 * A.Nth - 1 - q) * A.Nph + A.Nph / 2;
   return base + q;
 }
-__device__ __forceinline__ double load_c(const TcArgs& A, const Row& R, int q) {
-  const double v = A.src[elem(A, R.base, q)];
-  return (R.neg && q >= A.Nth) ? -v : v;
+// The parity sign of element q applies (theta circles of odd fields, second half).
+__device__ __forceinline__ bool flip(const TcArgs& A, const Row& R, int q) { return R.neg && q >= A.Nth; }
+// Element q as a fixed-point integer at scale E (the sign applied to the integer).
+__device__ __forceinline__ long long load_fx(const TcArgs& A, const Row& R, int q, int E) {
+  const long long t = fx64(A.src[elem(A, R.base, q)], E);
+  return flip(A, R, q) ? -t : t;
 }
-__device__ __forceinline__ void store_c(const TcArgs& A, const Row& R, int q, double v) {
-  A.dst[elem(A, R.base, q)] = (R.neg && q >= A.Nth) ? -v : v;
+// Writes c_q - hc for element q: the stored value is s (c_q - hc) = x_stored - s hc with s the
+// parity sign, so the sign goes on hc with an integer operation and one FP64 subtraction remains.
+__device__ __forceinline__ void update_c(const TcArgs& A, const Row& R, int q, double hc) {
+  const size_t o = elem(A, R.base, q);
+  const long long sb = flip(A, R, q) ? (long long)0x8000000000000000ULL : 0LL;
+  A.dst[o] = A.src[o] - __longlong_as_double(__double_as_longlong(hc) ^ sb);
 }
 
 struct Ctx {
@@ -256,8 +263,8 @@ __device__ __forceinline__ void gather8(Ctx& C, int op, int r, int k0, long long
     for (int i = 0; i < 8; ++i) {
       const int q = k0 + i;
       if (q <= H) {
-        long long u = fx64(load_c(A, R, q), R.ex);
-        if (q != 0 && q != H) u += fx64(load_c(A, R, L - q), R.ex);
+        long long u = load_fx(A, R, q, R.ex);
+        if (q != 0 && q != H) u += load_fx(A, R, L - q, R.ex);
         t[i] = u;
         *nyq += (q & 1) ? -u : u;  // cos(pi q)
       }
@@ -266,7 +273,7 @@ __device__ __forceinline__ void gather8(Ctx& C, int op, int r, int k0, long long
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int q = k0 + i + 1;
-      if (q < H) t[i] = fx64(load_c(A, R, q), R.ex) - fx64(load_c(A, R, L - q), R.ex);
+      if (q < H) t[i] = load_fx(A, R, q, R.ex) - load_fx(A, R, L - q, R.ex);
     }
   } else {
     const float2* src = op == kCI ? C.Yc + (size_t)r * (H + 1) : C.Ys + (size_t)r * (H - 1);
@@ -378,7 +385,7 @@ __device__ __forceinline__ void tmem_ld6(uint32_t taddr, int NPh, float d[kAcc][
 }
 
 // Epilogue of one pass of a GEMM. Warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (one vector
-// each) and half w / 4 of the pass's output columns.
+// each) and the 8-column groups w / 4, w / 4 + 4, ... of the pass's output columns.
 __device__ void epilogue(Ctx& C, int op, int half) {
   const TcArgs& A = C.A;
   const OpTab& T = A.op[op];
@@ -388,10 +395,10 @@ __device__ void epilogue(Ctx& C, int op, int half) {
   const Row& R = C.S.row[r];
   const int L = A.L, H = L / 2;
   const uint32_t taddr = C.tmem + ((uint32_t)(32 * quarter) << 16);
-  const int c_begin = side * (T.NPh / 2), c_end = c_begin + T.NPh / 2;
+  const int c_begin = side * 8, c_end = T.NPh, c_step = (kThr / 128) * 8;
   const int S2 = R.ex + A.Ef + R.ey + A.Ei;  // output scale of the inverse GEMMs
   int emax = 0;
-  for (int c0 = c_begin; c0 < c_end; c0 += 8) {
+  for (int c0 = c_begin; c0 < c_end; c0 += c_step) {
     float d[kAcc][8];
     tmem_ld6(taddr + (uint32_t)c0, T.NPh, d);
     if (!R.valid) continue;
@@ -405,14 +412,15 @@ __device__ void epilogue(Ctx& C, int op, int half) {
       const df z = combine6(dd);
       if (op == kCF || op == kSF) {
         const int m = op == kCF ? n : n + 1;
-        const df y = df_mul(z, df_from_double(R.h[m], 0));
+        const float2 hm = R.h[m];
+        const df y = df_mul(z, df{hm.x, hm.y});
         const float2 yv = make_float2(y.hi, y.lo);
         if (op == kCF) C.Yc[(size_t)r * (H + 1) + n] = yv;
         else C.Ys[(size_t)r * (H - 1) + n] = yv;
         emax = max(emax, (__float_as_int(y.hi) >> 23) & 0xFF);
       } else if (op == kCI) {
         const int k = n;
-        if (k == 0) store_c(A, R, 0, load_c(A, R, 0) - df_to_double(z, S2));
+        if (k == 0) update_c(A, R, 0, df_to_double(z, S2));
         else C.Ye[(size_t)r * (H + 1) + k] = make_float2(z.hi, z.lo);  // read by the SI epilogue
       } else {
         const int k = n + 1;
@@ -420,8 +428,8 @@ __device__ void epilogue(Ctx& C, int op, int half) {
         const df ye{e.x, e.y};
         const double hp = df_to_double(df_add(ye, z), S2);
         const double hm = df_to_double(df_add(ye, df_neg(z)), S2);
-        store_c(A, R, k, load_c(A, R, k) - hp);
-        store_c(A, R, L - k, load_c(A, R, L - k) - hm);
+        update_c(A, R, k, hp);
+        update_c(A, R, L - k, hm);
       }
     }
   }
@@ -431,13 +439,14 @@ __device__ void epilogue(Ctx& C, int op, int half) {
     if (op == kCF) {
       // X_c[H] in GEMM units: sum 2^-48 (data scale) 2^-Ef (operator scale)
       const df z = df_from_double((double)sum, 48 + A.Ef);
-      const df y = df_mul(z, df_from_double(R.h[H], 0));
+      const float2 hH = R.h[H];
+      const df y = df_mul(z, df{hH.x, hH.y});
       C.Yc[(size_t)r * (H + 1) + H] = make_float2(y.hi, y.lo);
       emax = max(emax, (__float_as_int(y.hi) >> 23) & 0xFF);
     } else {
       // y_e[H] = (1/L) sum_m w_m cos(pi m) h_m X_c[m], in GEMM units 2^-48 2^-Ei
       const df z = df_from_double((double)sum / (double)L, 48 + A.Ei);
-      store_c(A, R, H, load_c(A, R, H) - df_to_double(z, S2));
+      update_c(A, R, H, df_to_double(z, S2));
     }
   }
   if (op == kCF || op == kSF) atomicMax(&C.S.emax[r], emax);
@@ -500,13 +509,13 @@ __global__ void __launch_bounds__(kThr, 1) tc_pass_kernel(TcArgs A) {
       S.nyq[tid] = 0ull;
     }
     __syncthreads();
-    // input scale: largest FP64 exponent over the vector (two threads per vector)
+    // input scale: largest FP64 exponent over the vector (kThr / 128 threads per vector)
     {
-      const int r = tid & (kM - 1), hh = tid / kM;
+      const int r = tid & (kM - 1), part = tid / kM, np = kThr / kM;
       const Row& R = S.row[r];
       int e = 0;
       if (R.valid)
-        for (int q = hh * H; q < hh * H + H; ++q)
+        for (int q = part; q < L; q += np)
           e = max(e, (int)((__double_as_longlong(A.src[elem(A, R.base, q)]) >> 52) & 0x7FF));
       atomicMax(&S.emax[r], e);
     }
@@ -598,7 +607,7 @@ struct TcPass {
   void* d_tab = nullptr;           // the four operators' slices
   tcx::OpTab op[4];
   int Ef = 0, Ei = 0;
-  double* d_h = nullptr;
+  float2* d_h = nullptr;
   int* d_list = nullptr;
   std::vector<long long> var_off;  // list entries of fields [0, v): prefix counts
   std::vector<int> copy_runs;      // theta pass: [field, first shell, shells] runs of identity shells
@@ -659,17 +668,21 @@ sph_status tc_setup(sph_filter_plan_s* p) {
   if (st != SPH_OK) return st;
   const int Nr = p->Nr, Nth = p->Nth, Nph = p->Nph, ncls = p->ncls;
   // high-pass multipliers 1 - f (Sec. II.C filter functions) and the active vectors of each pass
-  std::vector<double> hth((size_t)ncls * Nr * (Nth + 1)), hph((size_t)ncls * Nr * Nth * (Nph / 2 + 1));
+  std::vector<float2> hth((size_t)ncls * Nr * (Nth + 1)), hph((size_t)ncls * Nr * Nth * (Nph / 2 + 1));
+  auto pair = [](long double v) {
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (long double)hi));
+  };
   for (int c = 0; c < ncls; ++c)
     for (int i = 0; i < Nr; ++i) {
       const long double lm = p->h_lmax[(size_t)c * Nr + i];
       for (int l = 0; l <= Nth; ++l)
-        hth[((size_t)c * Nr + i) * (Nth + 1) + l] = (double)(1.0L - filter_value(p->cls_kind[(size_t)c], l, lm));
+        hth[((size_t)c * Nr + i) * (Nth + 1) + l] = pair(1.0L - filter_value(p->cls_kind[(size_t)c], l, lm));
       for (int j = 0; j < Nth; ++j) {
         const long double mm = p->h_mmax[((size_t)c * Nr + i) * Nth + j];
         for (int m = 0; m <= Nph / 2; ++m)
           hph[(((size_t)c * Nr + i) * Nth + j) * (Nph / 2 + 1) + m] =
-              (double)(1.0L - filter_value(p->cls_kind[(size_t)c], m, mm));
+              pair(1.0L - filter_value(p->cls_kind[(size_t)c], m, mm));
       }
     }
   std::vector<int> lth, lph;
