@@ -509,8 +509,9 @@ __global__ void __launch_bounds__(kThr, 1) tc_pass_kernel(TcArgs A) {
       S.nyq[tid] = 0ull;
     }
     __syncthreads();
-    // input scale: largest FP64 exponent over the vector (kThr / 128 threads per vector)
-    {
+    // input scale: largest FP64 exponent over the vector; lanes run along contiguous memory (the
+    // vector index for theta circles, the ring for rings)
+    if (A.pass == 0) {
       const int r = tid & (kM - 1), part = tid / kM, np = kThr / kM;
       const Row& R = S.row[r];
       int e = 0;
@@ -518,6 +519,16 @@ __global__ void __launch_bounds__(kThr, 1) tc_pass_kernel(TcArgs A) {
         for (int q = part; q < L; q += np)
           e = max(e, (int)((__double_as_longlong(A.src[elem(A, R.base, q)]) >> 52) & 0x7FF));
       atomicMax(&S.emax[r], e);
+    } else {
+      const int lane = tid & 31;
+      for (int r = warp; r < kM; r += kThr / 32) {
+        const Row& R = S.row[r];
+        int e = 0;
+        if (R.valid)
+          for (int q = lane; q < L; q += 32) e = max(e, (int)((__double_as_longlong(A.src[R.base + q]) >> 52) & 0x7FF));
+        e = __reduce_max_sync(0xffffffffu, e);
+        if (lane == 0) atomicMax(&S.emax[r], e);
+      }
     }
     __syncthreads();
     if (tid < kM) {
