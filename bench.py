@@ -42,17 +42,22 @@ DF_INSTR_PER_FLOP = 866.0 / 98.0
 DF_PEAK_TFLOPS = F32_INSTR_PER_S / DF_INSTR_PER_FLOP / 1e12
 
 
-def kernel_sources_hash() -> str:
-    """Hash of the CUDA sources, to tell whether recorded ncu counters still describe the kernel."""
-    import glob
+KERNEL_FAMILIES = {
+    # CUDA sources whose device code each kernel family compiles from
+    "plain": ["shell_kernel.cuh", "shell_inst.cu", "shell_dispatch.cu", "filter_plain.cu", "df32.h"],
+    "tc": ["tc.cu", "df32.h"],
+}
+
+
+def kernel_sources_hash(family: str) -> str:
+    """Hash of a kernel family's CUDA sources, to tell whether recorded ncu counters still describe
+    the kernel."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2305_01537_gb300", "csrc")
-    files = sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))
-                   + glob.glob(os.path.join(csrc, "*.h")))
     h = hashlib.sha256()
-    for f in files:
-        h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
+    for name in KERNEL_FAMILIES[family]:
+        h.update(name.encode())
+        with open(os.path.join(csrc, name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
@@ -437,8 +442,10 @@ def main():
         if os.path.exists(tp):
             with open(tp) as f:
                 rec = json.load(f)
-            if rec.get("kernel_sources_sha256_16") == kernel_sources_hash():
-                traffic = rec.get(f"{args.precision}:{wl.name}")
+            fam = "tc" if args.precision == "tc" else "plain"
+            frec = rec.get("families", {}).get(fam, {})
+            if frec.get("sources_sha256_16") == kernel_sources_hash(fam):
+                traffic = frec.get(f"{args.precision}:{wl.name}")
         if args.precision == "f64":
             roof = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
