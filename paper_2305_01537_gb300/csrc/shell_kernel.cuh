@@ -1017,6 +1017,7 @@ struct LayoutCl {
   uint32_t A, B, lin, ov, tw_th, tw_ph, g_th;
   int2* pairs;
   int* misc;
+  unsigned char* rowact;   // rows that a pass transforms (1) or that pass through unchanged (0)
 };
 
 // Shared memory of one CTA of a pair: A (all rows, half the columns), B (half of the rows, the other
@@ -1042,6 +1043,7 @@ __device__ LayoutCl<P> carve_cl(const ShellArgs2& A, unsigned char* base) {
   L.g_th = saddr(take(8 * (size_t)(A.Nth + 1)));
   L.pairs = reinterpret_cast<int2*>(take(sizeof(int2) * (size_t)(A.Nth / 2 + 1)));
   L.misc = reinterpret_cast<int*>(take(sizeof(int) * 4));
+  L.rowact = take((size_t)A.Nth);
   return L;
 }
 
@@ -1056,6 +1058,7 @@ size_t shell_smem_cl(const ShellArgs2& a) {
   s += up(8 * (size_t)(a.Nth + 1));
   s += up(sizeof(int2) * (size_t)(a.Nth / 2 + 1));
   s += up(sizeof(int) * 4);
+  s += up((size_t)a.Nth);
   return s;
 }
 
@@ -1085,7 +1088,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512) shell_kernel_cl
   int v, i;
   const size_t off = shell_offset(A, io, sidx, &v, &i);
   const VarInfo vi = A.var[v];
-  const int Nth = A.Nth, Nph = A.Nph, QB = Nph / 4, ldc = (int)cl_ld(A);
+  // compile-time sizes for the fixed lengths
+  const int Nth = LEN ? LEN / 2 : A.Nth, Nph = LEN ? LEN : A.Nph, QB = Nph / 4;
+  const int ldc = LEN ? LEN / 2 + 2 : (int)cl_ld(A);
   const bool fwd = io.transpose == 0;
 
   for (int n = threadIdx.x; n < 2 * Nth; n += blockDim.x)
@@ -1134,17 +1139,26 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512) shell_kernel_cl
     }
     __syncthreads();
   }
+  // rows a pass transforms: every row when the theta pass runs, else the rows of active ring pairs
+  // (the same rows on both ranks); only these are converted to pairs, the rest stay FP64
+  const double lmax = A.lmax[vi.cls * A.Nr + i];
+  const bool theta_on = vi.kind == SPH_FILTER_GAUSS || lmax < (double)Nth;
+  const uint8_t* ring_info = A.ring_info + ((size_t)vi.cls * A.Nr + i) * Nth;
+  for (int j = threadIdx.x; j < Nth; j += blockDim.x)
+    L.rowact[j] = (theta_on || ((ring_info[j] | ring_info[Nth - 1 - j]) & 1)) ? 1 : 0;
+  __syncthreads();
   unsigned emax = 0;
   if (io.map_in == kMapTanh || dfp) {
     for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
       const int jr = e / cols, c = col_of(e - jr * cols);
-      const uint32_t a = addr_of(row_of(jr), c);
+      const int j = row_of(jr);
+      const uint32_t a = addr_of(j, c);
       double x = F64::ld8(a);
       if (io.map_in == kMapTanh) {
         x = tanh(x);
         F64::st8(a, x);
       }
-      if (dfp) emax = max(emax, (unsigned)df_exp_field(x));
+      if (dfp && L.rowact[j]) emax = max(emax, (unsigned)df_exp_field(x));
     }
   }
   int E = 0;
@@ -1160,17 +1174,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512) shell_kernel_cl
     E = max(L.misc[2], (int)other) - 1023;
     for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
       const int jr = e / cols, c = col_of(e - jr * cols);
-      const uint32_t a = addr_of(row_of(jr), c);
+      const int j = row_of(jr);
+      if (!L.rowact[j]) continue;
+      const uint32_t a = addr_of(j, c);
       P::st8(a, to_real<P>(F64::ld8(a), E));
     }
   }
 
   // per-shell tables
-  const double lmax = A.lmax[vi.cls * A.Nr + i];
-  const bool theta_on = vi.kind == SPH_FILTER_GAUSS || lmax < (double)Nth;
   const size_t gth_base = ((size_t)vi.cls * A.Nr + i) * (Nth + 1);
   for (int n = threadIdx.x; n <= Nth; n += blockDim.x) P::st8(L.g_th + 8u * n, P::from_tab(A.g_th, gth_base + n));
-  const uint8_t* ring_info = A.ring_info + ((size_t)vi.cls * A.Nr + i) * Nth;
   if (threadIdx.x == 0) {
     int np = 0, gen = 0;
     const int q = Nth / 4;
@@ -1272,7 +1285,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512) shell_kernel_cl
     const bool mine = cl_mine(c, QB, r, &lc);
     if (!fwd && !mine) continue;
     const uint32_t a = mine ? L.A + (uint32_t)(j * ldc + lc) * 8u : L.B + (uint32_t)(cl_brow(j, Nth, r) * ldc + lc) * 8u;
-    double y = from_real<P>(P::ld8(a), E);
+    double y = (dfp && !L.rowact[j]) ? F64::ld8(a) : from_real<P>(P::ld8(a), E);
     const size_t o = off + (size_t)j * Nph + c;
     if (io.map_out == kOutTanhGrad) {
       const double z = io.is_f32 ? (double)static_cast<const float*>(io.aux)[o] : static_cast<const double*>(io.aux)[o];
