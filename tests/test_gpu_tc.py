@@ -151,3 +151,48 @@ def test_full_state_128x64x128_sampled(torch_cuda):
     ref = oracle.filter_shells(x, shells, g.parity, g.kind, g.L, g.r, g.dr_min, g.floor)
     err = sampled_errors(lambda v, i: y[v, i], ref, shells)
     assert err.max() <= TOL, shells[int(err.argmax())]
+
+
+def test_adjoint_identity(torch_cuda):
+    """<F x, y> = <x, F^T y> with both sides from the tensor-core form (Sec. II.C passes are
+    symmetric, so F^T runs the phi pass, then the theta pass)."""
+    torch = torch_cuda
+    from paper_2305_01537_gb300 import Plan
+    g = W.grid_28(3, 16, 32)
+    x = W.random_state(g.shape, 21)
+    y = W.random_state(g.shape, 22)
+    plan = Plan.from_grid(g, precision=TC)
+    fx = plan.apply(torch.from_numpy(x).cuda()).cpu().numpy()
+    fty = plan.apply_adjoint(torch.from_numpy(y).cuda()).cpu().numpy()
+    assert plan.sync_status() == 0
+    lhs, rhs = float((fx * y).sum()), float((x * fty).sum())
+    assert abs(lhs - rhs) <= 1e-11 * np.sqrt((x * x).sum() * (y * y).sum())
+
+
+def test_batch_and_graph_with_tensor_core_plans(torch_cuda):
+    """The batch API and its CUDA-graph replay run tensor-core plans of uneven grids exactly as the
+    single-plan calls do (same kernels on the same vectors)."""
+    torch = torch_cuda
+    from paper_2305_01537_gb300 import Batch, Plan
+    shapes = [(16, 32, 3), (32, 64, 2), (64, 128, 2), (128, 256, 1)]
+    plans, xs = [], []
+    for n, (Nth, Nph, Nr) in enumerate(shapes):
+        g = W.grid_28(Nr, Nth, Nph)
+        g.r = np.linspace(0.5, 40.5, Nr)
+        plans.append(Plan.from_grid(g, precision=TC))
+        xs.append(torch.from_numpy(W.band_limited_state(g, seed=60 + n, mode_max=4, noise=0.05)).cuda())
+    b = Batch(plans)
+    outs = [torch.empty_like(x) for x in xs]
+    b.apply(xs, outs)
+    torch.cuda.synchronize()
+    for p, x, o in zip(plans, xs, outs):
+        assert torch.equal(o, p.apply(x))
+    # three applications per graph launch: in -> out, then out -> out twice
+    outs3 = [torch.empty_like(x) for x in xs]
+    b.capture(xs, outs3, 3)
+    b.launch()
+    torch.cuda.synchronize()
+    for p, x, o in zip(plans, xs, outs3):
+        ref = p.apply(p.apply(p.apply(x)))
+        assert torch.equal(o, ref)
+    assert all(p.sync_status() == 0 for p in plans)
