@@ -850,23 +850,29 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
   for (int j = threadIdx.x; j < Nth; j += blockDim.x) L.rowact[j] = theta_on ? 1 : 0;
   const uint8_t* ring_info = A.ring_info + ((size_t)vi.cls * A.Nr + i) * Nth;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
+    // active ring pairs in ascending j, compacted by one warp (ballot + prefix count)
+    const unsigned lane = threadIdx.x;
     int np = 0, gen = 0;
-    for (int j = 0; j < (Nth + 1) / 2; ++j) {
-      const int jj = Nth - 1 - j;
-      const uint8_t a = ring_info[j], b = ring_info[jj];
-      if (!((a | b) & 1)) continue;  // bit 0: ring active
-      L.rowact[j] = L.rowact[jj] = 1;
-      if (jj == j) {
-        L.pairs[np++] = make_int2(j, -1);
-      } else {
-        const int g = (a >> 1) & 1;  // bit 1: multipliers of j and its mirror differ
-        gen |= g;
-        L.pairs[np++] = make_int2(j | (g << 30), jj);
+    for (int j0 = 0; j0 < (Nth + 1) / 2; j0 += 32) {
+      const int j = j0 + (int)lane, jj = Nth - 1 - j;
+      const bool in = j < (Nth + 1) / 2;
+      const uint8_t a = in ? ring_info[j] : 0, b = in ? ring_info[jj] : 0;
+      const bool act = ((a | b) & 1) != 0;  // bit 0: ring active
+      const int g = (a >> 1) & 1;           // bit 1: multipliers of j and its mirror differ
+      const unsigned m = __ballot_sync(0xffffffffu, act);
+      if (act) {
+        const int pos = np + __popc(m & ((1u << lane) - 1u));
+        L.rowact[j] = L.rowact[jj] = 1;
+        L.pairs[pos] = jj == j ? make_int2(j, -1) : make_int2(j | (g << 30), jj);
       }
+      gen |= __any_sync(0xffffffffu, act && jj != j && g) ? 1 : 0;
+      np += __popc(m);
     }
-    L.misc[0] = np;
-    L.misc[1] = gen;
+    if (lane == 0) {
+      L.misc[0] = np;
+      L.misc[1] = gen;
+    }
   }
   __syncthreads();
 
@@ -948,6 +954,29 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
 
   // store (streaming), with the output map; untransformed rows are still FP64
   const uint32_t sb = saddr(buf);
+  if (!io.is_f32 && io.map_out == kOutNone) {
+    // plain FP64 output: two values per 16-byte store (rows are even in length)
+    double2* dst = reinterpret_cast<double2*>(static_cast<double*>(io.out) + off);
+    const bool out16 = ((uintptr_t)dst & 15u) == 0;
+    for (int n2 = threadIdx.x; n2 < npts / 2; n2 += blockDim.x) {
+      const int n = 2 * n2, jrow = n / Nph;
+      const int o = jrow * ld + n % Nph;
+      double2 y;
+      if (dfp && !L.rowact[jrow]) {
+        y = make_double2(Sd[o], Sd[o + 1]);
+      } else {
+        y.x = from_real<P>(P::ld8(sb + 8u * o), E);
+        y.y = from_real<P>(P::ld8(sb + 8u * (o + 1)), E);
+      }
+      if (out16) {
+        __stcs(dst + n2, y);
+      } else {
+        __stcs(reinterpret_cast<double*>(dst) + n, y.x);
+        __stcs(reinterpret_cast<double*>(dst) + n + 1, y.y);
+      }
+    }
+    return;
+  }
   for (int n = threadIdx.x; n < npts; n += blockDim.x) {
     const int jrow = n / Nph;
     const int o = jrow * ld + n % Nph;
@@ -1017,7 +1046,7 @@ struct LayoutCl {
   uint32_t A, B, lin, ov, tw_th, tw_ph, g_th;
   int2* pairs;
   int* misc;
-  unsigned char* rowact;   // rows that a pass transforms (1) or that pass through unchanged (0)
+  uint32_t rowact;         // shared address of the row flags: a pass transforms row j (1) or not (0)
 };
 
 // Shared memory of one CTA of a pair: A (all rows, half the columns), B (half of the rows, the other
@@ -1043,8 +1072,14 @@ __device__ LayoutCl<P> carve_cl(const ShellArgs2& A, unsigned char* base) {
   L.g_th = saddr(take(8 * (size_t)(A.Nth + 1)));
   L.pairs = reinterpret_cast<int2*>(take(sizeof(int2) * (size_t)(A.Nth / 2 + 1)));
   L.misc = reinterpret_cast<int*>(take(sizeof(int) * 4));
-  L.rowact = take((size_t)A.Nth);
+  L.rowact = saddr(take((size_t)A.Nth));
   return L;
+}
+
+__device__ __forceinline__ bool row_on(uint32_t flags, int j) {
+  unsigned v;
+  asm volatile("ld.shared.u8 %0, [%1];" : "=r"(v) : "r"(flags + (uint32_t)j));
+  return v != 0;
 }
 
 template <class P>
@@ -1141,11 +1176,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512) shell_kernel_cl
   }
   // rows a pass transforms: every row when the theta pass runs, else the rows of active ring pairs
   // (the same rows on both ranks); only these are converted to pairs, the rest stay FP64
-  const double lmax = A.lmax[vi.cls * A.Nr + i];
-  const bool theta_on = vi.kind == SPH_FILTER_GAUSS || lmax < (double)Nth;
-  const uint8_t* ring_info = A.ring_info + ((size_t)vi.cls * A.Nr + i) * Nth;
-  for (int j = threadIdx.x; j < Nth; j += blockDim.x)
-    L.rowact[j] = (theta_on || ((ring_info[j] | ring_info[Nth - 1 - j]) & 1)) ? 1 : 0;
+  {
+    const bool th_on = vi.kind == SPH_FILTER_GAUSS || A.lmax[vi.cls * A.Nr + i] < (double)Nth;
+    const uint8_t* ri = A.ring_info + ((size_t)vi.cls * A.Nr + i) * Nth;
+    for (int j = threadIdx.x; j < Nth; j += blockDim.x)
+      asm volatile("st.shared.u8 [%0], %1;" ::"r"(L.rowact + (uint32_t)j),
+                   "r"((th_on || ((ri[j] | ri[Nth - 1 - j]) & 1)) ? 1u : 0u));
+  }
   __syncthreads();
   unsigned emax = 0;
   if (io.map_in == kMapTanh || dfp) {
@@ -1158,7 +1195,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512) shell_kernel_cl
         x = tanh(x);
         F64::st8(a, x);
       }
-      if (dfp && L.rowact[j]) emax = max(emax, (unsigned)df_exp_field(x));
+      if (dfp && row_on(L.rowact, j)) emax = max(emax, (unsigned)df_exp_field(x));
     }
   }
   int E = 0;
@@ -1175,13 +1212,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512) shell_kernel_cl
     for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
       const int jr = e / cols, c = col_of(e - jr * cols);
       const int j = row_of(jr);
-      if (!L.rowact[j]) continue;
+      if (!row_on(L.rowact, j)) continue;
       const uint32_t a = addr_of(j, c);
       P::st8(a, to_real<P>(F64::ld8(a), E));
     }
   }
 
   // per-shell tables
+  const double lmax = A.lmax[vi.cls * A.Nr + i];
+  const bool theta_on = vi.kind == SPH_FILTER_GAUSS || lmax < (double)Nth;
+  const uint8_t* ring_info = A.ring_info + ((size_t)vi.cls * A.Nr + i) * Nth;
   const size_t gth_base = ((size_t)vi.cls * A.Nr + i) * (Nth + 1);
   for (int n = threadIdx.x; n <= Nth; n += blockDim.x) P::st8(L.g_th + 8u * n, P::from_tab(A.g_th, gth_base + n));
   if (threadIdx.x == 0) {
@@ -1285,7 +1325,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512) shell_kernel_cl
     const bool mine = cl_mine(c, QB, r, &lc);
     if (!fwd && !mine) continue;
     const uint32_t a = mine ? L.A + (uint32_t)(j * ldc + lc) * 8u : L.B + (uint32_t)(cl_brow(j, Nth, r) * ldc + lc) * 8u;
-    double y = (dfp && !L.rowact[j]) ? F64::ld8(a) : from_real<P>(P::ld8(a), E);
+    double y = (dfp && !row_on(L.rowact, j)) ? F64::ld8(a) : from_real<P>(P::ld8(a), E);
     const size_t o = off + (size_t)j * Nph + c;
     if (io.map_out == kOutTanhGrad) {
       const double z = io.is_f32 ? (double)static_cast<const float*>(io.aux)[o] : static_cast<const double*>(io.aux)[o];
