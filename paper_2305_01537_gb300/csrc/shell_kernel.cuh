@@ -874,7 +874,8 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
       L.misc[1] = gen;
     }
   }
-  __syncthreads();
+  if (!io.is_f32 && io.async_ok) asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncthreads();  // tables, pair list and the shell's values are in place
 
   // input map on every value; block exponent and conversion to the working precision (in place)
   // only on the rows that are transformed: the others are stored back as they were loaded
@@ -996,6 +997,12 @@ template <class P, int LEN>
 __global__ void __launch_bounds__(512) shell_kernel(ShellArgs2 A, LaunchIO io) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Layout<P> L = carve<P>(A, smem_raw);
+  const int sidx = blockIdx.x;
+  // the shell's asynchronous copy first; the tables below are fetched while it is in flight
+  if (!io.is_f32 && io.async_ok) {
+    issue_load<LEN>(A, io, sidx, L.buf);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
 
   // twiddles and radix constants, once per CTA
   const typename P::C* twth_g = static_cast<const typename P::C*>(A.tw_th);
@@ -1006,13 +1013,6 @@ __global__ void __launch_bounds__(512) shell_kernel(ShellArgs2 A, LaunchIO io) {
   K.c8 = P::from_tab(A.consts, 0);
   K.s3 = P::from_tab(A.consts, 1);
 
-  const int sidx = blockIdx.x;
-  if (!io.is_f32 && io.async_ok) {
-    issue_load<LEN>(A, io, sidx, L.buf);
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-  }
-  __syncthreads();
   filter_shell<P, LEN>(A, io, L, L.buf, sidx, K);
 }
 
