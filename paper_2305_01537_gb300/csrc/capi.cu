@@ -538,9 +538,12 @@ sph_status sph_filter_apply_host(sph_filter_plan plan, const double* host_in, do
   if (cudaEventRecord(plan->pipe_ev[3], s) != cudaSuccess) return SPH_ECUDA;
   for (cudaStream_t ps : plan->pipe)
     if (cudaStreamWaitEvent(ps, plan->pipe_ev[3], 0) != cudaSuccess) return SPH_ECUDA;
+  // the first and the last chunk hold one field: the pipeline fills and drains faster
+  const bool taper = chunk > 1 && plan->nvars > 2;
   int k = 0;
-  for (int v0 = 0; v0 < plan->nvars; v0 += chunk, ++k) {
-    const int nv = std::min(chunk, plan->nvars - v0);
+  for (int v0 = 0, nv = 0; v0 < plan->nvars; v0 += nv, ++k) {
+    const int left = plan->nvars - v0;
+    nv = (taper && (k == 0 || left == 1)) ? 1 : std::max(1, std::min(chunk, taper ? left - 1 : left));
     cudaStream_t ps = plan->pipe[k % 3];
     const size_t off = field * v0, cnt = field * nv;
     if (cudaMemcpyAsync(plan->d_stage_in + off, host_in + off, sizeof(double) * cnt, cudaMemcpyHostToDevice, ps) !=

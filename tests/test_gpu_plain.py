@@ -170,15 +170,17 @@ def test_generic_chunked_fallback(torch_cuda):
     assert field_errors(y, oracle_of(g, x)).max() <= TOL
 
 
-# sph_filter_apply_host moves chunks of whole fields of about 16 MiB; the sizes below give several
-# chunks and a shorter last one for each kernel (field bytes -> fields per chunk -> chunks).
+# sph_filter_apply_host moves chunks of whole fields of about 16 MiB, with one-field chunks first
+# and last; the sizes below give several chunks and uneven ones for each kernel
+# (field bytes -> chunks).
 @pytest.mark.parametrize("nvars,Nr,Nth,Nph,prec", [
-    (28, 3, 8, 16, 0),        # 3 KB fields: one chunk
-    (28, 10, 64, 128, 0),     # staged kernel: 640 KiB fields, chunks of 26 + 2
+    (28, 3, 8, 16, 0),        # 3 KB fields: chunks of 1 + 26 + 1
+    (28, 10, 64, 128, 0),     # staged kernel: 640 KiB fields, 1 + 26 + 1
     (28, 10, 64, 128, 2),
-    (11, 40, 64, 128, 2),     # 2.5 MiB fields: chunks of 6 + 5
-    (9, 1500, 5, 74, 0),      # chunked fallback kernel: 4.2 MiB fields, chunks of 4 + 4 + 1
-    (5, 34, 128, 256, 2),     # cluster kernel: 8.5 MiB fields, chunks of 2 + 2 + 1
+    (11, 40, 64, 128, 2),     # 2.5 MiB fields: 1 + 6 + 3 + 1
+    (9, 1500, 5, 74, 0),      # chunked fallback kernel: 4.2 MiB fields, 1 + 4 + 3 + 1
+    (5, 34, 128, 256, 2),     # cluster kernel: 8.5 MiB fields, 1 + 2 + 1 + 1
+    (1, 2, 8, 16, 0),         # one field, one chunk
 ])
 def test_host_entry_point(torch_cuda, nvars, Nr, Nth, Nph, prec):
     """sph_filter_apply_host pipelines chunks of whole fields over three streams; every field must
