@@ -346,7 +346,8 @@ def main():
     ap.add_argument("--precision", default="f32x2", choices=["f64", "f32x2", "tc"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="state28_128x64x128",
-                    choices=["state28_128x64x128", "state28_256x128x256", "batch6_uneven", "chain8_128x64x128"])
+                    choices=["state28_128x64x128", "state28_256x128x256", "batch6_uneven", "chain8_128x64x128",
+                             "state28_32x128x256"])
     ap.add_argument("--autotune", action="store_true", help="autotune the plan's launch shape before timing")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -368,7 +369,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     prec = {"f64": SPH_PREC_F64, "f32x2": SPH_PREC_F32X2, "tc": SPH_PREC_SPLIT_TC}[args.precision]
 
-    wl = W.full_state_128x64x128() if args.workload == "state28_128x64x128" else W.full_state_256x128x256()
+    wl = {"state28_128x64x128": W.full_state_128x64x128, "state28_256x128x256": W.full_state_256x128x256,
+          "state28_32x128x256": W.state_32x128x256}[args.workload]()
     g = wl.grids[0]
     x_host = torch.from_numpy(wl.state()).pin_memory()
     x = x_host.cuda()

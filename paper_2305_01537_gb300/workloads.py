@@ -189,6 +189,13 @@ def full_state_256x128x256() -> Workload:
                     "28 mixed-parity fields, band-limited m,l<=32 + U(-0.05,0.05)")
 
 
+def state_32x128x256() -> Workload:
+    """The 128 x 256 shells of the 256 x 128 x 256 workload at its first 32 radii (r = 0.5 .. 31.5):
+    28 fields, Nr = 32, seed 2; a case small enough for detailed profiles of the 128 x 256 kernels."""
+    return Workload("state28_32x128x256", [grid_28(32, 128, 256)], [2],
+                    "28 mixed-parity fields, band-limited m,l<=32 + U(-0.05,0.05)")
+
+
 BATCH_SHAPES = [(16, 32, 64), (32, 64, 96), (48, 96, 128), (64, 128, 256), (96, 192, 384), (128, 256, 512)]
 
 
