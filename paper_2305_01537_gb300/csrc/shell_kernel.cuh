@@ -735,8 +735,9 @@ struct Layout {
   uint32_t lin;        // FFT scratch
   uint32_t ov, tw_th, tw_ph, g_th;
   int2* pairs;
-  int* misc;               // [0] pair count, [1] general flag, [2] block max exponent
+  int* misc;               // [0] pair count, [1] general flag, [2] block max exponent, [3] active rows
   unsigned char* rowact;   // rows that are transformed (1) or passed through unchanged (0)
+  unsigned short* arow;    // the transformed rows, ascending
 };
 
 // Scratch for one batch: batch_th theta sequences (2 Ntheta slots each) or batch_ph phi pairs
@@ -766,6 +767,7 @@ __device__ Layout<P> carve(const ShellArgs2& A, unsigned char* base) {
   L.pairs = reinterpret_cast<int2*>(take(sizeof(int2) * (size_t)(A.Nth / 2 + 1)));
   L.misc = reinterpret_cast<int*>(take(sizeof(int) * 4));
   L.rowact = take((size_t)A.Nth);
+  L.arow = reinterpret_cast<unsigned short*>(take(sizeof(unsigned short) * (size_t)A.Nth));
   return L;
 }
 
@@ -846,7 +848,12 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
   const bool gauss = vi.kind == SPH_FILTER_GAUSS;
   const bool theta_on = gauss || lmax < (double)Nth;
   const size_t gth_base = ((size_t)vi.cls * A.Nr + i) * (Nth + 1);
-  for (int n = threadIdx.x; n <= Nth; n += blockDim.x) P::st8(L.g_th + 8u * n, P::from_tab(A.g_th, gth_base + n));
+  // theta multipliers: 8-byte table entries copied as they are (FP64, or an FP32 pair)
+  for (int n = threadIdx.x; n <= Nth; n += blockDim.x)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(L.g_th + 8u * n),
+                 "l"(static_cast<const unsigned char*>(A.g_th) + 8 * (gth_base + n))
+                 : "memory");
+  asm volatile("cp.async.commit_group;" ::: "memory");
   for (int j = threadIdx.x; j < Nth; j += blockDim.x) L.rowact[j] = theta_on ? 1 : 0;
   const uint8_t* ring_info = A.ring_info + ((size_t)vi.cls * A.Nr + i) * Nth;
   __syncthreads();
@@ -869,27 +876,41 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
       gen |= __any_sync(0xffffffffu, act && jj != j && g) ? 1 : 0;
       np += __popc(m);
     }
+    // the transformed rows, compacted (rowact is final for this warp after the sync)
+    __syncwarp();
+    int na = 0;
+    for (int j0 = 0; j0 < Nth; j0 += 32) {
+      const int j = j0 + (int)lane;
+      const bool act = j < Nth && L.rowact[j];
+      const unsigned m = __ballot_sync(0xffffffffu, act);
+      if (act) L.arow[na + __popc(m & ((1u << lane) - 1u))] = (unsigned short)j;
+      na += __popc(m);
+    }
     if (lane == 0) {
       L.misc[0] = np;
       L.misc[1] = gen;
+      L.misc[3] = na;
     }
   }
-  if (!io.is_f32 && io.async_ok) asm volatile("cp.async.wait_group 0;" ::: "memory");
-  __syncthreads();  // tables, pair list and the shell's values are in place
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncthreads();  // tables, twiddles, pair list and the shell's values are in place
 
   // input map on every value; block exponent and conversion to the working precision (in place)
   // only on the rows that are transformed: the others are stored back as they were loaded
   unsigned emax = 0;
-  if (io.map_in == kMapTanh || dfp) {
+  const int nact = L.misc[3];
+  if (io.map_in == kMapTanh) {
     for (int n = threadIdx.x; n < npts; n += blockDim.x) {
       const int jrow = n / Nph;
       const int o = jrow * ld + n % Nph;
-      double x = Sd[o];
-      if (io.map_in == kMapTanh) {
-        x = tanh(x);
-        Sd[o] = x;
-      }
+      const double x = tanh(Sd[o]);
+      Sd[o] = x;
       if (dfp && L.rowact[jrow]) emax = max(emax, (unsigned)df_exp_field(x));
+    }
+  } else if (dfp) {
+    for (int n = threadIdx.x; n < nact * Nph; n += blockDim.x) {
+      const int o = (int)L.arow[n / Nph] * ld + n % Nph;
+      emax = max(emax, (unsigned)df_exp_field(Sd[o]));
     }
   }
   int E = 0;
@@ -901,10 +922,8 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
     __syncthreads();
     E = L.misc[2] - 1023;
     const uint32_t sb = saddr(buf);
-    for (int n = threadIdx.x; n < npts; n += blockDim.x) {
-      const int jrow = n / Nph;
-      if (!L.rowact[jrow]) continue;
-      const int o = jrow * ld + n % Nph;
+    for (int n = threadIdx.x; n < nact * Nph; n += blockDim.x) {
+      const int o = (int)L.arow[n / Nph] * ld + n % Nph;
       P::st8(sb + 8u * o, to_real<P>(Sd[o], E));
     }
   }
@@ -998,17 +1017,16 @@ __global__ void __launch_bounds__(512) shell_kernel(ShellArgs2 A, LaunchIO io) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Layout<P> L = carve<P>(A, smem_raw);
   const int sidx = blockIdx.x;
-  // the shell's asynchronous copy first; the tables below are fetched while it is in flight
-  if (!io.is_f32 && io.async_ok) {
-    issue_load<LEN>(A, io, sidx, L.buf);
-    asm volatile("cp.async.commit_group;" ::: "memory");
-  }
-
-  // twiddles and radix constants, once per CTA
+  // the shell's asynchronous copy first, then the twiddles (16-byte table entries copied as they
+  // are); the tables in filter_shell are fetched while these are in flight
+  if (!io.is_f32 && io.async_ok) issue_load<LEN>(A, io, sidx, L.buf);
   const typename P::C* twth_g = static_cast<const typename P::C*>(A.tw_th);
   const typename P::C* twph_g = static_cast<const typename P::C*>(A.tw_ph);
-  for (int n = threadIdx.x; n < 2 * A.Nth; n += blockDim.x) P::st16(L.tw_th + 16u * n, twth_g[n]);
-  for (int n = threadIdx.x; n < A.Nph; n += blockDim.x) P::st16(L.tw_ph + 16u * n, twph_g[n]);
+  for (int n = threadIdx.x; n < 2 * A.Nth; n += blockDim.x)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(L.tw_th + 16u * n), "l"(twth_g + n) : "memory");
+  for (int n = threadIdx.x; n < A.Nph; n += blockDim.x)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(L.tw_ph + 16u * n), "l"(twph_g + n) : "memory");
+  asm volatile("cp.async.commit_group;" ::: "memory");
   Consts<P> K;
   K.c8 = P::from_tab(A.consts, 0);
   K.s3 = P::from_tab(A.consts, 1);
@@ -1361,6 +1379,7 @@ size_t shell_smem(const ShellArgs2& a) {
   s += up(sizeof(int2) * (size_t)(a.Nth / 2 + 1));
   s += up(sizeof(int) * 4);
   s += up((size_t)a.Nth);
+  s += up(sizeof(unsigned short) * (size_t)a.Nth);
   return s;
 }
 
