@@ -309,8 +309,10 @@ __device__ bool gemm(Ctx& C, int op, int half) {
     const int s = (int)(G & 1u);
     unsigned char* sa = C.stage + (size_t)s * kStage;
     unsigned char* sb = sa + kStageA;
-    // stage s is free once the MMAs of chunk G - 2 are done; every thread takes the same decision
-    if (G >= 2 && !__syncthreads_and(mbar_wait(su32(&C.S.bar[s]), ((G - 2) >> 1) & 1u) ? 1 : 0)) return false;
+    // stage s is free once the MMAs of chunk G - 2 are done; each thread waits by itself (no block
+    // barrier here, so the warps that do not issue MMAs start this chunk during the issue), and a
+    // wait that runs out is acted on at the barrier below
+    const bool waited = G < 2 || mbar_wait(su32(&C.S.bar[s]), ((G - 2) >> 1) & 1u);
     // operand A: six slices of the vector data
     for (int task = tid; task < kM * (kKC / 8); task += kThr) {
       const int r = task & (kM - 1), g = task / kM;
@@ -333,8 +335,8 @@ __device__ bool gemm(Ctx& C, int op, int half) {
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
+    if (!__syncthreads_and(waited ? 1 : 0)) return false;
+    if (tid == kThr - 32) {  // lane 0 of the last warp issues the chunk's MMAs
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t a0 = su32(sa), b0 = su32(sb);
 #pragma unroll
