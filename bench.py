@@ -349,6 +349,8 @@ def main():
                     choices=["state28_128x64x128", "state28_256x128x256", "batch6_uneven", "chain8_128x64x128",
                              "state28_32x128x256"])
     ap.add_argument("--autotune", action="store_true", help="autotune the plan's launch shape before timing")
+    ap.add_argument("--inplace", action="store_true",
+                    help="filter the state in place (out = in): only the rows a pass transforms are moved")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -374,7 +376,7 @@ def main():
     g = wl.grids[0]
     x_host = torch.from_numpy(wl.state()).pin_memory()
     x = x_host.cuda()
-    y = torch.empty_like(x)
+    y = x if args.inplace else torch.empty_like(x)
     plan = Plan.from_grid(g, precision=prec)
     if args.autotune:
         plan.autotune(x, y)
@@ -478,6 +480,7 @@ def main():
             "config": {"workload": wl.name, "Nr": g.Nr, "Ntheta": g.Ntheta, "Nphi": g.Nphi, "nvars": g.nvars,
                        "precision": args.precision,
                        "l2": f"inputs ({8 * points / 1e6:.0f} MB) larger than L2; no flush",
+                       "inplace": bool(args.inplace),
                        "parallelism": f"independent shards x{world}"},
             "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": peaks["hbm_gbs"], "frac": hbm_gbs / peaks["hbm_gbs"],
                     "peak_source": src, "bytes_per_point": 16},

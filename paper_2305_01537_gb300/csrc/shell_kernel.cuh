@@ -794,6 +794,14 @@ __device__ __forceinline__ size_t shell_offset(const ShellArgs2& A, const Launch
   return ((size_t)*v * A.Nr + *i) * (size_t)A.Nth * A.Nph;
 }
 
+// In-place plain FP64 calls move only the rows a pass transforms: the others already hold their
+// result in memory. Compiled in for the 128-point length (whose register budget has room for it).
+template <int LEN>
+__device__ __forceinline__ bool in_place_sparse(const LaunchIO& io) {
+  return LEN == 128 && io.in == io.out && !io.is_f32 && io.async_ok && io.map_in == kMapNone &&
+         io.map_out == kOutNone;
+}
+
 // Start the asynchronous copy of shell s into a buffer (16-byte pieces into the padded rows). The
 // sizes are compile-time constants for the fixed lengths.
 template <int LEN>
@@ -892,6 +900,23 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
       L.misc[3] = na;
     }
   }
+  if (in_place_sparse<LEN>(io)) {
+    __syncthreads();  // the active-row list is in place
+    const int na = L.misc[3];
+    if (na == 0) {  // nothing to transform: the shell already holds its result
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      return;
+    }
+    const double* src = static_cast<const double*>(io.in) + off;
+    const uint32_t dst = saddr(buf);
+    for (int c = threadIdx.x; c < na * (Nph / 2); c += blockDim.x) {
+      const int row = (int)L.arow[c / (Nph / 2)], k2 = c % (Nph / 2);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + (uint32_t)(row * ld + 2 * k2) * 8u),
+                   "l"(src + (size_t)row * Nph + 2 * k2)
+                   : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncthreads();  // tables, twiddles, pair list and the shell's values are in place
 
@@ -974,6 +999,20 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
 
   // store (streaming), with the output map; untransformed rows are still FP64
   const uint32_t sb = saddr(buf);
+  if (in_place_sparse<LEN>(io)) {
+    // in place: only the transformed rows change
+    double2* dst = reinterpret_cast<double2*>(static_cast<double*>(io.out) + off);
+    const int na = L.misc[3];
+    for (int c = threadIdx.x; c < na * (Nph / 2); c += blockDim.x) {
+      const int jrow = (int)L.arow[c / (Nph / 2)], k = 2 * (c % (Nph / 2));
+      const int o = jrow * ld + k;
+      double2 y;
+      y.x = from_real<P>(P::ld8(sb + 8u * o), E);
+      y.y = from_real<P>(P::ld8(sb + 8u * (o + 1)), E);
+      __stcs(dst + (jrow * Nph + k) / 2, y);
+    }
+    return;
+  }
   if (!io.is_f32 && io.map_out == kOutNone) {
     // plain FP64 output: two values per 16-byte store (rows are even in length)
     double2* dst = reinterpret_cast<double2*>(static_cast<double*>(io.out) + off);
@@ -1018,8 +1057,9 @@ __global__ void __launch_bounds__(512) shell_kernel(ShellArgs2 A, LaunchIO io) {
   const Layout<P> L = carve<P>(A, smem_raw);
   const int sidx = blockIdx.x;
   // the shell's asynchronous copy first, then the twiddles (16-byte table entries copied as they
-  // are); the tables in filter_shell are fetched while these are in flight
-  if (!io.is_f32 && io.async_ok) issue_load<LEN>(A, io, sidx, L.buf);
+  // are); the tables in filter_shell are fetched while these are in flight. An in-place call
+  // copies only the rows a pass transforms, once filter_shell knows them.
+  if (!io.is_f32 && io.async_ok && !in_place_sparse<LEN>(io)) issue_load<LEN>(A, io, sidx, L.buf);
   const typename P::C* twth_g = static_cast<const typename P::C*>(A.tw_th);
   const typename P::C* twph_g = static_cast<const typename P::C*>(A.tw_ph);
   for (int n = threadIdx.x; n < 2 * A.Nth; n += blockDim.x)

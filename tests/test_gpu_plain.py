@@ -220,3 +220,22 @@ def test_alias_and_errors(torch_cuda):
     assert e.value.status == 6
     with pytest.raises(SphFilterError):
         Plan(2, 8, 15, [0], [0], [3.0], [0.5, 1.5])
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_in_place_moves_only_transformed_rows(torch_cuda, prec):
+    """In-place calls on 64 x 128 shells load and store only the rows a pass transforms (the rest
+    already hold their result); the output must equal the out-of-place call's bit for bit, also
+    for shells with nothing to transform (exp filter with an enormous L)."""
+    torch = torch_cuda
+    from paper_2305_01537_gb300 import Plan
+    g = W.grid_28(6, 64, 128)
+    g.r = np.array([0.5, 3.5, 10.5, 40.5, 90.5, 127.5])
+    x = torch.from_numpy(W.band_limited_state(g, seed=91, mode_max=8, noise=0.05)).cuda()
+    for grid in (g, W.Grid(6, 64, 128, g.parity, [0] * 28, [1e6] * 28, g.r)):
+        plan = Plan.from_grid(grid, precision=prec)
+        ref = plan.apply(x)
+        y = x.clone()
+        plan.apply(y, out=y)
+        assert plan.sync_status() == 0
+        assert torch.equal(y, ref)
