@@ -81,6 +81,8 @@ struct TcArgs {
   OpTab op[4];
   int Ef, Ei;               // operator scales: forward (CF, SF) = 2^Ef * slices, inverse 2^Ei
   float2* scratch;          // per CTA: Yc [kM][H+1], Ys [kM][H-1], ye [kM][H+1]
+  uint4* akeep;             // per CTA: the A stages of a GEMM's first output half, [KP / kKC][kStageA / 16]
+  int akeep_chunks;         // chunks per CTA in akeep (0 when no GEMM has two output halves)
   unsigned* status;
 };
 
@@ -245,6 +247,7 @@ struct Ctx {
   float2* Yc;   // [kM][H+1]: h X_c[m], m = 0 .. H
   float2* Ys;   // [kM][H-1]: h X_s[m + 1]
   float2* Ye;   // [kM][H+1]: y_e[k]
+  uint4* akeep; // this CTA's copies of the first half's A stages
   unsigned G;   // chunks issued so far by this CTA
 };
 
@@ -313,17 +316,26 @@ __device__ bool gemm(Ctx& C, int op, int half) {
     // barrier here, so the warps that do not issue MMAs start this chunk during the issue), and a
     // wait that runs out is acted on at the barrier below
     const bool waited = G < 2 || mbar_wait(su32(&C.S.bar[s]), ((G - 2) >> 1) & 1u);
-    // operand A: six slices of the vector data
-    for (int task = tid; task < kM * (kKC / 8); task += kThr) {
-      const int r = task & (kM - 1), g = task / kM;
-      long long t[8], nyq;
-      gather8(C, op, r, kc * kKC + g * 8, t, &nyq);
-      if (half == 0 && nyq != 0) atomicAdd(&C.S.nyq[r], (unsigned long long)nyq);
-      uint4 w[kS];
-      slice8(t, w);
+    // operand A: six slices of the vector data. A GEMM with two output halves produces them in
+    // its first half and keeps a copy; the second half copies the stage back instead.
+    uint4* keep = T.nh > 1 ? C.akeep + (size_t)kc * (kStageA / 16) : nullptr;
+    if (half == 0) {
+      for (int task = tid; task < kM * (kKC / 8); task += kThr) {
+        const int r = task & (kM - 1), g = task / kM;
+        long long t[8], nyq;
+        gather8(C, op, r, kc * kKC + g * 8, t, &nyq);
+        if (nyq != 0) atomicAdd(&C.S.nyq[r], (unsigned long long)nyq);
+        uint4 w[kS];
+        slice8(t, w);
 #pragma unroll
-      for (int a = 0; a < kS; ++a)
-        *reinterpret_cast<uint4*>(sa + (size_t)a * kM * kKC * 2 + 2 * kmaj_elem(r, g * 8)) = w[a];
+        for (int a = 0; a < kS; ++a) {
+          const uint32_t o = a * kM * kKC * 2 + 2 * kmaj_elem(r, g * 8);
+          *reinterpret_cast<uint4*>(sa + o) = w[a];
+          if (keep) keep[o / 16] = w[a];
+        }
+      }
+    } else {
+      for (int i = tid; i < (int)(kStageA / 16); i += kThr) reinterpret_cast<uint4*>(sa)[i] = keep[i];
     }
     // operand B: the chunk's six operator slices, rows of this half (contiguous 8-row groups)
     {
@@ -474,10 +486,11 @@ __global__ void __launch_bounds__(kThr, 1) tc_pass_kernel(TcArgs A) {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  Ctx C{A, S, smem, S.tslot, nullptr, nullptr, nullptr, 0u};
+  Ctx C{A, S, smem, S.tslot, nullptr, nullptr, nullptr, nullptr, 0u};
   C.Yc = A.scratch + (size_t)kM * (3 * H + 1) * blockIdx.x;
   C.Ys = C.Yc + (size_t)kM * (H + 1);
   C.Ye = C.Ys + (size_t)kM * (H - 1);
+  C.akeep = A.akeep + (size_t)A.akeep_chunks * (kStageA / 16) * blockIdx.x;
   const long long ntiles = (A.nvec + kM - 1) / kM;
   bool ok = true;
   for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
@@ -629,6 +642,8 @@ struct TcPass {
 struct TcPlan {
   TcPass pass[2];
   float2* d_scratch = nullptr;
+  uint4* d_akeep = nullptr;
+  int akeep_chunks = 0;
   int nsm = 0;
 };
 
@@ -744,6 +759,13 @@ sph_status tc_setup(sph_filter_plan_s* p) {
   const int Hmax = std::max(Lth, Lph) / 2;
   const size_t per_cta = (size_t)tcx::kM * (3 * Hmax + 1);
   if (cudaMalloc((void**)&T->d_scratch, per_cta * T->nsm * sizeof(float2)) != cudaSuccess) return SPH_ENOMEM;
+  // kept A stages for GEMMs whose outputs take two passes of the K loop
+  for (int q = 0; q < 2; ++q)
+    for (int o = 0; o < 4; ++o)
+      if (T->pass[q].op[o].nh > 1) T->akeep_chunks = std::max(T->akeep_chunks, T->pass[q].op[o].KP / tcx::kKC);
+  if (T->akeep_chunks > 0 &&
+      cudaMalloc((void**)&T->d_akeep, (size_t)T->akeep_chunks * tcx::kStageA * T->nsm) != cudaSuccess)
+    return SPH_ENOMEM;
   if (cudaFuncSetAttribute(tcx::tc_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcx::kSmemBytes) !=
       cudaSuccess)
     return SPH_ECUDA;
@@ -759,6 +781,7 @@ void tc_free(sph_filter_plan_s* p) {
     cudaFree(P.d_list);
   }
   cudaFree(T->d_scratch);
+  cudaFree(T->d_akeep);
   delete T;
   p->tc = nullptr;
 }
@@ -786,6 +809,8 @@ cudaError_t launch_pass(sph_filter_plan_s* p, int q, const double* src, double* 
   a.Ef = P.Ef;
   a.Ei = P.Ei;
   a.scratch = T->d_scratch;
+  a.akeep = T->d_akeep;
+  a.akeep_chunks = T->akeep_chunks;
   a.status = p->d_status;
   const long long ntiles = (a.nvec + tcx::kM - 1) / tcx::kM;
   const int grid = (int)std::min<long long>(ntiles, T->nsm);
