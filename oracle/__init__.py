@@ -23,7 +23,7 @@ _LIBS = {"f64": os.path.join(_HERE, "liboracle_f64.so"), "ld": os.path.join(_HER
 _lock = threading.Lock()
 _loaded: dict = {}
 
-KIND_EXP, KIND_GAUSS, KIND_SHARP = 0, 1, 2
+KIND_EXP, KIND_GAUSS, KIND_SHARP, KIND_HYBRID = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> None:
@@ -50,11 +50,15 @@ def _lib(variant: str = "f64"):
             D = ctypes.c_double
             for name in ("filter", "filter_T"):
                 fn = getattr(lib, pre + name)
-                fn.argtypes = [I, I, I, I, P, P, P, P, D, D, P, P]
+                fn.argtypes = [I, I, I, I, P, P, P, P, D, D, D, P, P]
                 fn.restype = I
             fn = getattr(lib, pre + "single_pass")
-            fn.argtypes = [I, I, I, I, P, P, P, P, D, D, P, P, I]
+            fn.argtypes = [I, I, I, I, P, P, P, P, D, D, D, P, P, I]
             fn.restype = I
+            getattr(lib, pre + "detect").argtypes = [I, I, I, D, P, P, P]
+            getattr(lib, pre + "detect").restype = I
+            getattr(lib, pre + "jameson_fires").argtypes = [D, D, D, D]
+            getattr(lib, pre + "jameson_fires").restype = I
             getattr(lib, pre + "filter_value").argtypes = [I, D, D]
             getattr(lib, pre + "filter_value").restype = D
             getattr(lib, pre + "lmax").argtypes = [D, D, D, D]
@@ -81,35 +85,58 @@ def _prep(x, parity, kind, L, r):
     return x, parity, kind, L, r
 
 
-def _call(name, x, parity, kind, L, r, dr_min, floor, variant, extra=()):
+def _call(name, x, parity, kind, L, r, dr_min, floor, variant, eps, extra=()):
     x, parity, kind, L, r = _prep(x, parity, kind, L, r)
     lib, pre = _lib(variant)
     out = np.empty_like(x)
     nvars, Nr, Nth, Nph = x.shape
     rc = getattr(lib, pre + name)(Nr, Nth, Nph, nvars, parity.ctypes.data, kind.ctypes.data,
-                                  L.ctypes.data, r.ctypes.data, float(dr_min), float(floor),
+                                  L.ctypes.data, r.ctypes.data, float(dr_min), float(floor), float(eps),
                                   x.ctypes.data, out.ctypes.data, *extra)
     if rc != 0:
         raise ValueError(f"oracle rejected the arguments of {name}")
     return out
 
 
-def filter(x, parity, kind, L, r, dr_min=1.0, floor=2.0, variant="f64"):
-    """The double filter F: theta pass on the double-covered circles, then phi pass on the rings."""
-    return _call("filter", x, parity, kind, L, r, dr_min, floor, variant)
+def filter(x, parity, kind, L, r, dr_min=1.0, floor=2.0, variant="f64", eps=0.0):
+    """The double filter F: theta pass on the double-covered circles, then phi pass on the rings.
+    eps: the epsilon of Jameson's detector for hybrid fields (kind 3)."""
+    return _call("filter", x, parity, kind, L, r, dr_min, floor, variant, eps)
 
 
-def filter_T(x, parity, kind, L, r, dr_min=1.0, floor=2.0, variant="f64"):
-    """The transpose F^T: phi pass, then theta pass (each pass is real symmetric)."""
-    return _call("filter_T", x, parity, kind, L, r, dr_min, floor, variant)
+def filter_T(x, parity, kind, L, r, dr_min=1.0, floor=2.0, variant="f64", eps=0.0):
+    """The transpose F^T: phi pass, then theta pass (each pass is real symmetric). Not defined for
+    hybrid fields (the switch is nonlinear)."""
+    return _call("filter_T", x, parity, kind, L, r, dr_min, floor, variant, eps)
 
 
-def theta_pass(x, parity, kind, L, r, dr_min=1.0, floor=2.0, variant="f64"):
-    return _call("single_pass", x, parity, kind, L, r, dr_min, floor, variant, (1,))
+def theta_pass(x, parity, kind, L, r, dr_min=1.0, floor=2.0, variant="f64", eps=0.0):
+    return _call("single_pass", x, parity, kind, L, r, dr_min, floor, variant, eps, (1,))
 
 
-def phi_pass(x, parity, kind, L, r, dr_min=1.0, floor=2.0, variant="f64"):
-    return _call("single_pass", x, parity, kind, L, r, dr_min, floor, variant, (2,))
+def phi_pass(x, parity, kind, L, r, dr_min=1.0, floor=2.0, variant="f64", eps=0.0):
+    return _call("single_pass", x, parity, kind, L, r, dr_min, floor, variant, eps, (2,))
+
+
+def detect(shell, parity: int, eps: float):
+    """Jameson detector flags of one shell [Ntheta, Nphi] (Sec. II.C hybrid filter): (circ, ring),
+    circ[k] for the theta circles k < Nphi/2, ring[j] for the phi rings, as bool arrays."""
+    shell = np.ascontiguousarray(shell, dtype=np.float64)
+    Nth, Nph = shell.shape
+    circ = np.zeros(Nph // 2, dtype=np.uint8)
+    ring = np.zeros(Nth, dtype=np.uint8)
+    lib, pre = _lib("f64")
+    rc = getattr(lib, pre + "detect")(Nth, Nph, int(parity), float(eps), shell.ctypes.data, circ.ctypes.data,
+                                      ring.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments of detect")
+    return circ.astype(bool), ring.astype(bool)
+
+
+def jameson_fires(a: float, b: float, c: float, eps: float) -> bool:
+    """sigma >= 0.95 for one cell u_i = b with neighbours a, c."""
+    lib, pre = _lib("f64")
+    return bool(getattr(lib, pre + "jameson_fires")(float(a), float(b), float(c), float(eps)))
 
 
 def filter_value(kind: int, l: float, lmax: float, variant="f64") -> float:
@@ -138,7 +165,7 @@ def set_threads(n: int) -> None:
         getattr(lib, pre + "set_threads")(int(n))
 
 
-def filter_shells(x, shells, parity, kind, L, r, dr_min=1.0, floor=2.0, transpose=False):
+def filter_shells(x, shells, parity, kind, L, r, dr_min=1.0, floor=2.0, transpose=False, eps=0.0):
     """Filter only the listed (v, i) shells of a state; returns an array [len(shells), Ntheta, Nphi].
 
     Each shell is independent, so this is the oracle evaluated one shell at a time: used to check
@@ -152,5 +179,5 @@ def filter_shells(x, shells, parity, kind, L, r, dr_min=1.0, floor=2.0, transpos
     fn = filter_T if transpose else filter
     for (v, i) in shells:
         s = np.ascontiguousarray(x[v, i][None, None], dtype=np.float64)
-        out.append(fn(s, parity[v:v + 1], kind[v:v + 1], L[v:v + 1], r[i:i + 1], dr_min, floor)[0, 0])
+        out.append(fn(s, parity[v:v + 1], kind[v:v + 1], L[v:v + 1], r[i:i + 1], dr_min, floor, eps=eps)[0, 0])
     return np.stack(out)

@@ -27,6 +27,17 @@
  *    floor "2" is a parameter whose default is 2.
  *  - Filter functions act on |l| for every signed frequency in (-N/2, N/2]; the Nyquist mode
  *    gets f(N/2).
+ *  - Hybrid filter (Sec. II.C, the exponential/Gaussian switch by Jameson's shock detector): each
+ *    theta circle and each phi ring of a hybrid field takes the Gaussian filter if some cell of it
+ *    has sigma >= 0.95, else the exponential filter. Both detectors read the field as it enters the
+ *    filter (before the theta pass). The theta detector walks the double-covered circle (the
+ *    neighbours of a cell next to a pole are across the pole, with the parity sign); the phi
+ *    detector walks the periodic ring. sigma is evaluated in double precision in both builds as
+ *        num = |(u[i-1] + u[i+1]) - 2 u[i]|,  den = ((|u[i-1]| + |u[i+1]|) + 2 |u[i]|) + eps,
+ *        fire  <=>  num / den >= 0.95,
+ *    which is the paper's ratio with the two neighbours summed first (the result then does not
+ *    depend on the direction in which a circle is walked). eps is the caller's parameter. The
+ *    switch is nonlinear, so the transpose is not defined for hybrid fields.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -55,7 +66,7 @@ typedef double REAL;
 #define SYM(name) oracle_##name
 #endif
 
-enum { KIND_EXP = 0, KIND_GAUSS = 1, KIND_SHARP = 2 };
+enum { KIND_EXP = 0, KIND_GAUSS = 1, KIND_SHARP = 2, KIND_HYBRID = 3 };
 
 /* Filter function f(l, l_max).
  *  exp:      Eq. (exp_filter):      1 for |l| <= l_max, exp(-(|l| - l_max)) above.
@@ -81,6 +92,45 @@ static REAL lmax_of(REAL r, REAL dr_min, REAL L, REAL floor_) {
 static REAL mmax_of(REAL r, REAL dr_min, REAL L, REAL floor_, REAL theta) {
   REAL v = 2 * r / dr_min * RSIN(theta) * L;
   return v > floor_ ? v : floor_;
+}
+
+/* Jameson's shock detector (Sec. II.C) on one cell with neighbours a, c: 1 if sigma >= 0.95. Always
+ * double precision (the decision must not depend on the build). */
+static int jameson_fires(double a, double b, double c, double eps) {
+  double num = fabs((a + c) - 2.0 * b);
+  double den = ((fabs(a) + fabs(c)) + 2.0 * fabs(b)) + eps;
+  return num / den >= 0.95;
+}
+
+/* Detector flags of one shell x[j][k] (double input): circ[k] for the theta circles k < Nphi/2 (the
+ * circle of 2 Ntheta samples joining meridians k and k + Nphi/2 over the poles with the sign), and
+ * ring[j] for the phi rings. */
+static void detect_shell(int Nth, int Nph, int parity, double eps, const double* x, unsigned char* circ,
+                         unsigned char* ring) {
+  int M = 2 * Nth, half = Nph / 2;
+  double sign = parity ? -1.0 : 1.0;
+  double* c = (double*)malloc(sizeof(double) * (size_t)(M > Nph ? M : Nph));
+  for (int k = 0; k < half; ++k) {
+    for (int q = 0; q < M; ++q)
+      c[q] = q < Nth ? x[(size_t)q * Nph + k] : sign * x[(size_t)(M - 1 - q) * Nph + (k + half)];
+    circ[k] = 0;
+    for (int q = 0; q < M; ++q)
+      if (jameson_fires(c[(q + M - 1) % M], c[q], c[(q + 1) % M], eps)) circ[k] = 1;
+  }
+  for (int j = 0; j < Nth; ++j) {
+    const double* row = x + (size_t)j * Nph;
+    ring[j] = 0;
+    for (int k = 0; k < Nph; ++k)
+      if (jameson_fires(row[(k + Nph - 1) % Nph], row[k], row[(k + 1) % Nph], eps)) ring[j] = 1;
+  }
+  free(c);
+}
+
+/* The filter function a circle or ring uses: a hybrid field's Gaussian where its detector fired,
+ * else its exponential. */
+static int kind_used(int kind, const unsigned char* fired, int idx) {
+  if (kind != KIND_HYBRID) return kind;
+  return fired[idx] ? KIND_GAUSS : KIND_EXP;
 }
 
 /* Low-pass one real sequence c[0..M-1] in place: naive DFT over the signed frequencies
@@ -125,8 +175,10 @@ static void make_tables(int M, REAL* ctab, REAL* stab) {
 
 /* theta pass on one shell s[j][k] (Ntheta x Nphi), in place (Sec. II.C, first filter equation and
  * the double-covering definition). For each meridian pair (k, k + Nphi/2), k < Nphi/2, build the
- * circle of 2 Ntheta samples, low-pass it with f(|l|, l_max) and scatter back with the sign. */
-static void theta_pass_shell(int Nth, int Nph, int parity, int kind, REAL lmax, REAL* s) {
+ * circle of 2 Ntheta samples, low-pass it with f(|l|, l_max) and scatter back with the sign.
+ * circ: detector flags of a hybrid field (unused otherwise). */
+static void theta_pass_shell(int Nth, int Nph, int parity, int kind, const unsigned char* circ, REAL lmax,
+                             REAL* s) {
   int M = 2 * Nth, half = Nph / 2;
   REAL sign = parity ? (REAL)-1 : (REAL)1;
   REAL* buf = (REAL*)malloc(sizeof(REAL) * (size_t)M * 6);
@@ -138,7 +190,7 @@ static void theta_pass_shell(int Nth, int Nph, int parity, int kind, REAL lmax, 
       if (q < Nth) c[q] = s[(size_t)q * Nph + k];
       else c[q] = sign * s[(size_t)(M - 1 - q) * Nph + (k + half)];
     }
-    lowpass_sequence(M, c, kind, lmax, ctab, stab, re, im, tmp);
+    lowpass_sequence(M, c, kind_used(kind, circ, k), lmax, ctab, stab, re, im, tmp);
     for (int j = 0; j < Nth; ++j) {
       s[(size_t)j * Nph + k] = c[j];
       s[(size_t)j * Nph + (k + half)] = sign * c[M - 1 - j];
@@ -148,9 +200,9 @@ static void theta_pass_shell(int Nth, int Nph, int parity, int kind, REAL lmax, 
 }
 
 /* phi pass on one shell (Sec. II.C, second filter equation): each ring j is low-passed with
- * f(|m|, m_max(r, theta_j)). */
-static void phi_pass_shell(int Nth, int Nph, int kind, REAL r, REAL dr_min, REAL L, REAL floor_,
-                           REAL* s) {
+ * f(|m|, m_max(r, theta_j)). ring: detector flags of a hybrid field (unused otherwise). */
+static void phi_pass_shell(int Nth, int Nph, int kind, const unsigned char* ring, REAL r, REAL dr_min, REAL L,
+                           REAL floor_, REAL* s) {
   int M = Nph;
   REAL pi = RACOS((REAL)-1);
   REAL* buf = (REAL*)malloc(sizeof(REAL) * (size_t)M * 6);
@@ -161,19 +213,19 @@ static void phi_pass_shell(int Nth, int Nph, int kind, REAL r, REAL dr_min, REAL
     REAL theta = ((REAL)j + (REAL)0.5) * pi / (REAL)Nth;
     REAL mmax = mmax_of(r, dr_min, L, floor_, theta);
     for (int k = 0; k < M; ++k) c[k] = s[(size_t)j * Nph + k];
-    lowpass_sequence(M, c, kind, mmax, ctab, stab, re, im, tmp);
+    lowpass_sequence(M, c, kind_used(kind, ring, j), mmax, ctab, stab, re, im, tmp);
     for (int k = 0; k < M; ++k) s[(size_t)j * Nph + k] = c[k];
   }
   free(buf);
 }
 
 static int check_args(int Nr, int Nth, int Nph, int nvars, const int* parity, const int* kind,
-                      const double* L, const double* r, double dr_min, double floor_) {
+                      const double* L, const double* r, double dr_min, double floor_, double eps) {
   if (Nr < 1 || Nth < 1 || Nph < 2 || (Nph % 2) != 0 || nvars < 1) return 1;
-  if (!parity || !kind || !L || !r || !(dr_min > 0) || !(floor_ >= 0)) return 1;
+  if (!parity || !kind || !L || !r || !(dr_min > 0) || !(floor_ >= 0) || !(eps >= 0)) return 1;
   for (int v = 0; v < nvars; ++v) {
     if (parity[v] != 0 && parity[v] != 1) return 1;
-    if (kind[v] < 0 || kind[v] > 2) return 1;
+    if (kind[v] < 0 || kind[v] > 3) return 1;
     if (!(L[v] > 0)) return 1;
   }
   for (int i = 0; i < Nr; ++i)
@@ -182,11 +234,15 @@ static int check_args(int Nr, int Nth, int Nph, int nvars, const int* parity, co
 }
 
 /* which: bit 0 = theta pass, bit 1 = phi pass; order 0 = theta then phi (the filter),
- * order 1 = phi then theta (its transpose, since each pass is a real symmetric operator). */
+ * order 1 = phi then theta (its transpose, since each pass is a real symmetric operator; not
+ * defined for hybrid fields). */
 static int run(int Nr, int Nth, int Nph, int nvars, const int* parity, const int* kind,
-               const double* L, const double* r, double dr_min, double floor_, const double* in,
-               double* out, int which, int order) {
-  if (check_args(Nr, Nth, Nph, nvars, parity, kind, L, r, dr_min, floor_)) return 1;
+               const double* L, const double* r, double dr_min, double floor_, double eps,
+               const double* in, double* out, int which, int order) {
+  if (check_args(Nr, Nth, Nph, nvars, parity, kind, L, r, dr_min, floor_, eps)) return 1;
+  if (order != 0)
+    for (int v = 0; v < nvars; ++v)
+      if (kind[v] == KIND_HYBRID) return 1;
   long nshell = (long)nvars * Nr;
   size_t npts = (size_t)Nth * Nph;
 #pragma omp parallel for schedule(dynamic, 1)
@@ -195,43 +251,59 @@ static int run(int Nr, int Nth, int Nph, int nvars, const int* parity, const int
     REAL* s = (REAL*)malloc(sizeof(REAL) * npts);
     const double* src = in + (size_t)sidx * npts;
     for (size_t p = 0; p < npts; ++p) s[p] = (REAL)src[p];
+    unsigned char* circ = (unsigned char*)calloc((size_t)(Nph / 2 + Nth), 1);
+    unsigned char* ring = circ + Nph / 2;
+    if (kind[v] == KIND_HYBRID) detect_shell(Nth, Nph, parity[v], eps, src, circ, ring);
     REAL lmax = lmax_of((REAL)r[i], (REAL)dr_min, (REAL)L[v], (REAL)floor_);
     for (int step = 0; step < 2; ++step) {
       int pass = (order == 0) ? step : 1 - step; /* 0 = theta, 1 = phi */
-      if (pass == 0 && (which & 1)) theta_pass_shell(Nth, Nph, parity[v], kind[v], lmax, s);
+      if (pass == 0 && (which & 1)) theta_pass_shell(Nth, Nph, parity[v], kind[v], circ, lmax, s);
       if (pass == 1 && (which & 2))
-        phi_pass_shell(Nth, Nph, kind[v], (REAL)r[i], (REAL)dr_min, (REAL)L[v], (REAL)floor_, s);
+        phi_pass_shell(Nth, Nph, kind[v], ring, (REAL)r[i], (REAL)dr_min, (REAL)L[v], (REAL)floor_, s);
     }
     double* dst = out + (size_t)sidx * npts;
     for (size_t p = 0; p < npts; ++p) dst[p] = (double)s[p];
+    free(circ);
     free(s);
   }
   return 0;
 }
 
-/* ---- exported entry points (return 0 on success, 1 on invalid arguments) ---- */
+/* ---- exported entry points (return 0 on success, 1 on invalid arguments) ----
+ * eps: the detector's epsilon for hybrid fields (kind 3), >= 0. */
 
 /* The double filter: theta pass, then phi pass. */
 int SYM(filter)(int Nr, int Nth, int Nph, int nvars, const int* parity, const int* kind,
-                const double* L, const double* r, double dr_min, double floor_, const double* in,
-                double* out) {
-  return run(Nr, Nth, Nph, nvars, parity, kind, L, r, dr_min, floor_, in, out, 3, 0);
+                const double* L, const double* r, double dr_min, double floor_, double eps,
+                const double* in, double* out) {
+  return run(Nr, Nth, Nph, nvars, parity, kind, L, r, dr_min, floor_, eps, in, out, 3, 0);
 }
 
-/* Transpose of the double filter: phi pass, then theta pass. */
+/* Transpose of the double filter: phi pass, then theta pass (rejects hybrid fields). */
 int SYM(filter_T)(int Nr, int Nth, int Nph, int nvars, const int* parity, const int* kind,
-                  const double* L, const double* r, double dr_min, double floor_, const double* in,
-                  double* out) {
-  return run(Nr, Nth, Nph, nvars, parity, kind, L, r, dr_min, floor_, in, out, 3, 1);
+                  const double* L, const double* r, double dr_min, double floor_, double eps,
+                  const double* in, double* out) {
+  return run(Nr, Nth, Nph, nvars, parity, kind, L, r, dr_min, floor_, eps, in, out, 3, 1);
 }
 
-/* One pass alone: which = 1 theta pass only, 2 phi pass only. */
+/* One pass alone: which = 1 theta pass only, 2 phi pass only. Hybrid fields detect on the input. */
 int SYM(single_pass)(int Nr, int Nth, int Nph, int nvars, const int* parity, const int* kind,
-                     const double* L, const double* r, double dr_min, double floor_,
+                     const double* L, const double* r, double dr_min, double floor_, double eps,
                      const double* in, double* out, int which) {
   if (which != 1 && which != 2) return 1;
-  return run(Nr, Nth, Nph, nvars, parity, kind, L, r, dr_min, floor_, in, out, which, 0);
+  return run(Nr, Nth, Nph, nvars, parity, kind, L, r, dr_min, floor_, eps, in, out, which, 0);
 }
+
+/* Detector flags of one shell [Ntheta][Nphi]: circ[Nphi/2] (theta circles), ring[Ntheta] (phi rings). */
+int SYM(detect)(int Nth, int Nph, int parity, double eps, const double* shell, unsigned char* circ,
+                unsigned char* ring) {
+  if (Nth < 1 || Nph < 2 || (Nph % 2) != 0 || (parity != 0 && parity != 1) || !(eps >= 0)) return 1;
+  detect_shell(Nth, Nph, parity, eps, shell, circ, ring);
+  return 0;
+}
+
+/* sigma >= 0.95 for one cell (1) or not (0). */
+int SYM(jameson_fires)(double a, double b, double c, double eps) { return jameson_fires(a, b, c, eps); }
 
 double SYM(filter_value)(int kind, double l, double lmax) {
   return (double)filter_value(kind, (REAL)l, (REAL)lmax);

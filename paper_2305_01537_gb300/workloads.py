@@ -15,7 +15,9 @@ added at every grid point, so every Fourier mode carries power.
 The 28-field mix follows the paper's field classes (Sec. II.C): exponential filter with L = 3
 for spacetime fields, Gaussian with L = 12 for D, S_i, tau, entropy and exponential with L = 12
 for A_i and Phi. The parity split (20 even / 8 odd) is an assumption; the paper defers it to a
-table of another paper.
+table of another paper. The hybrid mix gives the six matter fields the hybrid filter instead of
+the Gaussian (Sec. II.C: exponential unless Jameson's detector finds a discontinuity), on a "star"
+state whose matter fields drop from O(1) to an atmosphere of 1e-10 across a sphere's surface.
 """
 from __future__ import annotations
 
@@ -24,7 +26,7 @@ from typing import List, Sequence
 
 import numpy as np
 
-EXP, GAUSS, SHARP = 0, 1, 2
+EXP, GAUSS, SHARP, HYBRID = 0, 1, 2, 3
 
 
 @dataclass
@@ -39,6 +41,7 @@ class Grid:
     r: np.ndarray = None
     dr_min: float = 1.0
     floor: float = 2.0
+    eps: float = 1e-12  # epsilon of Jameson's detector (hybrid fields)
 
     def __post_init__(self):
         if self.r is None:
@@ -71,6 +74,12 @@ def field_mix_28():
     return parity, kind, L
 
 
+def field_mix_28_hybrid():
+    """The 28-field mix with the six matter fields (Gaussian in field_mix_28) on the hybrid filter."""
+    parity, kind, L = field_mix_28()
+    return parity, [HYBRID if k == GAUSS else k for k in kind], L
+
+
 def field_mix_8():
     """Eight-field mix of the differentiable chain: 6 even and 2 odd, exponential, L = 3."""
     return [0] * 6 + [1] * 2, [EXP] * 8, [3.0] * 8
@@ -78,6 +87,11 @@ def field_mix_8():
 
 def grid_28(Nr, Nth, Nph) -> Grid:
     p, k, L = field_mix_28()
+    return Grid(Nr, Nth, Nph, p, k, L)
+
+
+def grid_28_hybrid(Nr, Nth, Nph) -> Grid:
+    p, k, L = field_mix_28_hybrid()
     return Grid(Nr, Nth, Nph, p, k, L)
 
 
@@ -121,6 +135,36 @@ def band_limited_state(grid: Grid, seed: int, mode_max: int, noise: float,
         out[s0:s1] = _mode_sum(shell_parity[s0:s1], amp_c[s0:s1], amp_s[s0:s1], grid.Ntheta, grid.Nphi)
         out[s0:s1] += rng.uniform(-noise, noise, size=(s1 - s0, grid.Ntheta, grid.Nphi))
     return out.reshape(grid.shape)
+
+
+def star_state(grid: Grid, seed: int, mode_max: int = 4, noise: float = 0.05) -> np.ndarray:
+    """Fields of hybrid kind get a "star": rho = 1 inside a ball, 1e-10 (atmosphere) outside, times a
+    smooth factor: rho (1 + g / 2) for even fields, rho g for odd ones, g a random band-limited
+    field of that parity (modes l, m <= mode_max) scaled to max |g| = 1. The ball has radius
+    0.234 Nr around the point at radius 0.3125 Nr, theta = pi/3, phi = 0.5 (shells r = i + 1/2),
+    so the middle shells cut its surface. The other fields are band_limited_state(mode_max =
+    Nphi / 8, noise). No noise on the star fields: their smooth parts keep Jameson's sigma small."""
+    x = band_limited_state(grid, seed, mode_max=max(1, grid.Nphi // 8), noise=noise)
+    hyb = [v for v in range(grid.nvars) if grid.kind[v] == HYBRID]
+    if not hyb:
+        return x
+    th, ph = theta_points(grid.Ntheta), phi_points(grid.Nphi)
+    r = np.asarray(grid.r, dtype=np.float64)
+    st, ct = np.sin(th)[None, :, None], np.cos(th)[None, :, None]
+    sp, cp = np.sin(ph)[None, None, :], np.cos(ph)[None, None, :]
+    rr = r[:, None, None]
+    X, Y, Z = rr * st * cp, rr * st * sp, rr * ct * np.ones_like(cp)
+    rc, tc, pc, R = 0.3125 * grid.Nr, np.pi / 3, 0.5, 0.234375 * grid.Nr
+    cx, cy, cz = rc * np.sin(tc) * np.cos(pc), rc * np.sin(tc) * np.sin(pc), rc * np.cos(tc)
+    rho = np.where((X - cx) ** 2 + (Y - cy) ** 2 + (Z - cz) ** 2 < R * R, 1.0, 1e-10)
+    rng = np.random.default_rng([seed, 2])
+    for v in hyb:
+        amp_c = rng.standard_normal((grid.Nr, mode_max + 1, mode_max + 1))
+        amp_s = rng.standard_normal((grid.Nr, mode_max + 1, mode_max + 1))
+        g = _mode_sum(np.full(grid.Nr, grid.parity[v]), amp_c, amp_s, grid.Ntheta, grid.Nphi)
+        g /= np.abs(g).max(axis=(1, 2), keepdims=True)
+        x[v] = rho * (g if grid.parity[v] else 1.0 + 0.5 * g)
+    return x
 
 
 def few_mode_state(grid: Grid, seed: int, nmodes: int, mode_max: int, noise: float) -> np.ndarray:
@@ -168,6 +212,8 @@ class Workload:
         seed = self.seeds[index]
         if self.name == "single_field_16x16x32":
             return few_mode_state(g, seed, nmodes=6, mode_max=4, noise=1e-3)
+        if self.name.startswith("hybrid28_"):
+            return star_state(g, seed)
         return band_limited_state(g, seed, mode_max=g.Nphi // 8, noise=0.05)
 
 
@@ -194,6 +240,13 @@ def state_32x128x256() -> Workload:
     28 fields, Nr = 32, seed 2; a case small enough for detailed profiles of the 128 x 256 kernels."""
     return Workload("state28_32x128x256", [grid_28(32, 128, 256)], [2],
                     "28 mixed-parity fields, band-limited m,l<=32 + U(-0.05,0.05)")
+
+
+def hybrid_state_128x64x128() -> Workload:
+    """The 28-field mix with hybrid-filtered matter fields on a star state, Nr = 128, Ntheta = 64,
+    Nphi = 128, seed 10."""
+    return Workload("hybrid28_128x64x128", [grid_28_hybrid(128, 64, 128)], [10],
+                    "28 fields, 6 hybrid matter fields with a star surface (1 -> 1e-10), others band-limited")
 
 
 BATCH_SHAPES = [(16, 32, 64), (32, 64, 96), (48, 96, 128), (64, 128, 256), (96, 192, 384), (128, 256, 512)]
