@@ -49,10 +49,25 @@ typedef enum {
 } sph_status;
 
 /* Filter functions (Sec. II.C):
- *  SPH_FILTER_EXP   Eq. (exp_filter): 1 for |l| <= l_max, exp(-(|l| - l_max)) above.
- *  SPH_FILTER_GAUSS Eq. (gaussian_filter): exp(log(0.9) (l / (l_max + 1))^2) for every l.
- *  SPH_FILTER_SHARP the spectrally sharp low-pass: 1 for |l| <= l_max, 0 above. */
-typedef enum { SPH_FILTER_EXP = 0, SPH_FILTER_GAUSS = 1, SPH_FILTER_SHARP = 2 } sph_kind;
+ *  SPH_FILTER_EXP    Eq. (exp_filter): 1 for |l| <= l_max, exp(-(|l| - l_max)) above.
+ *  SPH_FILTER_GAUSS  Eq. (gaussian_filter): exp(log(0.9) (l / (l_max + 1))^2) for every l.
+ *  SPH_FILTER_SHARP  the spectrally sharp low-pass: 1 for |l| <= l_max, 0 above.
+ *  SPH_FILTER_HYBRID the hybrid filter of Sec. II.C: each theta circle and each phi ring takes
+ *                    the Gaussian filter if Jameson's shock detector fires in one of its cells,
+ *                    else the exponential filter. For a cell u_i with neighbours u_{i-1}, u_{i+1}
+ *                    along the circle (across the poles with the parity sign) or the ring,
+ *                      sigma = |(u_{i-1} + u_{i+1}) - 2 u_i| / (((|u_{i-1}| + |u_{i+1}|) + 2 |u_i|) + eps)
+ *                    and the detector fires if sigma >= 0.95. Both detectors read the filter's
+ *                    input; the decision is that of this expression evaluated in FP64 with IEEE
+ *                    round-to-nearest, in this order. The switch makes the filter nonlinear, so
+ *                    plans with hybrid fields run only sph_filter_apply and its FP32-storage,
+ *                    host-buffer and batch forms (the adjoint and tanh calls return
+ *                    SPH_EUNSUPPORTED), with the FP64 or compensated-FP32 precision and shells
+ *                    that fit one CTA's shared memory (the 8 Ntheta (Nphi + 2) bytes of a shell
+ *                    plus FFT scratch within 227 KB, e.g. 96 x 192; 128 x 256 shells run on a CTA
+ *                    pair, which does not take hybrid fields); other plans with hybrid fields fail
+ *                    to create with SPH_EUNSUPPORTED. */
+typedef enum { SPH_FILTER_EXP = 0, SPH_FILTER_GAUSS = 1, SPH_FILTER_SHARP = 2, SPH_FILTER_HYBRID = 3 } sph_kind;
 
 /* Arithmetic of the plan's kernels. Inputs and outputs are FP64 for every choice.
  *  SPH_PREC_F64     plain form: FFTs in FP64 arithmetic.
@@ -69,6 +84,8 @@ typedef struct {
   const int* kind;  /* [nvars] sph_kind per field */
   double floor;     /* lower bound of l_max and m_max; the paper's value is 2; >= 0 */
   int precision;    /* sph_precision */
+  double eps;       /* epsilon of Jameson's detector (SPH_FILTER_HYBRID fields), finite, >= 0;
+                       ignored when no field is hybrid */
 } sph_cutoff_params;
 
 /* Create a plan for states of nvars fields on an Nr x Ntheta x Nphi grid, on the current CUDA
@@ -77,7 +94,9 @@ typedef struct {
  * (l_max per shell and field class, m_max per ring and class) and the twiddle tables in FP64 on
  * the host and copies them to the device. *out is set to NULL on failure.
  * Errors: SPH_EINVAL (Nr, Ntheta, nvars < 1; Nphi < 2 or odd; parity not 0/1; kind unknown;
- * dr_min <= 0; r < 0; L <= 0; floor < 0; precision unknown; NULL pointer), SPH_ENOMEM, SPH_ECUDA. */
+ * dr_min <= 0; r < 0; L <= 0; floor < 0; precision unknown; eps < 0 or not finite with a hybrid
+ * field; NULL pointer), SPH_EUNSUPPORTED (a hybrid field in a plan that cannot run it, see
+ * SPH_FILTER_HYBRID), SPH_ENOMEM, SPH_ECUDA. */
 sph_status sph_filter_plan_create(sph_filter_plan* out, int Nr, int Ntheta, int Nphi, int nvars,
                                   const int* parity, const sph_cutoff_params* params);
 

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsph_filter.so")
 
 SPH_OK, SPH_EINVAL, SPH_ENOMEM, SPH_ECUDA, SPH_EUNSUPPORTED, SPH_ETIMEOUT, SPH_EALIAS, SPH_EDEVICE = range(8)
-SPH_FILTER_EXP, SPH_FILTER_GAUSS, SPH_FILTER_SHARP = 0, 1, 2
+SPH_FILTER_EXP, SPH_FILTER_GAUSS, SPH_FILTER_SHARP, SPH_FILTER_HYBRID = 0, 1, 2, 3
 SPH_PREC_F64, SPH_PREC_SPLIT_TC, SPH_PREC_F32X2 = 0, 1, 2
 
 # Every symbol include/sph_filter.h declares (checked by the tests).
@@ -40,7 +40,8 @@ class SphFilterError(RuntimeError):
 
 class sph_cutoff_params(ctypes.Structure):
     _fields_ = [("r", ctypes.c_void_p), ("dr_min", ctypes.c_double), ("L", ctypes.c_void_p),
-                ("kind", ctypes.c_void_p), ("floor", ctypes.c_double), ("precision", ctypes.c_int)]
+                ("kind", ctypes.c_void_p), ("floor", ctypes.c_double), ("precision", ctypes.c_int),
+                ("eps", ctypes.c_double)]
 
 
 _lib = None
@@ -108,7 +109,8 @@ class Plan:
 
     def __init__(self, Nr: int, Ntheta: int, Nphi: int, parity: Sequence[int], kind: Sequence[int],
                  L: Sequence[float], r: Sequence[float], dr_min: float = 1.0, floor: float = 2.0,
-                 precision: int = SPH_PREC_F64):
+                 precision: int = SPH_PREC_F64, eps: float = 1e-12):
+        """eps: epsilon of Jameson's detector for SPH_FILTER_HYBRID fields."""
         lib = load()
         self.Nr, self.Ntheta, self.Nphi = int(Nr), int(Ntheta), int(Nphi)
         self.nvars = len(parity)
@@ -119,7 +121,7 @@ class Plan:
         if self._kind.shape != (self.nvars,) or self._L.shape != (self.nvars,) or self._r.shape != (self.Nr,):
             raise ValueError("kind and L need nvars entries, r needs Nr entries")
         prm = sph_cutoff_params(self._r.ctypes.data, float(dr_min), self._L.ctypes.data, self._kind.ctypes.data,
-                                float(floor), int(precision))
+                                float(floor), int(precision), float(eps))
         h = ctypes.c_void_p()
         _check(lib.sph_filter_plan_create(ctypes.byref(h), self.Nr, self.Ntheta, self.Nphi, self.nvars,
                                           self._parity.ctypes.data, ctypes.byref(prm)), "sph_filter_plan_create")
@@ -129,7 +131,7 @@ class Plan:
     @classmethod
     def from_grid(cls, grid, precision: int = SPH_PREC_F64) -> "Plan":
         return cls(grid.Nr, grid.Ntheta, grid.Nphi, grid.parity, grid.kind, grid.L, grid.r, grid.dr_min,
-                   grid.floor, precision)
+                   grid.floor, precision, getattr(grid, "eps", 1e-12))
 
     @property
     def shape(self):

@@ -28,8 +28,10 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build the library")
 
 
-# shell_inst.cu is compiled once per (precision, FFT length) instantiation of the shell kernel
-SHELL_INST = [(d, n) for d in (0, 1) for n in (0, 32, 64, 96, 128, 192, 256)]
+# shell_inst.cu is compiled once per (precision, FFT length, hybrid variant) instantiation of the
+# shell kernel; the hybrid variant exists for the lengths one CTA holds (not 256)
+SHELL_INST = [(d, n, h) for d in (0, 1) for n in (0, 32, 64, 96, 128, 192, 256) for h in (0, 1)
+              if not (h and n == 256)]
 
 
 def jobs():
@@ -38,9 +40,9 @@ def jobs():
     for src in sorted(glob.glob(os.path.join(CSRC, "*.cu"))):
         base = os.path.basename(src)[:-3]
         if base == "shell_inst":
-            for d, n in SHELL_INST:
-                out.append((src, os.path.join(OBJ, f"shell_inst_d{d}_n{n}.o"),
-                            [f"-DSPH_SHELL_DF={d}", f"-DSPH_SHELL_LEN={n}"]))
+            for d, n, h in SHELL_INST:
+                out.append((src, os.path.join(OBJ, f"shell_inst_d{d}_n{n}_h{h}.o"),
+                            [f"-DSPH_SHELL_DF={d}", f"-DSPH_SHELL_LEN={n}", f"-DSPH_SHELL_HYB={h}"]))
         else:
             out.append((src, os.path.join(OBJ, base + ".o"), []))
     return out

@@ -80,8 +80,10 @@ double mmax_of(double r, double dr_min, double L, double floor_, int j, int Nth)
 }
 
 
-// Filter function f(|l|, l_max) of Sec. II.C in extended precision (tables are rounded once).
+// Filter function f(|l|, l_max) of Sec. II.C in extended precision (tables are rounded once). A
+// hybrid field's own class holds the exponential filter (its Gaussian tables are another class).
 long double fval(int kind, long double al, long double lmax) {
+  if (kind == SPH_FILTER_HYBRID) kind = SPH_FILTER_EXP;
   if (kind == SPH_FILTER_GAUSS) {
     const long double t = al / (lmax + 1.0L);
     return expl(logl(0.9L) * t * t);
@@ -315,8 +317,15 @@ sph_status launch_plan_vars(sph_filter_plan_s* p, const void* in, const void* au
     if (cur != p->device) cudaSetDevice(cur);
     return e == cudaSuccess ? SPH_OK : SPH_ECUDA;
   }
-  LaunchIO io{in,        aux,    out, map_in, map_out, transpose, is_f32, ((uintptr_t)in % 16) == 0 ? 1 : 0,
-              var_begin, var_count};
+  int hybrid = 0;
+  for (int v = var_begin; v < var_begin + var_count; ++v) hybrid |= p->kind[(size_t)v] == SPH_FILTER_HYBRID;
+  if (hybrid && (transpose || map_in != kMapNone || map_out != kOutNone)) {
+    // the hybrid switch is nonlinear: neither its transpose nor the fused chain steps are defined
+    if (cur != p->device) cudaSetDevice(cur);
+    return SPH_EUNSUPPORTED;
+  }
+  LaunchIO io{in,        aux,       out, map_in, map_out, transpose, is_f32, ((uintptr_t)in % 16) == 0 ? 1 : 0,
+              var_begin, var_count, hybrid};
   cudaError_t e = !p->use_v2 ? launch_plain(*p, io, (cudaStream_t)stream)
                   : p->cluster ? launch_shell_cl(p->args2, p->precision, p->threads2, p->smem2, io, (cudaStream_t)stream)
                                : launch_shell(p->args2, p->precision, p->threads2, p->smem2, io, (cudaStream_t)stream);
@@ -346,11 +355,16 @@ sph_status sph_filter_plan_create(sph_filter_plan* out, int Nr, int Ntheta, int 
     return SPH_EINVAL;
   if (prm->precision != SPH_PREC_F64 && prm->precision != SPH_PREC_SPLIT_TC && prm->precision != SPH_PREC_F32X2)
     return SPH_EINVAL;
+  bool hybrid = false;
   for (int v = 0; v < nvars; ++v) {
     if (parity[v] != 0 && parity[v] != 1) return SPH_EINVAL;
-    if (prm->kind[v] < SPH_FILTER_EXP || prm->kind[v] > SPH_FILTER_SHARP) return SPH_EINVAL;
+    if (prm->kind[v] < SPH_FILTER_EXP || prm->kind[v] > SPH_FILTER_HYBRID) return SPH_EINVAL;
     if (!(prm->L[v] > 0) || !std::isfinite(prm->L[v])) return SPH_EINVAL;
+    hybrid |= prm->kind[v] == SPH_FILTER_HYBRID;
   }
+  if (hybrid && (!(prm->eps >= 0) || !std::isfinite(prm->eps))) return SPH_EINVAL;
+  // the tensor-core form builds one operator per pass and class: no per-circle switch
+  if (hybrid && prm->precision == SPH_PREC_SPLIT_TC) return SPH_EUNSUPPORTED;
   for (int i = 0; i < Nr; ++i)
     if (!(prm->r[i] >= 0) || !std::isfinite(prm->r[i])) return SPH_EINVAL;
 
@@ -371,18 +385,25 @@ sph_status sph_filter_plan_create(sph_filter_plan* out, int Nr, int Ntheta, int 
   p->kind.assign(prm->kind, prm->kind + nvars);
   p->L.assign(prm->L, prm->L + nvars);
   p->r.assign(prm->r, prm->r + Nr);
-  // cutoff classes: distinct (kind, L)
-  p->var_cls.resize((size_t)nvars);
-  for (int v = 0; v < nvars; ++v) {
+  p->has_hybrid = hybrid;
+  // cutoff classes: distinct (kind, L); a hybrid field also needs the Gaussian class of its L
+  auto class_of = [p](int kind, double L) {
     int c = 0;
     for (; c < p->ncls; ++c)
-      if (p->cls_kind[(size_t)c] == p->kind[(size_t)v] && p->cls_L[(size_t)c] == p->L[(size_t)v]) break;
+      if (p->cls_kind[(size_t)c] == kind && p->cls_L[(size_t)c] == L) break;
     if (c == p->ncls) {
-      p->cls_kind.push_back(p->kind[(size_t)v]);
-      p->cls_L.push_back(p->L[(size_t)v]);
+      p->cls_kind.push_back(kind);
+      p->cls_L.push_back(L);
       ++p->ncls;
     }
-    p->var_cls[(size_t)v] = c;
+    return c;
+  };
+  p->var_cls.resize((size_t)nvars);
+  std::vector<int> alt_cls((size_t)nvars);
+  for (int v = 0; v < nvars; ++v) {
+    p->var_cls[(size_t)v] = class_of(p->kind[(size_t)v], p->L[(size_t)v]);
+    alt_cls[(size_t)v] = p->kind[(size_t)v] == SPH_FILTER_HYBRID ? class_of(SPH_FILTER_GAUSS, p->L[(size_t)v])
+                                                                 : p->var_cls[(size_t)v];
   }
   p->h_lmax.resize((size_t)p->ncls * Nr);
   p->h_mmax.resize((size_t)p->ncls * Nr * Ntheta);
@@ -394,7 +415,8 @@ sph_status sph_filter_plan_create(sph_filter_plan* out, int Nr, int Ntheta, int 
             mmax_of(p->r[(size_t)i], p->dr_min, p->cls_L[(size_t)c], p->floor_, j, Ntheta);
     }
   std::vector<VarInfo> vi((size_t)nvars);
-  for (int v = 0; v < nvars; ++v) vi[(size_t)v] = VarInfo{p->parity[(size_t)v], p->kind[(size_t)v], p->var_cls[(size_t)v], 0};
+  for (int v = 0; v < nvars; ++v)
+    vi[(size_t)v] = VarInfo{p->parity[(size_t)v], p->kind[(size_t)v], p->var_cls[(size_t)v], alt_cls[(size_t)v]};
 
   sph_status st = SPH_OK;
   if (st == SPH_OK) st = upload(&p->d_lmax, p->h_lmax.data(), p->h_lmax.size());
@@ -419,10 +441,16 @@ sph_status sph_filter_plan_create(sph_filter_plan* out, int Nr, int Ntheta, int 
     return SPH_OK;
   }
   // the staged shell kernel when the shape fits it; otherwise the chunked FP64 kernel
+  p->args2.eps = prm->eps;
   st = setup_v2(p);
   if (st != SPH_OK && st != SPH_EUNSUPPORTED) {
     free_plan(p);
     return st;
+  }
+  if (hybrid && (!p->use_v2 || p->cluster)) {
+    // the detector and the per-circle multipliers live in the single-CTA shell kernel
+    free_plan(p);
+    return SPH_EUNSUPPORTED;
   }
   if (!p->use_v2) {
     if (p->precision != SPH_PREC_F64) {

@@ -20,12 +20,14 @@ struct Factors {
   int radix[kMaxStages] = {};
 };
 
-// Per-field description the kernels read: parity a, filter kind, cutoff-class index.
+// Per-field description the kernels read: parity a, filter kind, cutoff-class index. A hybrid
+// field's class holds its exponential tables and alt_cls its Gaussian ones (alt_cls = cls for the
+// other kinds).
 struct VarInfo {
   int parity;
   int kind;
   int cls;
-  int pad;
+  int alt_cls;
 };
 
 // Everything a shell kernel needs, passed by value.
@@ -59,6 +61,7 @@ struct LaunchIO {
   int async_ok;       // input 16-byte aligned: shells may be copied with cp.async
   int var_begin;      // fields [var_begin, var_begin + var_count) are filtered (pointers are to
   int var_count;      // the whole state)
+  int hybrid;         // some field of the launch takes the hybrid filter (every row is loaded)
 };
 
 // Arguments of the staged shell kernel (shell_kernel.cuh). Tables hold FP64 values, or
@@ -77,33 +80,37 @@ struct ShellArgs2 {
   const void* tw_ph;          // [Nph]   exp(-2 pi i n / Nph)
   const void* consts;         // [2] sqrt(1/2), sqrt(3)/2
   unsigned* status;
+  double eps;                 // epsilon of Jameson's detector (hybrid fields)
 };
 
-// Instantiations of the staged shell kernel, one per (compensated precision?, FFT length);
-// defined by shell_inst.cu compiled once per pair.
-template <int DFP, int LEN>
+// Instantiations of the staged shell kernel, one per (compensated precision?, FFT length, hybrid
+// variant); defined by shell_inst.cu compiled once per triple. The hybrid variant (HYB = 1) exists
+// for the lengths a single CTA holds.
+template <int DFP, int LEN, int HYB>
 cudaError_t launch_shell_inst(const ShellArgs2& a, int threads, size_t smem, const LaunchIO& io, cudaStream_t s);
-template <int DFP, int LEN>
+template <int DFP, int LEN, int HYB>
 cudaError_t set_attr_inst(int bytes);
-#define SPH_DECLARE_SHELL_INST(D, L)                                                                    \
-  template <>                                                                                           \
-  cudaError_t launch_shell_inst<D, L>(const ShellArgs2&, int, size_t, const LaunchIO&, cudaStream_t); \
-  template <>                                                                                           \
-  cudaError_t set_attr_inst<D, L>(int);
-SPH_DECLARE_SHELL_INST(0, 0)
-SPH_DECLARE_SHELL_INST(0, 32)
-SPH_DECLARE_SHELL_INST(0, 64)
-SPH_DECLARE_SHELL_INST(0, 96)
-SPH_DECLARE_SHELL_INST(0, 128)
-SPH_DECLARE_SHELL_INST(0, 192)
-SPH_DECLARE_SHELL_INST(0, 256)
-SPH_DECLARE_SHELL_INST(1, 0)
-SPH_DECLARE_SHELL_INST(1, 32)
-SPH_DECLARE_SHELL_INST(1, 64)
-SPH_DECLARE_SHELL_INST(1, 96)
-SPH_DECLARE_SHELL_INST(1, 128)
-SPH_DECLARE_SHELL_INST(1, 192)
-SPH_DECLARE_SHELL_INST(1, 256)
+#define SPH_DECLARE_SHELL_INST(D, L, H)                                                                    \
+  template <>                                                                                              \
+  cudaError_t launch_shell_inst<D, L, H>(const ShellArgs2&, int, size_t, const LaunchIO&, cudaStream_t); \
+  template <>                                                                                              \
+  cudaError_t set_attr_inst<D, L, H>(int);
+#define SPH_DECLARE_SHELL_INST_2(D, L) SPH_DECLARE_SHELL_INST(D, L, 0) SPH_DECLARE_SHELL_INST(D, L, 1)
+SPH_DECLARE_SHELL_INST_2(0, 0)
+SPH_DECLARE_SHELL_INST_2(0, 32)
+SPH_DECLARE_SHELL_INST_2(0, 64)
+SPH_DECLARE_SHELL_INST_2(0, 96)
+SPH_DECLARE_SHELL_INST_2(0, 128)
+SPH_DECLARE_SHELL_INST_2(0, 192)
+SPH_DECLARE_SHELL_INST(0, 256, 0)
+SPH_DECLARE_SHELL_INST_2(1, 0)
+SPH_DECLARE_SHELL_INST_2(1, 32)
+SPH_DECLARE_SHELL_INST_2(1, 64)
+SPH_DECLARE_SHELL_INST_2(1, 96)
+SPH_DECLARE_SHELL_INST_2(1, 128)
+SPH_DECLARE_SHELL_INST_2(1, 192)
+SPH_DECLARE_SHELL_INST(1, 256, 0)
+#undef SPH_DECLARE_SHELL_INST_2
 #undef SPH_DECLARE_SHELL_INST
 // Cluster-pair instantiations for shells too large for one CTA (lengths 256 and generic).
 template <int DFP, int LEN>
@@ -143,6 +150,7 @@ struct sph_filter_plan_s {
   std::vector<int> parity, kind, var_cls;
   std::vector<double> L, r;
   int ncls = 0;
+  bool has_hybrid = false;
   std::vector<int> cls_kind;
   std::vector<double> cls_L;
   std::vector<double> h_lmax, h_mmax;

@@ -21,6 +21,10 @@
 //  A lone circle (Nphi/2 odd) or lone middle ring (Ntheta odd) is transformed in an extra buffer.
 //  Identity skipping: exponential and sharp filters keep every mode when l_max >= Ntheta (theta)
 //    or m_max >= Nphi/2 (phi); those shells and rings are not transformed at all.
+//  Hybrid fields (Sec. II.C, Jameson's shock detector): the detector runs on the FP64 shell before
+//    anything else is decided; a circle or ring whose detector fired takes the Gaussian table, the
+//    others the exponential one, and circle pairs or mirror rings that take different tables use
+//    the exact two-real-FFT split above.
 //
 // Shared memory is addressed with 32-bit shared-window addresses. The first stage reads and the last
 // stage writes the shell's own row-major layout (row stride Nphi + 2, so value pairs are 16-byte
@@ -268,19 +272,29 @@ struct ThetaAcc {
   struct Seq {
     int b;
     bool lone;
-    bool general;
+    bool general;  // hybrid field: the two circles take different tables (exact split)
+    bool alt;      // hybrid field: both circles take the second (Gaussian) table
   };
   uint32_t S;    // shell, row stride ld (8-byte elements)
   uint32_t ov;   // lone-circle slots (16-byte complex)
   uint32_t lin;  // scratch: sequence b, index n at (b - b0) * M + swizzled n
-  uint32_t g;    // multipliers f(|l|)/M, l = 0..Ntheta
+  uint32_t g;    // multipliers f(|l|)/M, l = 0..Ntheta; a hybrid field's Gaussian row follows
+  const unsigned char* sel;   // hybrid field, per sequence: 0 first table, 1 second, 2 mixed
+  const unsigned char* circ;  // hybrid field, per circle: 1 = second table
+  bool hyb;
   int ld, Nth, Nth8, h, M, M8, nseq, b0;
   bool lone_last;  // Nphi/2 odd: the last sequence holds circle h-1 alone
   bool odd;        // parity a = 1
   bool hodd;       // h odd: pairs at column 2s+h are only 8-byte aligned
 
   __device__ __forceinline__ uint32_t el(int row, int col) const { return S + (uint32_t)(row * ld + col) * 8u; }
-  __device__ __forceinline__ Seq seq(int b) const { return Seq{b, lone_last && b == nseq - 1, false}; }
+  __device__ __forceinline__ Seq seq(int b) const {
+    const bool lone = lone_last && b == nseq - 1;
+    if (!hyb) return Seq{b, lone, false, false};
+    const int t = sel[b];
+    return Seq{b, lone, t == 2, t == 1};
+  }
+  __device__ __forceinline__ int seq_len() const { return M; }
   __device__ __forceinline__ C pair_ld(uint32_t a, bool split) const {
     return split ? C{P::ld8(a), P::ld8(a + 8)} : P::ld16(a);
   }
@@ -323,7 +337,15 @@ struct ThetaAcc {
     if (s.lone) P::st8(a, v.re);
     else pair_st(a, hodd && !up, v);
   }
-  __device__ __forceinline__ T mult(const Seq&, int l) const { return P::ld8(g + 8u * (l <= Nth ? l : M - l)); }
+  __device__ __forceinline__ T mult(const Seq& s, int l) const {
+    return P::ld8(g + (s.alt ? 8u * (uint32_t)(Nth + 1) : 0u) + 8u * (l <= Nth ? l : M - l));
+  }
+  // multipliers of the sequence's circles 2b and 2b+1 (split multiply of a mixed pair)
+  __device__ __forceinline__ void mult2(const Seq& s, int l, T& f1, T& f2) const {
+    const uint32_t alt = 8u * (uint32_t)(Nth + 1), o = 8u * (uint32_t)(l <= Nth ? l : M - l);
+    f1 = P::ld8(g + (circ[2 * s.b] ? alt : 0u) + o);
+    f2 = P::ld8(g + (circ[2 * s.b + 1] ? alt : 0u) + o);
+  }
   __device__ __forceinline__ uint32_t lin_at(int b, int n) const {
     return lin + 16u * (uint32_t)((b - b0) * M + swz(n, M8));
   }
@@ -354,19 +376,23 @@ struct PhiAcc {
   struct Seq {
     int j1, j2;  // j2 < 0: lone middle ring
     bool general;
+    bool alt1, alt2;  // hybrid field: ring j1 / j2 takes the second (Gaussian) table
   };
   uint32_t S, ov;
   uint32_t lin;       // scratch: sequence b, index n at (b - b0) * N + swizzled n
-  const int2* pairs;  // (j1 | general << 30, j2) in shared memory
+  const int2* pairs;  // (j1 | general << 30 | alt1 << 29 | alt2 << 28, j2) in shared memory
   const void* gtab;   // multipliers f(|m|)/Nphi of this shell: [Ntheta][Nphi/2+1] (global)
-  size_t gbase;
+  size_t gbase, gbase_alt;  // the shell's rows of the first and the second table
+  bool hyb;                 // hybrid field: the alt bits select the table
   int ld, N, N8, hN, hN8, nh, b0;
 
   __device__ __forceinline__ uint32_t el(int row, int col) const { return S + (uint32_t)(row * ld + col) * 8u; }
   __device__ __forceinline__ Seq seq(int b) const {
     const int2 p = pairs[b];
-    return Seq{p.x & 0x3fffffff, p.y, ((p.x >> 30) & 1) != 0};
+    return Seq{p.x & 0x0fffffff, p.y, ((p.x >> 30) & 1) != 0, hyb && ((p.x >> 29) & 1) != 0,
+               hyb && ((p.x >> 28) & 1) != 0};
   }
+  __device__ __forceinline__ int seq_len() const { return N; }
   __device__ __forceinline__ uint32_t slot(const Seq& s, int n) const {
     const bool lo = n < hN;
     const int u = lo ? n : n - hN;
@@ -386,10 +412,14 @@ struct PhiAcc {
     P::st8(el(s.j1, k), v.re);
     if (s.j2 >= 0) P::st8(el(s.j2, k), v.im);
   }
-  __device__ __forceinline__ T ring_mult(int j, int m) const {
-    return P::from_tab(gtab, gbase + (size_t)j * nh + (m <= hN ? m : N - m));
+  __device__ __forceinline__ T ring_mult(int j, int m, bool alt) const {
+    return P::from_tab(gtab, (alt ? gbase_alt : gbase) + (size_t)j * nh + (m <= hN ? m : N - m));
   }
-  __device__ __forceinline__ T mult(const Seq& s, int m) const { return ring_mult(s.j1, m); }
+  __device__ __forceinline__ T mult(const Seq& s, int m) const { return ring_mult(s.j1, m, s.alt1); }
+  __device__ __forceinline__ void mult2(const Seq& s, int m, T& f1, T& f2) const {
+    f1 = ring_mult(s.j1, m, s.alt1);
+    f2 = ring_mult(s.j2, m, s.alt2);
+  }
   __device__ __forceinline__ uint32_t lin_at(int b, int n) const {
     return lin + 16u * (uint32_t)((b - b0) * N + swz(n, N8));
   }
@@ -435,10 +465,11 @@ struct PhiSplitAcc {
     const bool mine = blk == r || blk == 2 + r;
     return mine ? A + (uint32_t)(j * ld + lc) * 8u : Bm + (uint32_t)(brow(j) * ld + lc) * 8u;
   }
-  __device__ __forceinline__ Seq seq(int b) const {
+  __device__ __forceinline__ Seq seq(int b) const {  // (hybrid fields do not run on CTA pairs)
     const int2 p = pairs[b];
-    return Seq{p.x & 0x3fffffff, p.y, ((p.x >> 30) & 1) != 0};
+    return Seq{p.x & 0x3fffffff, p.y, ((p.x >> 30) & 1) != 0, false, false};
   }
+  __device__ __forceinline__ int seq_len() const { return N; }
   // slots: segments of Nphi/4 complex in A row j1, B row j1, A row j2, B row j2
   __device__ __forceinline__ uint32_t slot(const Seq& s, int n) const {
     const int seg = n / QB, u = n - seg * QB;
@@ -459,6 +490,10 @@ struct PhiSplitAcc {
     return P::from_tab(gtab, gbase + (size_t)j * nh + (m <= hN ? m : N - m));
   }
   __device__ __forceinline__ T mult(const Seq& s, int m) const { return ring_mult(s.j1, m); }
+  __device__ __forceinline__ void mult2(const Seq& s, int m, T& f1, T& f2) const {
+    f1 = ring_mult(s.j1, m);
+    f2 = ring_mult(s.j2, m);
+  }
   __device__ __forceinline__ uint32_t lin_at(int b, int n) const {
     const int bl = b - b0;
     const bool second = bl >= cap;
@@ -487,7 +522,8 @@ enum { kFirst = 1, kLast = 2, kMul = 4 };
 
 // One radix-R Stockham stage over all B sequences: from the shell slots to the scratch (FROM_SLOTS)
 // or back. kFirst reads the logical sequence out of the shell layout, kLast writes it back there,
-// kMul multiplies each input by the spectral multiplier.
+// kMul multiplies each input by the spectral multiplier (sequences flagged `general` were
+// multiplied before, by general_multiply).
 template <class P, class Acc, int R, int DIR, int MODE, bool FROM_SLOTS>
 __device__ __forceinline__ void stage(const Acc& A, int N, int B, int Ns, uint32_t tw, const Consts<P>& k) {
   using C = typename P::C;
@@ -551,61 +587,20 @@ __device__ __forceinline__ void stage_r(int R, const Acc& A, int N, int B, int N
   }
 }
 
-// Exact two-real-sequence multiply for ring pairs whose multipliers differ:
-// W_m = (f1+f2)/2 Z_m + (f1-f2)/2 conj(Z_{N-m}), on the spectrum held in the slots.
-template <class P>
-__device__ void general_multiply(const PhiAcc<P>& A, int B, bool in_slots) {
+// Exact two-real-sequence multiply for sequences whose two halves take different multipliers:
+// W_m = (f1+f2)/2 Z_m + (f1-f2)/2 conj(Z_{N-m}), on the spectrum held in the slots or the scratch.
+// Used for mirror rings whose cutoffs differ beyond rounding and, for hybrid fields, for circle
+// pairs and mirror rings of which one takes the Gaussian filter and the other the exponential.
+template <class P, class Acc>
+__device__ void general_multiply(const Acc& A, int B, bool in_slots) {
   using C = typename P::C;
-  const int nh = A.N / 2 + 1;
+  const int N = A.seq_len();
+  const int nh = N / 2 + 1;
   for (int base = 0; base < B * nh; base += blockDim.x) {
     const int w = base + threadIdx.x;
     bool act = false;
     int m = 0, mn = 0, bb = 0;
-    typename PhiAcc<P>::Seq sq{0, -1, false};
-    C wm, wn;
-    if (w < B * nh) {
-      const int b = A.b0 + w / nh;
-      bb = b;
-      m = w - (w / nh) * nh;
-      sq = A.seq(b);
-      act = sq.general;
-      if (act) {
-        mn = (A.N - m) % A.N;
-        const C zm = in_slots ? A.slot_ld(sq, m) : A.lin_ld(b, m);
-        const C zn = in_slots ? A.slot_ld(sq, mn) : A.lin_ld(b, mn);
-        const auto f1 = A.ring_mult(sq.j1, m), f2 = A.ring_mult(sq.j2, m);
-        const auto ca = P::half(P::add(f1, f2)), cd = P::half(P::sub(f1, f2));
-        wm = C{P::add(P::mul(zm.re, ca), P::mul(zn.re, cd)), P::sub(P::mul(zm.im, ca), P::mul(zn.im, cd))};
-        wn = C{P::add(P::mul(zn.re, ca), P::mul(zm.re, cd)), P::sub(P::mul(zn.im, ca), P::mul(zm.im, cd))};
-      }
-    }
-    __syncthreads();
-    if (act) {
-      if (in_slots) {
-        A.slot_st(sq, m, wm);
-        if (mn != m) A.slot_st(sq, mn, wn);
-      } else {
-        A.lin_st(bb, m, wm);
-        if (mn != m) A.lin_st(bb, mn, wn);
-      }
-    }
-    __syncthreads();
-  }
-}
-
-template <class P>
-__device__ __forceinline__ void maybe_general_multiply(const ThetaAcc<P>&, int, bool) {}
-
-// Split-shell pairs whose multipliers differ: same exact split as general_multiply.
-template <class P>
-__device__ void maybe_general_multiply(const PhiSplitAcc<P>& A, int B, bool in_slots) {
-  using C = typename P::C;
-  const int nh = A.N / 2 + 1;
-  for (int base = 0; base < B * nh; base += blockDim.x) {
-    const int w = base + threadIdx.x;
-    bool act = false;
-    int m = 0, mn = 0, bb = 0;
-    typename PhiAcc<P>::Seq sq{0, -1, false};
+    typename Acc::Seq sq{};
     C wm, wn;
     if (w < B * nh) {
       bb = A.b0 + w / nh;
@@ -613,10 +608,11 @@ __device__ void maybe_general_multiply(const PhiSplitAcc<P>& A, int B, bool in_s
       sq = A.seq(bb);
       act = sq.general;
       if (act) {
-        mn = (A.N - m) % A.N;
+        mn = (N - m) % N;
         const C zm = in_slots ? A.slot_ld(sq, m) : A.lin_ld(bb, m);
         const C zn = in_slots ? A.slot_ld(sq, mn) : A.lin_ld(bb, mn);
-        const auto f1 = A.ring_mult(sq.j1, m), f2 = A.ring_mult(sq.j2, m);
+        typename P::T f1, f2;
+        A.mult2(sq, m, f1, f2);
         const auto ca = P::half(P::add(f1, f2)), cd = P::half(P::sub(f1, f2));
         wm = C{P::add(P::mul(zm.re, ca), P::mul(zn.re, cd)), P::sub(P::mul(zm.im, ca), P::mul(zn.im, cd))};
         wn = C{P::add(P::mul(zn.re, ca), P::mul(zm.re, cd)), P::sub(P::mul(zn.im, ca), P::mul(zm.im, cd))};
@@ -634,10 +630,6 @@ __device__ void maybe_general_multiply(const PhiSplitAcc<P>& A, int B, bool in_s
     }
     __syncthreads();
   }
-}
-template <class P>
-__device__ __forceinline__ void maybe_general_multiply(const PhiAcc<P>& A, int B, bool in_slots) {
-  general_multiply<P>(A, B, in_slots);
 }
 
 // Runtime radix sequence (generic lengths).
@@ -652,7 +644,7 @@ __device__ void pass_rt(const Acc& A, int N, int B, const Factors& f, uint32_t t
     else stage_r<P, Acc, -1, 0>(R, A, N, B, Ns, tw, k, (s & 1) == 0);
     Ns *= R;
   }
-  if (has_general) maybe_general_multiply<P>(A, B, (f.nst & 1) == 0);
+  if (has_general) general_multiply<P, Acc>(A, B, (f.nst & 1) == 0);
   Ns = 1;
   for (int s = 0; s < f.nst; ++s) {
     const int R = f.radix[s];
@@ -680,7 +672,7 @@ __device__ __forceinline__ void pass_ct(const Acc& A, int N, int B, uint32_t tw,
                                         bool has_general) {
   constexpr bool even = (sizeof...(Rs) % 2) == 0;  // the spectrum lands in the slots
   run_stages<P, Acc, -1, kFirst, true, Rs...>(A, N, B, 1, tw, k);
-  if (has_general) maybe_general_multiply<P>(A, B, even);
+  if (has_general) general_multiply<P, Acc>(A, B, even);
   run_stages<P, Acc, 1, kMul, even, Rs...>(A, N, B, 1, tw, k);
 }
 
@@ -702,20 +694,25 @@ __device__ __forceinline__ void run_pass(const Acc& A, int N, int B, const Facto
   else pass_rt<P, Acc>(A, N, B, f, tw, k, g);
 }
 
-// Each pass is its own function: its registers are allocated apart from the load/store code.
-template <class P, int LEN, bool SPLIT = false>
-__device__ __noinline__ void theta_pass_fn(ThetaAcc<P> TA, Factors f, uint32_t tw, Consts<P> K, int batch) {
+// Each pass is its own function: its registers are allocated apart from the load/store code. HYB
+// (hybrid fields: per-circle or per-ring tables, split multiplies of mixed pairs) is a compile-time
+// flag, so that the other fields run code without those choices.
+template <class P, int LEN, bool SPLIT = false, bool HYB = false>
+__device__ __noinline__ void theta_pass_fn(ThetaAcc<P> TA, Factors f, uint32_t tw, Consts<P> K, int batch,
+                                           bool has_general) {
   TA.template fix<LEN, SPLIT>();
+  TA.hyb = HYB;
   for (int b0 = 0; b0 < TA.nseq; b0 += batch) {
     TA.b0 = b0;
-    run_pass<P, ThetaAcc<P>, LEN>(TA, TA.M, min(batch, TA.nseq - b0), f, tw, K, false);
+    run_pass<P, ThetaAcc<P>, LEN>(TA, TA.M, min(batch, TA.nseq - b0), f, tw, K, HYB && has_general);
   }
 }
 
-template <class P, int LEN>
+template <class P, int LEN, bool HYB = false>
 __device__ __noinline__ void phi_pass_fn(PhiAcc<P> PA, int npairs, bool has_general, Factors f, uint32_t tw,
                                          Consts<P> K, int batch) {
   PA.template fix<LEN>();
+  PA.hyb = HYB;
   for (int b0 = 0; b0 < npairs; b0 += batch) {
     PA.b0 = b0;
     run_pass<P, PhiAcc<P>, LEN>(PA, PA.N, min(batch, npairs - b0), f, tw, K, has_general);
@@ -740,9 +737,13 @@ struct Layout {
   uint32_t lin;        // FFT scratch
   uint32_t ov, tw_th, tw_ph, g_th;
   int2* pairs;
-  int* misc;               // [0] pair count, [1] general flag, [2] block max exponent, [3] active rows
+  int* misc;               // [0] pair count, [1] general flag, [2] block max exponent, [3] active rows,
+                           // hybrid fields: [4] mixed circle pairs, [5] some circle fired, [6] scratch
   unsigned char* rowact;   // rows that are transformed (1) or passed through unchanged (0)
   unsigned short* arow;    // the transformed rows, ascending
+  unsigned char* circ;     // hybrid fields: detector flags of the theta circles [Nphi/2],
+  unsigned char* ring;     //   of the phi rings [Ntheta],
+  unsigned char* thsel;    //   and the table choice of each theta sequence [(Nphi/2 + 1)/2]
 };
 
 // Scratch for one batch: batch_th theta sequences (2 Ntheta slots each) or batch_ph phi pairs
@@ -768,11 +769,14 @@ __device__ Layout<P> carve(const ShellArgs2& A, unsigned char* base) {
   L.ov = saddr(take(16 * (size_t)max(2 * A.Nth, A.Nph)));
   L.tw_th = saddr(take(16 * 2 * (size_t)A.Nth));
   L.tw_ph = saddr(take(16 * (size_t)A.Nph));
-  L.g_th = saddr(take(8 * (size_t)(A.Nth + 1)));
+  L.g_th = saddr(take(16 * (size_t)(A.Nth + 1)));  // two rows: a hybrid field's Gaussian one second
   L.pairs = reinterpret_cast<int2*>(take(sizeof(int2) * (size_t)(A.Nth / 2 + 1)));
-  L.misc = reinterpret_cast<int*>(take(sizeof(int) * 4));
+  L.misc = reinterpret_cast<int*>(take(sizeof(int) * 8));
   L.rowact = take((size_t)A.Nth);
   L.arow = reinterpret_cast<unsigned short*>(take(sizeof(unsigned short) * (size_t)A.Nth));
+  L.circ = take((size_t)(A.Nph / 2 + A.Nth + (A.Nph / 2 + 1) / 2));
+  L.ring = L.circ + A.Nph / 2;
+  L.thsel = L.ring + A.Nth;
   return L;
 }
 
@@ -804,7 +808,7 @@ __device__ __forceinline__ size_t shell_offset(const ShellArgs2& A, const Launch
 template <int LEN>
 __device__ __forceinline__ bool in_place_sparse(const LaunchIO& io) {
   return LEN == 128 && io.in == io.out && !io.is_f32 && io.async_ok && io.map_in == kMapNone &&
-         io.map_out == kOutNone;
+         io.map_out == kOutNone && !io.hybrid;  // hybrid fields: every row may be transformed
 }
 
 // Start the asynchronous copy of shell s into a buffer (16-byte pieces into the padded rows). The
@@ -824,7 +828,103 @@ __device__ __forceinline__ void issue_load(const ShellArgs2& A, const LaunchIO& 
   }
 }
 
-template <class P, int LEN>
+// ------------------------------------------------------------------ hybrid filter: shock detector
+
+// x 2^-E as FP32 for the detector's screen, E = emax - 1023 with emax the largest exponent field of
+// the shell's finite values (so |x 2^-E| < 2): the significand truncated to 24 bits (relative error
+// below 2^-23), values under 2^-120 on that scale set to 0. Subnormal, infinite and NaN inputs set
+// `bad` (their cells are decided exactly); zero converts exactly.
+__device__ __forceinline__ float screen_value(double x, int emax, bool& bad) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  bad |= e == 0x7ff || (e == 0 && (u << 1) != 0ull);
+  const int fe = e - emax + 127;  // FP32 biased exponent on the shell's scale
+  const unsigned bits = (hi & 0x80000000u) | ((unsigned)fe << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  return fe >= 7 ? __uint_as_float(bits) : 0.0f;
+}
+
+// Jameson's sigma >= 0.95 for the cell b between a and c, in FP64 with round-to-nearest, operation
+// for operation: num = |(a + c) - 2 b|, den = ((|a| + |c|) + 2 |b|) + eps, num / den >= 0.95.
+__device__ __forceinline__ bool jameson_exact(double a, double b, double c, double eps) {
+  const double num = fabs(__dsub_rn(__dadd_rn(a, c), __dmul_rn(2.0, b)));
+  const double den = __dadd_rn(__dadd_rn(__dadd_rn(fabs(a), fabs(c)), __dmul_rn(2.0, fabs(b))), eps);
+  return __ddiv_rn(num, den) >= 0.95;
+}
+
+// The same decision screened in FP32 on the shell's scale. With den_f >= 2^-80 the flushed values
+// and the FP32 rounding of eps do not count, and the truncated inputs plus the roundings of num
+// and den move sigma by less than 1e-6; a margin of 4e-6 around 0.95 (and the rounding of the
+// products below) therefore settles every cell outside the band exactly as the FP64 expression
+// does. Cells inside the band, or with a flagged input, take the FP64 expression.
+__device__ __forceinline__ bool jameson(double a, double b, double c, float af, float bf, float cf, bool bad,
+                                        float epsf, double eps) {
+  const float num = fabsf(__fsub_rn(__fadd_rn(af, cf), 2.0f * bf));
+  const float den = __fadd_rn(__fadd_rn(__fadd_rn(fabsf(af), fabsf(cf)), 2.0f * fabsf(bf)), epsf);
+  if (!bad && den >= 0x1p-80f) {
+    if (num >= __fmul_rn(0.950004f, den)) return true;
+    if (num < __fmul_rn(0.949996f, den)) return false;
+  }
+  return jameson_exact(a, b, c, eps);
+}
+
+// Jameson's shock detector of the hybrid filter (Sec. II.C) on the FP64 shell at shared address S
+// (row stride lds): ring[j] = 1 if some cell of phi ring j has sigma >= 0.95, circ[k] = 1 likewise
+// for theta circle k < Nphi/2 (meridians k and k + Nphi/2 joined over the poles, the values across
+// a pole with the parity sign). misc[5] = 1 if some circle fired; misc[6] is scratch. Called by
+// every thread of the CTA; the caller synchronises afterwards.
+template <int LEN>
+__device__ __noinline__ void detect_shell(uint32_t S, int lds, int Nth, int Nph, bool odd, double eps,
+                                          unsigned char* circ, unsigned char* ring, int* misc) {
+  if constexpr (LEN > 0) {
+    Nth = LEN / 2;
+    Nph = LEN;
+    lds = LEN + 2;
+  }
+  const int npts = Nth * Nph, h = Nph / 2;
+  auto at = [&](int j, int k) { return F64::ld8(S + 8u * (uint32_t)(j * lds + k)); };
+  for (int n = threadIdx.x; n < h + Nth; n += blockDim.x) circ[n] = 0;  // circ, then ring
+  if (threadIdx.x == 0) {
+    misc[5] = 0;
+    misc[6] = 0;
+  }
+  unsigned em = 0;
+  for (int n = threadIdx.x; n < npts; n += blockDim.x) {
+    const int j = n / Nph;
+    const unsigned e = (unsigned)((unsigned long long)__double_as_longlong(at(j, n - j * Nph)) >> 52) & 0x7ffu;
+    if (e != 0x7ffu) em = max(em, e);
+  }
+  em = __reduce_max_sync(0xffffffffu, em);
+  __syncthreads();  // flags and misc cleared
+  if ((threadIdx.x & 31) == 0) atomicMax(&misc[6], (int)em);
+  __syncthreads();
+  const int emax = misc[6];
+  const float epsf = __double2float_rn(scalbn(eps, 1023 - emax));
+  const unsigned long long flip = odd ? 0x8000000000000000ull : 0ull;
+  bool fired = false;
+  for (int n = threadIdx.x; n < npts; n += blockDim.x) {
+    const int j = n / Nph, k = n - j * Nph;
+    const int ko = k < h ? k + h : k - h;  // the meridian across the pole
+    const double b = at(j, k);
+    const double pa = at(j, k == 0 ? Nph - 1 : k - 1), pc = at(j, k == Nph - 1 ? 0 : k + 1);
+    const double ta = j > 0 ? at(j - 1, k) : __longlong_as_double(__double_as_longlong(at(0, ko)) ^ flip);
+    const double tc = j < Nth - 1 ? at(j + 1, k) : __longlong_as_double(__double_as_longlong(at(Nth - 1, ko)) ^ flip);
+    bool badb = false;
+    const float bf = screen_value(b, emax, badb);
+    bool badp = badb, badt = badb;
+    const float paf = screen_value(pa, emax, badp), pcf = screen_value(pc, emax, badp);
+    const float taf = screen_value(ta, emax, badt), tcf = screen_value(tc, emax, badt);
+    if (jameson(pa, b, pc, paf, bf, pcf, badp, epsf, eps)) ring[j] = 1;
+    if (jameson(ta, b, tc, taf, bf, tcf, badt, epsf, eps)) {
+      circ[k < h ? k : k - h] = 1;
+      fired = true;
+    }
+  }
+  if (__any_sync(0xffffffffu, fired) && (threadIdx.x & 31) == 0) misc[5] = 1;
+}
+
+// HYB: the kernel variant for launches with hybrid fields (the other variant has none of their code).
+template <class P, int LEN, bool HYB>
 __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layout<P>& L, unsigned char* buf, int s,
                              const Consts<P>& K) {
   constexpr bool dfp = std::is_same<P, DF>::value;
@@ -859,16 +959,29 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
   // per-shell tables: theta multipliers, phi ring pairs, rows that will be transformed
   const double lmax = A.lmax[vi.cls * A.Nr + i];
   const bool gauss = vi.kind == SPH_FILTER_GAUSS;
-  const bool theta_on = gauss || lmax < (double)Nth;
+  const bool hyb = HYB && vi.kind == SPH_FILTER_HYBRID;
   const size_t gth_base = ((size_t)vi.cls * A.Nr + i) * (Nth + 1);
-  // theta multipliers: 8-byte table entries copied as they are (FP64, or an FP32 pair)
-  for (int n = threadIdx.x; n <= Nth; n += blockDim.x)
+  const size_t gth_alt = ((size_t)vi.alt_cls * A.Nr + i) * (Nth + 1);
+  // theta multipliers: 8-byte table entries copied as they are (FP64, or an FP32 pair); a hybrid
+  // field's Gaussian row follows its exponential one
+  for (int n = threadIdx.x; n < (hyb ? 2 : 1) * (Nth + 1); n += blockDim.x) {
+    const size_t t = n <= Nth ? gth_base + n : gth_alt + (n - (Nth + 1));
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(L.g_th + 8u * n),
-                 "l"(static_cast<const unsigned char*>(A.g_th) + 8 * (gth_base + n))
+                 "l"(static_cast<const unsigned char*>(A.g_th) + 8 * t)
                  : "memory");
+  }
   asm volatile("cp.async.commit_group;" ::: "memory");
+  if (hyb) {
+    // a hybrid field's choices come from the whole FP64 shell: wait for it, run the detector
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    detect_shell<LEN>(saddr(buf), ld, Nth, Nph, vi.parity != 0, A.eps, L.circ, L.ring, L.misc);
+    __syncthreads();
+  }
+  const bool theta_on = gauss || lmax < (double)Nth || (hyb && L.misc[5] != 0);
   for (int j = threadIdx.x; j < Nth; j += blockDim.x) L.rowact[j] = theta_on ? 1 : 0;
   const uint8_t* ring_info = A.ring_info + ((size_t)vi.cls * A.Nr + i) * Nth;
+  const uint8_t* ring_alt = A.ring_info + ((size_t)vi.alt_cls * A.Nr + i) * Nth;
   __syncthreads();
   if (threadIdx.x < 32) {
     // active ring pairs in ascending j, compacted by one warp (ballot + prefix count)
@@ -878,13 +991,17 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
       const int j = j0 + (int)lane, jj = Nth - 1 - j;
       const bool in = j < (Nth + 1) / 2;
       const uint8_t a = in ? ring_info[j] : 0, b = in ? ring_info[jj] : 0;
-      const bool act = ((a | b) & 1) != 0;  // bit 0: ring active
-      const int g = (a >> 1) & 1;           // bit 1: multipliers of j and its mirror differ
+      // hybrid field: a ring whose detector fired takes the Gaussian table (never the identity)
+      const int fa = (hyb && in) ? L.ring[j] : 0, fb = (hyb && in) ? L.ring[jj] : 0;
+      const bool act = ((a | b) & 1) != 0 || fa || fb;  // bit 0: ring active
+      // the multipliers of j and its mirror differ: different tables, or one table whose cutoffs
+      // differ beyond rounding (bit 1)
+      const int g = fa != fb ? 1 : ((fa ? (in ? ring_alt[j] : 0) : a) >> 1) & 1;
       const unsigned m = __ballot_sync(0xffffffffu, act);
       if (act) {
         const int pos = np + __popc(m & ((1u << lane) - 1u));
         L.rowact[j] = L.rowact[jj] = 1;
-        L.pairs[pos] = jj == j ? make_int2(j, -1) : make_int2(j | (g << 30), jj);
+        L.pairs[pos] = jj == j ? make_int2(j | (fa << 29), -1) : make_int2(j | (g << 30) | (fa << 29) | (fb << 28), jj);
       }
       gen |= __any_sync(0xffffffffu, act && jj != j && g) ? 1 : 0;
       np += __popc(m);
@@ -899,10 +1016,27 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
       if (act) L.arow[na + __popc(m & ((1u << lane) - 1u))] = (unsigned short)j;
       na += __popc(m);
     }
+    // hybrid field: table of each theta sequence (circles 2b, 2b+1): 0 exponential, 1 Gaussian,
+    // 2 one of each (split multiply); a lone last circle counts twice
+    int gth = 0;
+    if (hyb) {
+      const int h = Nph / 2, nseq = (h + 1) / 2;
+      for (int b0 = 0; b0 < nseq; b0 += 32) {
+        const int b = b0 + (int)lane;
+        int t = 0;
+        if (b < nseq) {
+          const int c1 = L.circ[2 * b], c2 = 2 * b + 1 < h ? L.circ[2 * b + 1] : c1;
+          t = c1 == c2 ? c1 : 2;
+          L.thsel[b] = (unsigned char)t;
+        }
+        gth |= __any_sync(0xffffffffu, t == 2) ? 1 : 0;
+      }
+    }
     if (lane == 0) {
       L.misc[0] = np;
       L.misc[1] = gen;
       L.misc[3] = na;
+      L.misc[4] = gth;
     }
   }
   if (in_place_sparse<LEN>(io)) {
@@ -960,12 +1094,16 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
   __syncthreads();
   const int npairs = L.misc[0];
   const bool has_general = L.misc[1] != 0;
+  const bool th_general = hyb && L.misc[4] != 0;
 
   ThetaAcc<P> TA;
   TA.S = saddr(buf);
   TA.ov = L.ov;
   TA.lin = L.lin;
   TA.g = L.g_th;
+  TA.sel = L.thsel;
+  TA.circ = L.circ;
+  TA.hyb = hyb;
   TA.ld = ld;
   TA.Nth = Nth;
   TA.Nth8 = Nth & ~7;
@@ -985,6 +1123,8 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
   PA.pairs = L.pairs;
   PA.gtab = A.g_ph;
   PA.gbase = ((size_t)vi.cls * A.Nr + i) * (size_t)Nth * (Nph / 2 + 1);
+  PA.gbase_alt = ((size_t)vi.alt_cls * A.Nr + i) * (size_t)Nth * (Nph / 2 + 1);
+  PA.hyb = hyb;
   PA.ld = ld;
   PA.N = Nph;
   PA.N8 = Nph & ~7;
@@ -996,9 +1136,13 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
   // the filter: theta pass then phi pass, or the reverse order for the transpose
   for (int step = 0; step < 2; ++step) {
     if ((step == 0) != (io.transpose != 0)) {
-      if (theta_on) theta_pass_fn<P, LEN>(TA, A.f_th, L.tw_th, K, A.batch_th);
-    } else {
-      if (npairs) phi_pass_fn<P, LEN>(PA, npairs, has_general, A.f_ph, L.tw_ph, K, A.batch_ph);
+      if (theta_on) {
+        if (hyb) theta_pass_fn<P, LEN, false, true>(TA, A.f_th, L.tw_th, K, A.batch_th, th_general);
+        else theta_pass_fn<P, LEN>(TA, A.f_th, L.tw_th, K, A.batch_th, false);
+      }
+    } else if (npairs) {
+      if (hyb) phi_pass_fn<P, LEN, true>(PA, npairs, has_general, A.f_ph, L.tw_ph, K, A.batch_ph);
+      else phi_pass_fn<P, LEN>(PA, npairs, has_general, A.f_ph, L.tw_ph, K, A.batch_ph);
     }
   }
 
@@ -1056,7 +1200,7 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
   }
 }
 
-template <class P, int LEN>
+template <class P, int LEN, bool HYB>
 __global__ void __launch_bounds__(512) shell_kernel(ShellArgs2 A, LaunchIO io) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Layout<P> L = carve<P>(A, smem_raw);
@@ -1076,7 +1220,7 @@ __global__ void __launch_bounds__(512) shell_kernel(ShellArgs2 A, LaunchIO io) {
   K.c8 = P::from_tab(A.consts, 0);
   K.s3 = P::from_tab(A.consts, 1);
 
-  filter_shell<P, LEN>(A, io, L, L.buf, sidx, K);
+  filter_shell<P, LEN, HYB>(A, io, L, L.buf, sidx, K);
 }
 
 
@@ -1321,6 +1465,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512) shell_kernel_cl
   TA.odd = vi.parity != 0;
   TA.hodd = (Nph / 4) & 1;
   TA.b0 = 0;
+  TA.sel = nullptr;
+  TA.circ = nullptr;
+  TA.hyb = false;  // plans with hybrid fields do not run on CTA pairs
 
   PhiSplitAcc<P> PA;
   PA.A = L.A;
@@ -1368,13 +1515,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512) shell_kernel_cl
   };
 
   if (fwd) {
-    if (theta_on) theta_pass_fn<P, LEN, true>(TA, A.f_th, L.tw_th, K, A.batch_th);
+    if (theta_on) theta_pass_fn<P, LEN, true>(TA, A.f_th, L.tw_th, K, A.batch_th, false);
     exchange();
     if (npairs) phi_split_pass_fn<P, LEN>(PA, npairs, has_general, A.f_ph, L.tw_ph, K, A.batch_ph);
   } else {
     if (npairs) phi_split_pass_fn<P, LEN>(PA, npairs, has_general, A.f_ph, L.tw_ph, K, A.batch_ph);
     exchange();
-    if (theta_on) theta_pass_fn<P, LEN, true>(TA, A.f_th, L.tw_th, K, A.batch_th);
+    if (theta_on) theta_pass_fn<P, LEN, true>(TA, A.f_th, L.tw_th, K, A.batch_th, false);
   }
   __syncthreads();
 
@@ -1420,24 +1567,25 @@ size_t shell_smem(const ShellArgs2& a) {
   s += up(16 * (size_t)std::max(2 * a.Nth, a.Nph));
   s += up(16 * 2 * (size_t)a.Nth);
   s += up(16 * (size_t)a.Nph);
-  s += up(8 * (size_t)(a.Nth + 1));
+  s += up(16 * (size_t)(a.Nth + 1));
   s += up(sizeof(int2) * (size_t)(a.Nth / 2 + 1));
-  s += up(sizeof(int) * 4);
+  s += up(sizeof(int) * 8);
   s += up((size_t)a.Nth);
   s += up(sizeof(unsigned short) * (size_t)a.Nth);
+  s += up((size_t)(a.Nph / 2 + a.Nth + (a.Nph / 2 + 1) / 2));
   return s;
 }
 
-template <class P, int LEN>
+template <class P, int LEN, bool HYB>
 cudaError_t launch_impl(const ShellArgs2& a, int threads, size_t smem, const LaunchIO& io, cudaStream_t s) {
   const dim3 grid((unsigned)(io.var_count * a.Nr));
-  shell_kernel<P, LEN><<<grid, threads, smem, s>>>(a, io);
+  shell_kernel<P, LEN, HYB><<<grid, threads, smem, s>>>(a, io);
   return cudaGetLastError();
 }
 
-template <class P, int LEN>
+template <class P, int LEN, bool HYB>
 cudaError_t set_attr_impl(int bytes) {
-  return cudaFuncSetAttribute(shell_kernel<P, LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return cudaFuncSetAttribute(shell_kernel<P, LEN, HYB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 template <class P>

@@ -137,13 +137,15 @@ def band_limited_state(grid: Grid, seed: int, mode_max: int, noise: float,
     return out.reshape(grid.shape)
 
 
-def star_state(grid: Grid, seed: int, mode_max: int = 4, noise: float = 0.05) -> np.ndarray:
+def star_state(grid: Grid, seed: int, mode_max: int = 4, noise: float = 0.05, centre_r: float = None,
+               radius: float = None) -> np.ndarray:
     """Fields of hybrid kind get a "star": rho = 1 inside a ball, 1e-10 (atmosphere) outside, times a
     smooth factor: rho (1 + g / 2) for even fields, rho g for odd ones, g a random band-limited
     field of that parity (modes l, m <= mode_max) scaled to max |g| = 1. The ball has radius
-    0.234 Nr around the point at radius 0.3125 Nr, theta = pi/3, phi = 0.5 (shells r = i + 1/2),
-    so the middle shells cut its surface. The other fields are band_limited_state(mode_max =
-    Nphi / 8, noise). No noise on the star fields: their smooth parts keep Jameson's sigma small."""
+    `radius` (default 0.234 Nr) around the point at radius `centre_r` (default 0.3125 Nr),
+    theta = pi/3, phi = 0.5, so that with shells r = i + 1/2 the middle shells cut its surface.
+    The other fields are band_limited_state(mode_max = Nphi / 8, noise). No noise on the star
+    fields: their smooth parts keep Jameson's sigma small."""
     x = band_limited_state(grid, seed, mode_max=max(1, grid.Nphi // 8), noise=noise)
     hyb = [v for v in range(grid.nvars) if grid.kind[v] == HYBRID]
     if not hyb:
@@ -154,7 +156,9 @@ def star_state(grid: Grid, seed: int, mode_max: int = 4, noise: float = 0.05) ->
     sp, cp = np.sin(ph)[None, None, :], np.cos(ph)[None, None, :]
     rr = r[:, None, None]
     X, Y, Z = rr * st * cp, rr * st * sp, rr * ct * np.ones_like(cp)
-    rc, tc, pc, R = 0.3125 * grid.Nr, np.pi / 3, 0.5, 0.234375 * grid.Nr
+    rc = 0.3125 * grid.Nr if centre_r is None else centre_r
+    R = 0.234375 * grid.Nr if radius is None else radius
+    tc, pc = np.pi / 3, 0.5
     cx, cy, cz = rc * np.sin(tc) * np.cos(pc), rc * np.sin(tc) * np.sin(pc), rc * np.cos(tc)
     rho = np.where((X - cx) ** 2 + (Y - cy) ** 2 + (Z - cz) ** 2 < R * R, 1.0, 1e-10)
     rng = np.random.default_rng([seed, 2])

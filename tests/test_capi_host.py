@@ -51,14 +51,14 @@ def test_status_strings(lib):
 
 
 def _create(lib, Nr=2, Nth=4, Nph=8, parity=(0,), kind=(0,), L=(3.0,), r=None, dr_min=1.0, floor=2.0,
-            precision=0):
+            precision=0, eps=1e-12):
     from paper_2305_01537_gb300 import binding
     nv = len(parity)
     par = np.asarray(parity, dtype=np.int32)
     kd = np.asarray(kind, dtype=np.int32)
     Ls = np.asarray(L, dtype=np.float64)
     rs = np.asarray(r if r is not None else np.arange(Nr) + 0.5, dtype=np.float64)
-    prm = binding.sph_cutoff_params(rs.ctypes.data, dr_min, Ls.ctypes.data, kd.ctypes.data, floor, precision)
+    prm = binding.sph_cutoff_params(rs.ctypes.data, dr_min, Ls.ctypes.data, kd.ctypes.data, floor, precision, eps)
     h = ctypes.c_void_p()
     st = lib.sph_filter_plan_create(ctypes.byref(h), Nr, Nth, Nph, nv, par.ctypes.data, ctypes.byref(prm))
     if st == 0:
@@ -73,7 +73,11 @@ def test_plan_create_rejects_invalid_arguments(lib):
     assert _create(lib, Nr=0) == EINVAL
     assert _create(lib, Nth=0) == EINVAL
     assert _create(lib, parity=(2,)) == EINVAL
-    assert _create(lib, kind=(3,)) == EINVAL
+    assert _create(lib, kind=(4,)) == EINVAL
+    assert _create(lib, kind=(-1,)) == EINVAL
+    assert _create(lib, kind=(3,), eps=-1.0) == EINVAL         # hybrid field: eps >= 0 and finite
+    assert _create(lib, kind=(3,), eps=float("nan")) == EINVAL
+    assert _create(lib, kind=(3,), eps=float("inf")) == EINVAL
     assert _create(lib, L=(0.0,)) == EINVAL
     assert _create(lib, r=[0.5, -1.0]) == EINVAL
     assert _create(lib, dr_min=0.0) == EINVAL
@@ -82,6 +86,12 @@ def test_plan_create_rejects_invalid_arguments(lib):
     h = ctypes.c_void_p()
     assert lib.sph_filter_plan_create(ctypes.byref(h), 2, 4, 8, 1, None, None) == EINVAL
     assert lib.sph_filter_plan_create(None, 2, 4, 8, 1, None, None) == EINVAL
+
+
+def test_hybrid_plans_the_tensor_core_form_cannot_run(lib):
+    """The split-precision tensor-core form has no per-circle filter switch: a hybrid field there is
+    rejected before any device work (SPH_EUNSUPPORTED)."""
+    assert _create(lib, kind=(0, 3), parity=(0, 1), L=(3.0, 12.0), precision=1) == 4
 
 
 def test_calls_on_null_plan_are_rejected(lib):
