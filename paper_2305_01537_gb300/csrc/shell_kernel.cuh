@@ -831,48 +831,71 @@ __device__ __forceinline__ void issue_load(const ShellArgs2& A, const LaunchIO& 
 // ------------------------------------------------------------------ hybrid filter: shock detector
 
 // x 2^-E as FP32 for the detector's screen, E = emax - 1023 with emax the largest exponent field of
-// the shell's finite values (so |x 2^-E| < 2): the significand truncated to 24 bits (relative error
-// below 2^-23), values under 2^-120 on that scale set to 0. Subnormal, infinite and NaN inputs set
-// `bad` (their cells are decided exactly); zero converts exactly.
-__device__ __forceinline__ float screen_value(double x, int emax, bool& bad) {
+// the shell's finite values (so |x 2^-E| < 2), from the high word of x alone: the significand keeps
+// its 20 leading bits (relative error below 2^-20), values under 2^-120 on that scale become 0.
+// Subnormal, infinite and NaN inputs give NaN, which sends their cells to the exact decision;
+// zero converts exactly.
+__device__ __forceinline__ float screen_value(double x, int emax) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+  const unsigned hi = (unsigned)(u >> 32);
   const int e = (int)((hi >> 20) & 0x7ffu);
-  bad |= e == 0x7ff || (e == 0 && (u << 1) != 0ull);
   const int fe = e - emax + 127;  // FP32 biased exponent on the shell's scale
-  const unsigned bits = (hi & 0x80000000u) | ((unsigned)fe << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
-  return fe >= 7 ? __uint_as_float(bits) : 0.0f;
+  const float v = __uint_as_float((hi & 0x80000000u) | ((unsigned)fe << 23) | ((hi & 0xfffffu) << 3));
+  if ((unsigned)(e - 1) >= 0x7feu)  // zero, subnormal, infinite or NaN
+    return (u << 1) == 0ull ? 0.0f : __int_as_float(0x7fffffff);
+  return fe >= 7 ? v : 0.0f;
+}
+
+// The same conversion for the column walk, for shells whose values are all zero or normal and whose
+// emax is at least 128: |x| is clamped to the scale's 2^-120 floor (floor_a = (emax - 120) << 20 on
+// the high word without its sign; an absolute change below 2^-119, like the flush above), then the
+// exponent is rebased (adj = (emax - 127) << 20) and moved into place.
+__device__ __forceinline__ float screen_value_walk(double x, unsigned floor_a, unsigned adj) {
+  const unsigned hi = (unsigned)((unsigned long long)__double_as_longlong(x) >> 32);
+  const unsigned a = max(hi & 0x7fffffffu, floor_a);
+  return __uint_as_float(((a - adj) << 3) | (hi & 0x80000000u));
 }
 
 // Jameson's sigma >= 0.95 for the cell b between a and c, in FP64 with round-to-nearest, operation
-// for operation: num = |(a + c) - 2 b|, den = ((|a| + |c|) + 2 |b|) + eps, num / den >= 0.95.
-__device__ __forceinline__ bool jameson_exact(double a, double b, double c, double eps) {
+// for operation: num = |(a + c) - 2 b|, den = ((|a| + |c|) + 2 |b|) + eps, num / den >= 0.95. Out of
+// line, so that the compiler cannot evaluate it ahead of the screen that rarely needs it (the FP64
+// pipe is slow on this GPU). A template only to give it one definition per translation unit.
+template <int = 0>
+__device__ __noinline__ bool jameson_exact(double a, double b, double c, double eps) {
   const double num = fabs(__dsub_rn(__dadd_rn(a, c), __dmul_rn(2.0, b)));
   const double den = __dadd_rn(__dadd_rn(__dadd_rn(fabs(a), fabs(c)), __dmul_rn(2.0, fabs(b))), eps);
   return __ddiv_rn(num, den) >= 0.95;
 }
 
-// The same decision screened in FP32 on the shell's scale. With den_f >= 2^-80 the flushed values
-// and the FP32 rounding of eps do not count, and the truncated inputs plus the roundings of num
-// and den move sigma by less than 1e-6; a margin of 4e-6 around 0.95 (and the rounding of the
-// products below) therefore settles every cell outside the band exactly as the FP64 expression
-// does. Cells inside the band, or with a flagged input, take the FP64 expression.
-__device__ __forceinline__ bool jameson(double a, double b, double c, float af, float bf, float cf, bool bad,
-                                        float epsf, double eps) {
-  const float num = fabsf(__fsub_rn(__fadd_rn(af, cf), 2.0f * bf));
-  const float den = __fadd_rn(__fadd_rn(__fadd_rn(fabsf(af), fabsf(cf)), 2.0f * fabsf(bf)), epsf);
-  if (!bad && den >= 0x1p-80f) {
-    if (num >= __fmul_rn(0.950004f, den)) return true;
-    if (num < __fmul_rn(0.949996f, den)) return false;
+// The same decision screened in FP32 on the shell's scale: 1 fires, 0 does not, -1 undecided.
+// Error budget: the inputs carry relative errors below 2^-20, so num and den move by less than
+// 2^-20 D each (D = |a| + 2|b| + |c| <= den), and their four FP32 roundings add less than 2^-22 den;
+// with den_f >= 2^-80 the flushed values and the rounding of eps do not count. Hence
+// |num_f - sigma den_f| < 2.3e-6 den_f, and s = num_f - 0.95 den_f (one FMA, 0.95f within 1.2e-8
+// of 0.95) decides every cell with |sigma - 0.95| > 4e-6 exactly as the FP64 expression does.
+// Cells inside the band, or with a NaN (flagged) input, are undecided and take that expression.
+__device__ __forceinline__ int jameson_screen(float af, float bf, float cf, float epsf) {
+  const float num = fabsf(__fmaf_rn(-2.0f, bf, __fadd_rn(af, cf)));
+  const float den = __fadd_rn(__fmaf_rn(2.0f, fabsf(bf), __fadd_rn(fabsf(af), fabsf(cf))), epsf);
+  const float sv = __fmaf_rn(-0.95f, den, num), m = 4e-6f * den;
+  if (den >= 0x1p-80f) {
+    if (sv >= m) return 1;
+    if (sv < -m) return 0;
   }
-  return jameson_exact(a, b, c, eps);
+  return -1;
 }
 
 // Jameson's shock detector of the hybrid filter (Sec. II.C) on the FP64 shell at shared address S
 // (row stride lds): ring[j] = 1 if some cell of phi ring j has sigma >= 0.95, circ[k] = 1 likewise
 // for theta circle k < Nphi/2 (meridians k and k + Nphi/2 joined over the poles, the values across
-// a pole with the parity sign). misc[5] = 1 if some circle fired; misc[6] is scratch. Called by
+// a pole with the parity sign). misc[5] = 1 if some circle fired; misc[6] receives emax. Called by
 // every thread of the CTA; the caller synchronises afterwards.
+// When Nphi is a multiple of 32, thread t walks meridian t mod Nphi down one band of rows: each
+// value is read and converted once, the theta neighbours are the previous and the next row of the
+// walk, and the phi neighbours come from the adjacent lanes (a warp holds 32 consecutive meridians
+// of one band; its edge lanes read theirs); it only screens. Without the walk (other Nphi, shells
+// with subnormal or non-finite values or emax < 128), or when the screen left a cell undecided,
+// every cell reads its four neighbours and undecided cells take the FP64 expression.
 template <int LEN>
 __device__ __noinline__ void detect_shell(uint32_t S, int lds, int Nth, int Nph, bool odd, double eps,
                                           unsigned char* circ, unsigned char* ring, int* misc) {
@@ -883,41 +906,81 @@ __device__ __noinline__ void detect_shell(uint32_t S, int lds, int Nth, int Nph,
   }
   const int npts = Nth * Nph, h = Nph / 2;
   auto at = [&](int j, int k) { return F64::ld8(S + 8u * (uint32_t)(j * lds + k)); };
+  const unsigned long long flip = odd ? 0x8000000000000000ull : 0ull;
+  auto across = [&](double x) { return __longlong_as_double(__double_as_longlong(x) ^ flip); };
   for (int n = threadIdx.x; n < h + Nth; n += blockDim.x) circ[n] = 0;  // circ, then ring
   if (threadIdx.x == 0) {
     misc[5] = 0;
     misc[6] = 0;
   }
   unsigned em = 0;
+  bool special = false;  // a subnormal, infinite or NaN value
   for (int n = threadIdx.x; n < npts; n += blockDim.x) {
     const int j = n / Nph;
-    const unsigned e = (unsigned)((unsigned long long)__double_as_longlong(at(j, n - j * Nph)) >> 52) & 0x7ffu;
+    const unsigned long long u = (unsigned long long)__double_as_longlong(at(j, n - j * Nph));
+    const unsigned e = (unsigned)(u >> 52) & 0x7ffu;
+    special |= e == 0x7ffu || (e == 0u && (u << 1) != 0ull);
     if (e != 0x7ffu) em = max(em, e);
   }
   em = __reduce_max_sync(0xffffffffu, em);
   __syncthreads();  // flags and misc cleared
   if ((threadIdx.x & 31) == 0) atomicMax(&misc[6], (int)em);
-  __syncthreads();
+  const bool any_special = __syncthreads_or(special) != 0;
   const int emax = misc[6];
   const float epsf = __double2float_rn(scalbn(eps, 1023 - emax));
-  const unsigned long long flip = odd ? 0x8000000000000000ull : 0ull;
-  bool fired = false;
-  for (int n = threadIdx.x; n < npts; n += blockDim.x) {
-    const int j = n / Nph, k = n - j * Nph;
-    const int ko = k < h ? k + h : k - h;  // the meridian across the pole
-    const double b = at(j, k);
-    const double pa = at(j, k == 0 ? Nph - 1 : k - 1), pc = at(j, k == Nph - 1 ? 0 : k + 1);
-    const double ta = j > 0 ? at(j - 1, k) : __longlong_as_double(__double_as_longlong(at(0, ko)) ^ flip);
-    const double tc = j < Nth - 1 ? at(j + 1, k) : __longlong_as_double(__double_as_longlong(at(Nth - 1, ko)) ^ flip);
-    bool badb = false;
-    const float bf = screen_value(b, emax, badb);
-    bool badp = badb, badt = badb;
-    const float paf = screen_value(pa, emax, badp), pcf = screen_value(pc, emax, badp);
-    const float taf = screen_value(ta, emax, badt), tcf = screen_value(tc, emax, badt);
-    if (jameson(pa, b, pc, paf, bf, pcf, badp, epsf, eps)) ring[j] = 1;
-    if (jameson(ta, b, tc, taf, bf, tcf, badt, epsf, eps)) {
-      circ[k < h ? k : k - h] = 1;
-      fired = true;
+  bool fired = false, undecided = false;
+  const int bands = (Nph & 31) == 0 && !any_special && emax >= 128 ? (int)blockDim.x / Nph : 0;
+  if (bands > 0) {
+    const unsigned floor_a = (unsigned)(emax - 120) << 20, adj = (unsigned)(emax - 127) << 20;
+    const int t = threadIdx.x, k = t % Nph, g = t / Nph, lane = t & 31;
+    if (g < bands) {  // whole warps
+      const int j0 = g * Nth / bands, j1 = (g + 1) * Nth / bands;
+      const int ko = k < h ? k + h : k - h;  // the meridian across the pole
+      // the phi neighbour a lane cannot take from the adjacent lane: left for lane 0, right for 31
+      const int ke = lane == 0 ? (k == 0 ? Nph - 1 : k - 1) : (k == Nph - 1 ? 0 : k + 1);
+      const int c = k < h ? k : k - h;
+      float upf = screen_value_walk(j0 > 0 ? at(j0 - 1, k) : across(at(0, ko)), floor_a, adj);
+      float cuf = screen_value_walk(at(j0, k), floor_a, adj);
+#pragma unroll 2
+      for (int j = j0; j < j1; ++j) {
+        const float dnf = screen_value_walk(j < Nth - 1 ? at(j + 1, k) : across(at(Nth - 1, ko)), floor_a, adj);
+        const float ef = screen_value_walk(at(j, ke), floor_a, adj);
+        int d = jameson_screen(upf, cuf, dnf, epsf);
+        undecided |= d < 0;
+        if (d > 0) {
+          circ[c] = 1;
+          fired = true;
+        }
+        const float lsh = __shfl_up_sync(0xffffffffu, cuf, 1), rsh = __shfl_down_sync(0xffffffffu, cuf, 1);
+        d = jameson_screen(lane == 0 ? ef : lsh, cuf, lane == 31 ? ef : rsh, epsf);
+        undecided |= d < 0;
+        if (d > 0) ring[j] = 1;
+        upf = cuf;
+        cuf = dnf;
+      }
+    }
+  }
+  // a shell with an undecided cell anywhere (rare) takes the cell-by-cell pass below, which repeats
+  // every decision (the same screen) and settles the undecided ones with the FP64 expression
+  const bool per_cell = bands > 0 ? __syncthreads_or(undecided) != 0 : true;
+  if (per_cell) {
+    for (int n = threadIdx.x; n < npts; n += blockDim.x) {
+      const int j = n / Nph, k = n - j * Nph;
+      const int ko = k < h ? k + h : k - h;
+      const double b = at(j, k);
+      const double pa = at(j, k == 0 ? Nph - 1 : k - 1), pc = at(j, k == Nph - 1 ? 0 : k + 1);
+      const double ta = j > 0 ? at(j - 1, k) : across(at(0, ko));
+      const double tc = j < Nth - 1 ? at(j + 1, k) : across(at(Nth - 1, ko));
+      const float bf = screen_value(b, emax);
+      int d = jameson_screen(screen_value(pa, emax), bf, screen_value(pc, emax), epsf);
+      if (d < 0) d = jameson_exact(pa, b, pc, eps);
+      if (d) ring[j] = 1;
+      d = jameson_screen(screen_value(ta, emax), bf, screen_value(tc, emax), epsf);
+      if (d < 0) d = jameson_exact(ta, b, tc, eps);
+      if (d) {
+        circ[k < h ? k : k - h] = 1;
+        fired = true;
+      }
     }
   }
   if (__any_sync(0xffffffffu, fired) && (threadIdx.x & 31) == 0) misc[5] = 1;

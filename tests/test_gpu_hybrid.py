@@ -103,12 +103,15 @@ def test_mixed_circle_pairs_and_mirror_rings(torch_cuda, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_decisions_inside_the_screening_band(torch_cuda, prec):
+@pytest.mark.parametrize("Nth,Nph", [(12, 24), (16, 32), (32, 64), (64, 128)])
+def test_decisions_inside_the_screening_band(torch_cuda, prec, Nth, Nph):
     """Cells whose sigma lies within 1e-7 of 0.95, on both sides, in rings and in circles: the
     kernel must take the exact FP64 decision there. A ring (1, x, 1, 1, x, 1, ...) has sigma =
-    (1 - x) / (1 + x) at its x cells and 1/3 elsewhere, so x near 1/39 decides it."""
+    (1 - x) / (1 + x) at its x cells and about 1/3 elsewhere, so x near 1/39 decides it. Nphi a
+    multiple of 32 takes the kernel's column walk, whose undecided cells send the shell to the
+    cell-by-cell pass; Nphi = 24 takes that pass directly."""
     rng = np.random.default_rng(3)
-    Nth, Nph, Nr = 12, 24, 6
+    Nr = 6
     g = W.Grid(Nr, Nth, Nph, [0], [HYB], [2.0], r=np.linspace(0.5, 30.5, Nr), eps=0.0)
     x = np.ones(g.shape)
     x0 = 1.0 / 39.0
