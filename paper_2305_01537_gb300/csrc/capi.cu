@@ -442,6 +442,12 @@ sph_status sph_filter_plan_create(sph_filter_plan* out, int Nr, int Ntheta, int 
   }
   // the staged shell kernel when the shape fits it; otherwise the chunked FP64 kernel
   p->args2.eps = prm->eps;
+  {
+    int e = 0;
+    const double m = std::frexp(prm->eps, &e);  // eps = m 2^e, 0.5 <= m < 1 (m = 0 for eps = 0)
+    p->args2.eps_m = (float)m;
+    p->args2.eps_p = e;
+  }
   st = setup_v2(p);
   if (st != SPH_OK && st != SPH_EUNSUPPORTED) {
     free_plan(p);

@@ -81,6 +81,8 @@ struct ShellArgs2 {
   const void* consts;         // [2] sqrt(1/2), sqrt(3)/2
   unsigned* status;
   double eps;                 // epsilon of Jameson's detector (hybrid fields)
+  float eps_m;                // eps = eps_m 2^eps_p, eps_m an FP32 rounding of its significand (the
+  int eps_p;                  // detector's FP32 screen scales it without FP64 arithmetic)
 };
 
 // Instantiations of the staged shell kernel, one per (compensated precision?, FFT length, hybrid

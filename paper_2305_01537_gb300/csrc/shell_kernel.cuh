@@ -897,8 +897,8 @@ __device__ __forceinline__ int jameson_screen(float af, float bf, float cf, floa
 // with subnormal or non-finite values or emax < 128), or when the screen left a cell undecided,
 // every cell reads its four neighbours and undecided cells take the FP64 expression.
 template <int LEN>
-__device__ __noinline__ void detect_shell(uint32_t S, int lds, int Nth, int Nph, bool odd, double eps,
-                                          unsigned char* circ, unsigned char* ring, int* misc) {
+__device__ __noinline__ void detect_shell(uint32_t S, int lds, int Nth, int Nph, bool odd, double eps, float eps_m,
+                                          int eps_p, unsigned char* circ, unsigned char* ring, int* misc) {
   if constexpr (LEN > 0) {
     Nth = LEN / 2;
     Nph = LEN;
@@ -927,7 +927,7 @@ __device__ __noinline__ void detect_shell(uint32_t S, int lds, int Nth, int Nph,
   if ((threadIdx.x & 31) == 0) atomicMax(&misc[6], (int)em);
   const bool any_special = __syncthreads_or(special) != 0;
   const int emax = misc[6];
-  const float epsf = __double2float_rn(scalbn(eps, 1023 - emax));
+  const float epsf = ldexpf(eps_m, eps_p + 1023 - emax);  // eps on the scale, in FP32 (0 or inf at the ends)
   bool fired = false, undecided = false;
   const int bands = (Nph & 31) == 0 && !any_special && emax >= 128 ? (int)blockDim.x / Nph : 0;
   if (bands > 0) {
@@ -1038,7 +1038,7 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
     // a hybrid field's choices come from the whole FP64 shell: wait for it, run the detector
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
-    detect_shell<LEN>(saddr(buf), ld, Nth, Nph, vi.parity != 0, A.eps, L.circ, L.ring, L.misc);
+    detect_shell<LEN>(saddr(buf), ld, Nth, Nph, vi.parity != 0, A.eps, A.eps_m, A.eps_p, L.circ, L.ring, L.misc);
     __syncthreads();
   }
   const bool theta_on = gauss || lmax < (double)Nth || (hyb && L.misc[5] != 0);
