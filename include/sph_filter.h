@@ -21,7 +21,9 @@
  *    sph_filter_plan_sync_status().
  *  - There is no CPU fallback: without a usable CUDA device every call fails with SPH_ECUDA.
  *  - The plan is immutable after creation; concurrent calls on different streams with the same
- *    plan are allowed.
+ *    plan are allowed. (The tensor-core form keeps per-CTA scratch in the plan: the library orders
+ *    its launches of one plan one after the other across streams, except inside a CUDA-graph
+ *    capture, whose launches are ordered by the graph.)
  */
 #ifndef SPH_FILTER_H
 #define SPH_FILTER_H
@@ -62,11 +64,11 @@ typedef enum {
  *                    round-to-nearest, in this order. The switch makes the filter nonlinear, so
  *                    plans with hybrid fields run only sph_filter_apply and its FP32-storage,
  *                    host-buffer and batch forms (the adjoint and tanh calls return
- *                    SPH_EUNSUPPORTED), with the FP64 or compensated-FP32 precision and shells
- *                    that fit one CTA's shared memory (the 8 Ntheta (Nphi + 2) bytes of a shell
- *                    plus FFT scratch within 227 KB, e.g. 96 x 192; 128 x 256 shells run on a CTA
- *                    pair, which does not take hybrid fields); other plans with hybrid fields fail
- *                    to create with SPH_EUNSUPPORTED. */
+ *                    SPH_EUNSUPPORTED), with the FP64 or compensated-FP32 precision and the
+ *                    staged shell kernels (one CTA per shell, or a CTA pair for shells such as
+ *                    128 x 256); plans that need the chunked FP64 kernel (lengths with prime
+ *                    factors above 3) or the tensor-core form fail to create with
+ *                    SPH_EUNSUPPORTED. */
 typedef enum { SPH_FILTER_EXP = 0, SPH_FILTER_GAUSS = 1, SPH_FILTER_SHARP = 2, SPH_FILTER_HYBRID = 3 } sph_kind;
 
 /* Arithmetic of the plan's kernels. Inputs and outputs are FP64 for every choice.
@@ -137,8 +139,10 @@ sph_status sph_filter_apply_adjoint_tanh_f32(sph_filter_plan plan, const float* 
 /* End-to-end variant for host-resident states: copies host_in to the device, filters, copies
  * the result to host_out, all on `stream`, and returns after enqueueing. host_in/host_out should
  * be page-locked for the copies to overlap. The device staging buffers are allocated by the plan
- * on first use and kept until the plan is destroyed. Synchronise the stream before reading
- * host_out. Errors as sph_filter_apply, plus SPH_ENOMEM. */
+ * on first use and kept until the plan is destroyed (for the tensor-core form also three more sets
+ * of its per-CTA scratch, one per pipeline stream); calls of this function on one plan share them,
+ * so order such calls (one stream, or a synchronisation between them). Synchronise the stream
+ * before reading host_out. Errors as sph_filter_apply, plus SPH_ENOMEM. */
 sph_status sph_filter_apply_host(sph_filter_plan plan, const double* host_in, double* host_out,
                                  sph_stream_t stream);
 

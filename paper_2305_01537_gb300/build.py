@@ -29,9 +29,8 @@ def nvcc() -> str:
 
 
 # shell_inst.cu is compiled once per (precision, FFT length, hybrid variant) instantiation of the
-# shell kernel; the hybrid variant exists for the lengths one CTA holds (not 256)
-SHELL_INST = [(d, n, h) for d in (0, 1) for n in (0, 32, 64, 96, 128, 192, 256) for h in (0, 1)
-              if not (h and n == 256)]
+# shell kernels (for length 256 the hybrid object holds only the cluster-pair kernel)
+SHELL_INST = [(d, n, h) for d in (0, 1) for n in (0, 32, 64, 96, 128, 192, 256) for h in (0, 1)]
 
 
 def jobs():

@@ -265,6 +265,7 @@ void free_plan(sph_filter_plan_s* p) {
   cudaFree(p->d_status);
   cudaFree(p->d_tabs);
   tc_free(p);
+  if (p->tc_ev) cudaEventDestroy(p->tc_ev);
   cudaFree(p->d_stage_in);
   cudaFree(p->d_stage_out);
   for (cudaStream_t s : p->pipe)
@@ -293,7 +294,7 @@ sph_status launch_plan(sph_filter_plan_s* p, const void* in, const void* aux, vo
 
 sph_status launch_plan_vars(sph_filter_plan_s* p, const void* in, const void* aux, void* out, int map_in,
                             int map_out, int transpose, int is_f32, int var_begin, int var_count,
-                            cudaStream_t stream) {
+                            cudaStream_t stream, int tc_set) {
   if (!p || var_begin < 0 || var_count < 1 || var_begin + var_count > p->nvars) return SPH_EINVAL;
   sph_status st = check_io(p, in, out, is_f32 ? sizeof(float) : sizeof(double));
   if (st != SPH_OK) return st;
@@ -312,8 +313,20 @@ sph_status launch_plan_vars(sph_filter_plan_s* p, const void* in, const void* au
       if (cur != p->device) cudaSetDevice(cur);
       return SPH_EUNSUPPORTED;
     }
-    const cudaError_t e = tc_launch(p, static_cast<const double*>(in), static_cast<double*>(out), transpose,
-                                    var_begin, var_count, (cudaStream_t)stream);
+    // one launch with the main scratch set at a time, whatever the stream; a stream being captured
+    // into a graph orders its own work and is not chained, nor are the pipeline's own sets
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing((cudaStream_t)stream, &cap);
+    std::lock_guard<std::mutex> lock(p->tc_mu);
+    const bool chain = e == cudaSuccess && cap == cudaStreamCaptureStatusNone && tc_set == 0;
+    if (e == cudaSuccess && chain && p->tc_ev_recorded) e = cudaStreamWaitEvent((cudaStream_t)stream, p->tc_ev, 0);
+    if (e == cudaSuccess)
+      e = tc_launch(p, static_cast<const double*>(in), static_cast<double*>(out), transpose, var_begin, var_count,
+                    (cudaStream_t)stream, tc_set);
+    if (e == cudaSuccess && chain) {
+      e = cudaEventRecord(p->tc_ev, (cudaStream_t)stream);
+      p->tc_ev_recorded = e == cudaSuccess;
+    }
     if (cur != p->device) cudaSetDevice(cur);
     return e == cudaSuccess ? SPH_OK : SPH_ECUDA;
   }
@@ -432,6 +445,7 @@ sph_status sph_filter_plan_create(sph_filter_plan* out, int Nr, int Ntheta, int 
   }
   if (p->precision == SPH_PREC_SPLIT_TC) {
     st = tc_setup(p);
+    if (st == SPH_OK && cudaEventCreateWithFlags(&p->tc_ev, cudaEventDisableTiming) != cudaSuccess) st = SPH_ECUDA;
     if (st != SPH_OK) {
       free_plan(p);
       return st;
@@ -453,8 +467,8 @@ sph_status sph_filter_plan_create(sph_filter_plan* out, int Nr, int Ntheta, int 
     free_plan(p);
     return st;
   }
-  if (hybrid && (!p->use_v2 || p->cluster)) {
-    // the detector and the per-circle multipliers live in the single-CTA shell kernel
+  if (hybrid && !p->use_v2) {
+    // the detector and the per-circle multipliers live in the staged shell kernels
     free_plan(p);
     return SPH_EUNSUPPORTED;
   }
@@ -556,6 +570,10 @@ sph_status sph_filter_apply_host(sph_filter_plan plan, const double* host_in, do
       return SPH_ENOMEM;
     }
   }
+  if (plan->tc) {
+    const sph_status st = tc_reserve_pipeline(plan);
+    if (st != SPH_OK) return st;
+  }
   if (!plan->pipe[0]) {
     for (cudaStream_t& s : plan->pipe)
       if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return SPH_ECUDA;
@@ -583,8 +601,9 @@ sph_status sph_filter_apply_host(sph_filter_plan plan, const double* host_in, do
     if (cudaMemcpyAsync(plan->d_stage_in + off, host_in + off, sizeof(double) * cnt, cudaMemcpyHostToDevice, ps) !=
         cudaSuccess)
       return SPH_ECUDA;
+    // the tensor-core form's scratch set of this stream (chunks on different streams may overlap)
     const sph_status st = launch_plan_vars(plan, plan->d_stage_in, nullptr, plan->d_stage_out, kMapNone, kOutNone, 0,
-                                           0, v0, nv, ps);
+                                           0, v0, nv, ps, 1 + k % 3);
     if (st != SPH_OK) return st;
     if (cudaMemcpyAsync(host_out + off, plan->d_stage_out + off, sizeof(double) * cnt, cudaMemcpyDeviceToHost, ps) !=
         cudaSuccess)

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 #include <vector>
 
 #include "../../include/sph_filter.h"
@@ -86,8 +87,8 @@ struct ShellArgs2 {
 };
 
 // Instantiations of the staged shell kernel, one per (compensated precision?, FFT length, hybrid
-// variant); defined by shell_inst.cu compiled once per triple. The hybrid variant (HYB = 1) exists
-// for the lengths a single CTA holds.
+// variant); defined by shell_inst.cu compiled once per triple. The single-CTA kernel's hybrid
+// variant (HYB = 1) exists for the lengths a single CTA holds (not 256).
 template <int DFP, int LEN, int HYB>
 cudaError_t launch_shell_inst(const ShellArgs2& a, int threads, size_t smem, const LaunchIO& io, cudaStream_t s);
 template <int DFP, int LEN, int HYB>
@@ -114,20 +115,25 @@ SPH_DECLARE_SHELL_INST_2(1, 192)
 SPH_DECLARE_SHELL_INST(1, 256, 0)
 #undef SPH_DECLARE_SHELL_INST_2
 #undef SPH_DECLARE_SHELL_INST
-// Cluster-pair instantiations for shells too large for one CTA (lengths 256 and generic).
-template <int DFP, int LEN>
+// Cluster-pair instantiations for shells too large for one CTA (lengths 256 and generic), with and
+// without the hybrid variant.
+template <int DFP, int LEN, int HYB>
 cudaError_t launch_shell_cl_inst(const ShellArgs2& a, int threads, size_t smem, const LaunchIO& io, cudaStream_t s);
-template <int DFP, int LEN>
+template <int DFP, int LEN, int HYB>
 cudaError_t set_attr_cl_inst(int bytes);
-#define SPH_DECLARE_SHELL_CL_INST(D, L)                                                                    \
-  template <>                                                                                              \
-  cudaError_t launch_shell_cl_inst<D, L>(const ShellArgs2&, int, size_t, const LaunchIO&, cudaStream_t); \
-  template <>                                                                                              \
-  cudaError_t set_attr_cl_inst<D, L>(int);
-SPH_DECLARE_SHELL_CL_INST(0, 0)
-SPH_DECLARE_SHELL_CL_INST(0, 256)
-SPH_DECLARE_SHELL_CL_INST(1, 0)
-SPH_DECLARE_SHELL_CL_INST(1, 256)
+#define SPH_DECLARE_SHELL_CL_INST(D, L, H)                                                                    \
+  template <>                                                                                                 \
+  cudaError_t launch_shell_cl_inst<D, L, H>(const ShellArgs2&, int, size_t, const LaunchIO&, cudaStream_t); \
+  template <>                                                                                                 \
+  cudaError_t set_attr_cl_inst<D, L, H>(int);
+SPH_DECLARE_SHELL_CL_INST(0, 0, 0)
+SPH_DECLARE_SHELL_CL_INST(0, 0, 1)
+SPH_DECLARE_SHELL_CL_INST(0, 256, 0)
+SPH_DECLARE_SHELL_CL_INST(0, 256, 1)
+SPH_DECLARE_SHELL_CL_INST(1, 0, 0)
+SPH_DECLARE_SHELL_CL_INST(1, 0, 1)
+SPH_DECLARE_SHELL_CL_INST(1, 256, 0)
+SPH_DECLARE_SHELL_CL_INST(1, 256, 1)
 #undef SPH_DECLARE_SHELL_CL_INST
 size_t shell_smem_cl_bytes(const ShellArgs2& a, int precision);
 cudaError_t launch_shell_cl(const ShellArgs2& a, int precision, int threads, size_t smem, const LaunchIO& io,
@@ -176,8 +182,14 @@ struct sph_filter_plan_s {
   double2* d_tw_ph = nullptr;
   unsigned* d_status = nullptr;
 
-  // split-precision tensor-core form (SPH_PREC_SPLIT_TC)
+  // split-precision tensor-core form (SPH_PREC_SPLIT_TC). Its kernels keep per-CTA scratch in the
+  // plan's global memory, so launches of one plan on different streams with the main scratch set are
+  // chained: each waits for tc_ev, recorded after the previous one (under tc_mu). The host-buffer
+  // pipeline's streams have scratch sets of their own.
   sph::TcPlan* tc = nullptr;
+  std::mutex tc_mu;
+  cudaEvent_t tc_ev = nullptr;
+  bool tc_ev_recorded = false;
 
   // staging buffers and pipeline streams of sph_filter_apply_host (created on first use)
   double* d_stage_in = nullptr;
@@ -192,19 +204,22 @@ long double filter_value(int kind, long double al, long double lmax);
 
 // Split-precision tensor-core form (tc.cu): tables at plan creation, release, and one application
 // (theta then phi pass, or the reverse for the transpose) of the fields [var_begin, var_begin +
-// var_count) from in to out (in == out allowed).
+// var_count) from in to out (in == out allowed), with per-CTA scratch set `set` (0: the plan's
+// main set; 1..3: the host-buffer pipeline's streams, reserved by tc_reserve_pipeline).
 sph_status tc_setup(sph_filter_plan_s* p);
 void tc_free(sph_filter_plan_s* p);
+sph_status tc_reserve_pipeline(sph_filter_plan_s* p);
 cudaError_t tc_launch(sph_filter_plan_s* p, const double* in, double* out, int transpose, int var_begin,
-                      int var_count, cudaStream_t s);
+                      int var_count, cudaStream_t s, int set);
 
 // Enqueue one filter application of a plan (validates pointers; see sph_filter_apply).
 sph_status launch_plan(sph_filter_plan_s* p, const void* in, const void* aux, void* out, int map_in, int map_out,
                        int transpose, int is_f32, cudaStream_t stream);
-// The same for the fields [var_begin, var_begin + var_count) only.
+// The same for the fields [var_begin, var_begin + var_count) only. tc_set: the tensor-core form's
+// scratch set (0 for every caller but the host-buffer pipeline, which passes 1..3 by stream).
 sph_status launch_plan_vars(sph_filter_plan_s* p, const void* in, const void* aux, void* out, int map_in,
                             int map_out, int transpose, int is_f32, int var_begin, int var_count,
-                            cudaStream_t stream);
+                            cudaStream_t stream, int tc_set = 0);
 // Shared-memory bytes the plain shell kernel needs for this plan's shape (0 if it cannot fit).
 size_t plain_smem_bytes(const ShellArgs& a, int* chunk_th, int* chunk_ph);
 // Enqueue the plain FP64 shell kernel.

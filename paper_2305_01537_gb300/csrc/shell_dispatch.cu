@@ -44,9 +44,14 @@ size_t shell_smem_cl_bytes(const ShellArgs2& a, int precision) {
 cudaError_t launch_shell_cl(const ShellArgs2& a, int precision, int threads, size_t smem, const LaunchIO& io,
                             cudaStream_t s) {
   const bool fixed = fixed_length(a) == 256;
-  if (precision == SPH_PREC_F32X2)
-    return fixed ? launch_shell_cl_inst<1, 256>(a, threads, smem, io, s) : launch_shell_cl_inst<1, 0>(a, threads, smem, io, s);
-  return fixed ? launch_shell_cl_inst<0, 256>(a, threads, smem, io, s) : launch_shell_cl_inst<0, 0>(a, threads, smem, io, s);
+  if (precision == SPH_PREC_F32X2) {
+    if (io.hybrid)
+      return fixed ? launch_shell_cl_inst<1, 256, 1>(a, threads, smem, io, s) : launch_shell_cl_inst<1, 0, 1>(a, threads, smem, io, s);
+    return fixed ? launch_shell_cl_inst<1, 256, 0>(a, threads, smem, io, s) : launch_shell_cl_inst<1, 0, 0>(a, threads, smem, io, s);
+  }
+  if (io.hybrid)
+    return fixed ? launch_shell_cl_inst<0, 256, 1>(a, threads, smem, io, s) : launch_shell_cl_inst<0, 0, 1>(a, threads, smem, io, s);
+  return fixed ? launch_shell_cl_inst<0, 256, 0>(a, threads, smem, io, s) : launch_shell_cl_inst<0, 0, 0>(a, threads, smem, io, s);
 }
 
 template <int DFP>
@@ -63,7 +68,8 @@ static cudaError_t set_attr_p(int bytes) {
   both(set_attr_inst<DFP, 128, 0>, set_attr_inst<DFP, 128, 1>);
   both(set_attr_inst<DFP, 192, 0>, set_attr_inst<DFP, 192, 1>);
   both(set_attr_inst<DFP, 256, 0>, nullptr);
-  both(set_attr_cl_inst<DFP, 0>, set_attr_cl_inst<DFP, 256>);
+  both(set_attr_cl_inst<DFP, 0, 0>, set_attr_cl_inst<DFP, 0, 1>);
+  both(set_attr_cl_inst<DFP, 256, 0>, set_attr_cl_inst<DFP, 256, 1>);
   return e;
 }
 

@@ -2,7 +2,7 @@
 // (precision, FFT length, hybrid variant) triple with -DSPH_SHELL_DF=0|1
 // -DSPH_SHELL_LEN=0|32|64|96|128|192|256 -DSPH_SHELL_HYB=0|1, so the instantiations compile in
 // parallel; shell_dispatch.cu selects one at launch time. The cluster-pair kernel is instantiated
-// with the non-hybrid variant.
+// for the lengths 256 and generic, in both variants.
 #include "shell_kernel.cuh"
 
 #ifndef SPH_SHELL_DF
@@ -23,6 +23,7 @@ using InstPolicy = shellk::DF;
 using InstPolicy = shellk::F64;
 #endif
 
+#if !(SPH_SHELL_HYB && SPH_SHELL_LEN == 256)  // 128 x 256 shells run on CTA pairs
 template <>
 cudaError_t launch_shell_inst<SPH_SHELL_DF, SPH_SHELL_LEN, SPH_SHELL_HYB>(const ShellArgs2& a, int threads, size_t smem,
                                                                         const LaunchIO& io, cudaStream_t s) {
@@ -33,17 +34,19 @@ template <>
 cudaError_t set_attr_inst<SPH_SHELL_DF, SPH_SHELL_LEN, SPH_SHELL_HYB>(int bytes) {
   return shellk::set_attr_impl<InstPolicy, SPH_SHELL_LEN, SPH_SHELL_HYB != 0>(bytes);
 }
+#endif
 
-#if SPH_SHELL_HYB == 0 && (SPH_SHELL_LEN == 0 || SPH_SHELL_LEN == 256)
+#if SPH_SHELL_LEN == 0 || SPH_SHELL_LEN == 256
 template <>
-cudaError_t launch_shell_cl_inst<SPH_SHELL_DF, SPH_SHELL_LEN>(const ShellArgs2& a, int threads, size_t smem,
-                                                            const LaunchIO& io, cudaStream_t s) {
-  return shellk::launch_cl_impl<InstPolicy, SPH_SHELL_LEN>(a, threads, smem, io, s);
+cudaError_t launch_shell_cl_inst<SPH_SHELL_DF, SPH_SHELL_LEN, SPH_SHELL_HYB>(const ShellArgs2& a, int threads,
+                                                                           size_t smem, const LaunchIO& io,
+                                                                           cudaStream_t s) {
+  return shellk::launch_cl_impl<InstPolicy, SPH_SHELL_LEN, SPH_SHELL_HYB != 0>(a, threads, smem, io, s);
 }
 
 template <>
-cudaError_t set_attr_cl_inst<SPH_SHELL_DF, SPH_SHELL_LEN>(int bytes) {
-  return shellk::set_attr_cl_impl<InstPolicy, SPH_SHELL_LEN>(bytes);
+cudaError_t set_attr_cl_inst<SPH_SHELL_DF, SPH_SHELL_LEN, SPH_SHELL_HYB>(int bytes) {
+  return shellk::set_attr_cl_impl<InstPolicy, SPH_SHELL_LEN, SPH_SHELL_HYB != 0>(bytes);
 }
 #endif
 

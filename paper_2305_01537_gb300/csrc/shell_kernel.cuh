@@ -452,7 +452,8 @@ struct PhiSplitAcc {
   int cap;
   const int2* pairs;
   const void* gtab;
-  size_t gbase;
+  size_t gbase, gbase_alt;  // the shell's rows of the first and the second table
+  bool hyb;                 // hybrid field: the alt bits select the table
   int ld, N, N8, QB, QB8, Nth, r, hN, nh, b0;
 
   __device__ __forceinline__ int brow(int j) const {
@@ -465,9 +466,10 @@ struct PhiSplitAcc {
     const bool mine = blk == r || blk == 2 + r;
     return mine ? A + (uint32_t)(j * ld + lc) * 8u : Bm + (uint32_t)(brow(j) * ld + lc) * 8u;
   }
-  __device__ __forceinline__ Seq seq(int b) const {  // (hybrid fields do not run on CTA pairs)
+  __device__ __forceinline__ Seq seq(int b) const {
     const int2 p = pairs[b];
-    return Seq{p.x & 0x3fffffff, p.y, ((p.x >> 30) & 1) != 0, false, false};
+    return Seq{p.x & 0x0fffffff, p.y, ((p.x >> 30) & 1) != 0, hyb && ((p.x >> 29) & 1) != 0,
+               hyb && ((p.x >> 28) & 1) != 0};
   }
   __device__ __forceinline__ int seq_len() const { return N; }
   // slots: segments of Nphi/4 complex in A row j1, B row j1, A row j2, B row j2
@@ -486,13 +488,13 @@ struct PhiSplitAcc {
     P::st8(el(s.j1, k), v.re);
     P::st8(el(s.j2, k), v.im);
   }
-  __device__ __forceinline__ T ring_mult(int j, int m) const {
-    return P::from_tab(gtab, gbase + (size_t)j * nh + (m <= hN ? m : N - m));
+  __device__ __forceinline__ T ring_mult(int j, int m, bool alt) const {
+    return P::from_tab(gtab, (alt ? gbase_alt : gbase) + (size_t)j * nh + (m <= hN ? m : N - m));
   }
-  __device__ __forceinline__ T mult(const Seq& s, int m) const { return ring_mult(s.j1, m); }
+  __device__ __forceinline__ T mult(const Seq& s, int m) const { return ring_mult(s.j1, m, s.alt1); }
   __device__ __forceinline__ void mult2(const Seq& s, int m, T& f1, T& f2) const {
-    f1 = ring_mult(s.j1, m);
-    f2 = ring_mult(s.j2, m);
+    f1 = ring_mult(s.j1, m, s.alt1);
+    f2 = ring_mult(s.j2, m, s.alt2);
   }
   __device__ __forceinline__ uint32_t lin_at(int b, int n) const {
     const int bl = b - b0;
@@ -719,10 +721,11 @@ __device__ __noinline__ void phi_pass_fn(PhiAcc<P> PA, int npairs, bool has_gene
   }
 }
 
-template <class P, int LEN>
+template <class P, int LEN, bool HYB = false>
 __device__ __noinline__ void phi_split_pass_fn(PhiSplitAcc<P> PA, int npairs, bool has_general, Factors f,
                                                uint32_t tw, Consts<P> K, int batch) {
   PA.template fix<LEN>();
+  PA.hyb = HYB;
   for (int b0 = 0; b0 < npairs; b0 += batch) {
     PA.b0 = b0;
     run_pass<P, PhiSplitAcc<P>, LEN>(PA, PA.N, min(batch, npairs - b0), f, tw, K, has_general);
@@ -885,27 +888,41 @@ __device__ __forceinline__ int jameson_screen(float af, float bf, float cf, floa
   return -1;
 }
 
-// Jameson's shock detector of the hybrid filter (Sec. II.C) on the FP64 shell at shared address S
-// (row stride lds): ring[j] = 1 if some cell of phi ring j has sigma >= 0.95, circ[k] = 1 likewise
-// for theta circle k < Nphi/2 (meridians k and k + Nphi/2 joined over the poles, the values across
-// a pole with the parity sign). misc[5] = 1 if some circle fired; misc[6] receives emax. Called by
-// every thread of the CTA; the caller synchronises afterwards.
-// When Nphi is a multiple of 32, thread t walks meridian t mod Nphi down one band of rows: each
-// value is read and converted once, the theta neighbours are the previous and the next row of the
-// walk, and the phi neighbours come from the adjacent lanes (a warp holds 32 consecutive meridians
-// of one band; its edge lanes read theirs); it only screens. Without the walk (other Nphi, shells
-// with subnormal or non-finite values or emax < 128), or when the screen left a cell undecided,
-// every cell reads its four neighbours and undecided cells take the FP64 expression.
+// Where the detector finds a shell's FP64 values. DetShell: the whole shell in this CTA (row stride
+// lds, W = Nphi columns, periodic rings). The cluster kernel's DetHalf (defined with it) holds half
+// of the meridians and reads its rings' other half from the peer CTA.
 template <int LEN>
-__device__ __noinline__ void detect_shell(uint32_t S, int lds, int Nth, int Nph, bool odd, double eps, float eps_m,
-                                          int eps_p, unsigned char* circ, unsigned char* ring, int* misc) {
-  if constexpr (LEN > 0) {
-    Nth = LEN / 2;
-    Nph = LEN;
-    lds = LEN + 2;
+struct DetShell {
+  static constexpr bool kPair = false;
+  uint32_t S;
+  int nth, w, ld;
+  __device__ __forceinline__ int Nth() const { return LEN ? LEN / 2 : nth; }
+  __device__ __forceinline__ int W() const { return LEN ? LEN : w; }
+  __device__ __forceinline__ int lds() const { return LEN ? LEN + 2 : ld; }
+  __device__ __forceinline__ double at(int j, int c) const { return F64::ld8(S + 8u * (uint32_t)(j * lds() + c)); }
+  // the phi neighbour of column c on row j (dir = -1 left, +1 right)
+  __device__ __forceinline__ double nbr(int j, int c, int dir) const {
+    c += dir;
+    return at(j, c < 0 ? W() - 1 : (c == W() ? 0 : c));
   }
-  const int npts = Nth * Nph, h = Nph / 2;
-  auto at = [&](int j, int k) { return F64::ld8(S + 8u * (uint32_t)(j * lds + k)); };
+};
+
+// Jameson's shock detector of the hybrid filter (Sec. II.C) on the FP64 values the geometry G holds
+// (W columns, W/2 circles: column c and c + W/2 are the two meridians of circle c < W/2): ring[j] = 1
+// if some cell of phi ring j has sigma >= 0.95, circ[c] = 1 likewise for theta circle c (the values
+// across a pole with the parity sign). misc[5] = 1 if some circle fired; misc[6], misc[7] are
+// scratch. For a CTA pair both CTAs screen on one scale and leave with the ring flags and misc[5]
+// combined over the pair. Called by every thread of the CTA; the caller synchronises afterwards.
+// When W is a multiple of 32 and at most the block size, thread t walks column t mod W down one band
+// of rows: each value is read and converted once, the theta neighbours are the previous and the next
+// row of the walk, and the phi neighbours come from the adjacent lanes (a warp holds 32 consecutive
+// columns of one band; its edge lanes read theirs); it only screens. Without the walk (other W,
+// values that are subnormal or not finite, emax < 128), or when the screen left a cell undecided,
+// every cell reads its four neighbours and undecided cells take the FP64 expression.
+template <class G>
+__device__ __noinline__ void detect_shell(const G g, bool odd, double eps, float eps_m, int eps_p, unsigned char* circ,
+                                          unsigned char* ring, int* misc) {
+  const int Nth = g.Nth(), W = g.W(), h = W / 2;
   const unsigned long long flip = odd ? 0x8000000000000000ull : 0ull;
   auto across = [&](double x) { return __longlong_as_double(__double_as_longlong(x) ^ flip); };
   for (int n = threadIdx.x; n < h + Nth; n += blockDim.x) circ[n] = 0;  // circ, then ring
@@ -913,38 +930,50 @@ __device__ __noinline__ void detect_shell(uint32_t S, int lds, int Nth, int Nph,
     misc[5] = 0;
     misc[6] = 0;
   }
+  const int bands = (W & 31) == 0 ? (int)blockDim.x / W : 0;
+  const int t = threadIdx.x, k = bands ? t % W : 0, band = bands ? t / W : 0;
+  const int j0 = band < bands ? band * Nth / bands : 0, j1 = band < bands ? (band + 1) * Nth / bands : 0;
+  // the largest exponent field of the finite values, and whether any value is subnormal or not finite
   unsigned em = 0;
-  bool special = false;  // a subnormal, infinite or NaN value
-  for (int n = threadIdx.x; n < npts; n += blockDim.x) {
-    const int j = n / Nph;
-    const unsigned long long u = (unsigned long long)__double_as_longlong(at(j, n - j * Nph));
+  bool special = false;
+  auto take = [&](double x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
     const unsigned e = (unsigned)(u >> 52) & 0x7ffu;
     special |= e == 0x7ffu || (e == 0u && (u << 1) != 0ull);
     if (e != 0x7ffu) em = max(em, e);
+  };
+  if (bands) {
+    for (int j = j0; j < j1; ++j) take(g.at(j, k));
+  } else {
+    for (int n = threadIdx.x; n < Nth * W; n += blockDim.x) take(g.at(n / W, n % W));
   }
   em = __reduce_max_sync(0xffffffffu, em);
   __syncthreads();  // flags and misc cleared
   if ((threadIdx.x & 31) == 0) atomicMax(&misc[6], (int)em);
-  const bool any_special = __syncthreads_or(special) != 0;
-  const int emax = misc[6];
+  bool any_special = __syncthreads_or(special) != 0;
+  int emax = misc[6];
+  if constexpr (G::kPair) {
+    // one scale for the pair: the edge values come from the peer
+    if (threadIdx.x == 0) misc[7] = any_special ? 1 : 0;
+    g.pair_sync();  // also: the peer's values are in its shared memory
+    emax = max(emax, g.peer_int(&misc[6]));
+    any_special |= g.peer_int(&misc[7]) != 0;
+  }
   const float epsf = ldexpf(eps_m, eps_p + 1023 - emax);  // eps on the scale, in FP32 (0 or inf at the ends)
   bool fired = false, undecided = false;
-  const int bands = (Nph & 31) == 0 && !any_special && emax >= 128 ? (int)blockDim.x / Nph : 0;
-  if (bands > 0) {
+  if (bands && !any_special && emax >= 128) {
     const unsigned floor_a = (unsigned)(emax - 120) << 20, adj = (unsigned)(emax - 127) << 20;
-    const int t = threadIdx.x, k = t % Nph, g = t / Nph, lane = t & 31;
-    if (g < bands) {  // whole warps
-      const int j0 = g * Nth / bands, j1 = (g + 1) * Nth / bands;
-      const int ko = k < h ? k + h : k - h;  // the meridian across the pole
-      // the phi neighbour a lane cannot take from the adjacent lane: left for lane 0, right for 31
-      const int ke = lane == 0 ? (k == 0 ? Nph - 1 : k - 1) : (k == Nph - 1 ? 0 : k + 1);
+    if (band < bands) {  // whole warps
+      const int lane = t & 31, ko = k < h ? k + h : k - h;  // ko: the column across the pole
       const int c = k < h ? k : k - h;
-      float upf = screen_value_walk(j0 > 0 ? at(j0 - 1, k) : across(at(0, ko)), floor_a, adj);
-      float cuf = screen_value_walk(at(j0, k), floor_a, adj);
+      // the phi neighbour a lane cannot take from the adjacent lane: left for lane 0, right for 31
+      const int dir = lane == 0 ? -1 : 1;
+      float upf = screen_value_walk(j0 > 0 ? g.at(j0 - 1, k) : across(g.at(0, ko)), floor_a, adj);
+      float cuf = screen_value_walk(g.at(j0, k), floor_a, adj);
 #pragma unroll 2
       for (int j = j0; j < j1; ++j) {
-        const float dnf = screen_value_walk(j < Nth - 1 ? at(j + 1, k) : across(at(Nth - 1, ko)), floor_a, adj);
-        const float ef = screen_value_walk(at(j, ke), floor_a, adj);
+        const float dnf = screen_value_walk(j < Nth - 1 ? g.at(j + 1, k) : across(g.at(Nth - 1, ko)), floor_a, adj);
+        const float ef = screen_value_walk(g.nbr(j, k, dir), floor_a, adj);
         int d = jameson_screen(upf, cuf, dnf, epsf);
         undecided |= d < 0;
         if (d > 0) {
@@ -959,18 +988,19 @@ __device__ __noinline__ void detect_shell(uint32_t S, int lds, int Nth, int Nph,
         cuf = dnf;
       }
     }
+  } else {
+    undecided = true;
   }
   // a shell with an undecided cell anywhere (rare) takes the cell-by-cell pass below, which repeats
   // every decision (the same screen) and settles the undecided ones with the FP64 expression
-  const bool per_cell = bands > 0 ? __syncthreads_or(undecided) != 0 : true;
-  if (per_cell) {
-    for (int n = threadIdx.x; n < npts; n += blockDim.x) {
-      const int j = n / Nph, k = n - j * Nph;
-      const int ko = k < h ? k + h : k - h;
-      const double b = at(j, k);
-      const double pa = at(j, k == 0 ? Nph - 1 : k - 1), pc = at(j, k == Nph - 1 ? 0 : k + 1);
-      const double ta = j > 0 ? at(j - 1, k) : across(at(0, ko));
-      const double tc = j < Nth - 1 ? at(j + 1, k) : across(at(Nth - 1, ko));
+  if (__syncthreads_or(undecided)) {
+    for (int n = threadIdx.x; n < Nth * W; n += blockDim.x) {
+      const int j = n / W, kk = n - j * W;
+      const int ko = kk < h ? kk + h : kk - h;
+      const double b = g.at(j, kk);
+      const double pa = g.nbr(j, kk, -1), pc = g.nbr(j, kk, 1);
+      const double ta = j > 0 ? g.at(j - 1, kk) : across(g.at(0, ko));
+      const double tc = j < Nth - 1 ? g.at(j + 1, kk) : across(g.at(Nth - 1, ko));
       const float bf = screen_value(b, emax);
       int d = jameson_screen(screen_value(pa, emax), bf, screen_value(pc, emax), epsf);
       if (d < 0) d = jameson_exact(pa, b, pc, eps);
@@ -978,12 +1008,20 @@ __device__ __noinline__ void detect_shell(uint32_t S, int lds, int Nth, int Nph,
       d = jameson_screen(screen_value(ta, emax), bf, screen_value(tc, emax), epsf);
       if (d < 0) d = jameson_exact(ta, b, tc, eps);
       if (d) {
-        circ[k < h ? k : k - h] = 1;
+        circ[kk < h ? kk : kk - h] = 1;
         fired = true;
       }
     }
   }
   if (__any_sync(0xffffffffu, fired) && (threadIdx.x & 31) == 0) misc[5] = 1;
+  if constexpr (G::kPair) {
+    // the pair's ring flags and "a circle fired" are the union of both halves (OR is idempotent,
+    // so reading the peer's flags while it ORs ours in is harmless)
+    g.pair_sync();  // both halves' flags are final; the peer's values are not read after this
+    for (int j = threadIdx.x; j < Nth; j += blockDim.x)
+      if (g.peer_u8(ring + j)) ring[j] = 1;
+    if (threadIdx.x == 0 && g.peer_int(&misc[5])) misc[5] = 1;
+  }
 }
 
 // HYB: the kernel variant for launches with hybrid fields (the other variant has none of their code).
@@ -1038,7 +1076,12 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
     // a hybrid field's choices come from the whole FP64 shell: wait for it, run the detector
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
-    detect_shell<LEN>(saddr(buf), ld, Nth, Nph, vi.parity != 0, A.eps, A.eps_m, A.eps_p, L.circ, L.ring, L.misc);
+    DetShell<LEN> geo;
+    geo.S = saddr(buf);
+    geo.nth = Nth;
+    geo.w = Nph;
+    geo.ld = ld;
+    detect_shell(geo, vi.parity != 0, A.eps, A.eps_m, A.eps_p, L.circ, L.ring, L.misc);
     __syncthreads();
   }
   const bool theta_on = gauss || lmax < (double)Nth || (hyb && L.misc[5] != 0);
@@ -1307,6 +1350,47 @@ __device__ __forceinline__ uint4 ld_peer16(uint32_t a) {
   asm volatile("ld.shared::cluster.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
   return v;
 }
+__device__ __forceinline__ double ld_peer8(uint32_t a) {
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a));
+  return v;
+}
+
+// The detector's view of one CTA of a pair (hybrid fields): its buffer A holds every row of the
+// global meridian blocks r and r + 2 (Nphi/4 columns each) at local columns [0, Nphi/4) and
+// [Nphi/4, Nphi/2), so local column c and c + Nphi/4 are the two meridians of a circle. A ring's
+// cells next to a block edge have their phi neighbour in the peer's buffer (same layout), read
+// through distributed shared memory.
+template <int LEN>
+struct DetHalf {
+  static constexpr bool kPair = true;
+  uint32_t S;
+  int nth, nph, ld, r;
+  __device__ __forceinline__ int Nth() const { return LEN ? LEN / 2 : nth; }
+  __device__ __forceinline__ int W() const { return LEN ? LEN / 2 : nph / 2; }
+  __device__ __forceinline__ int lds() const { return LEN ? LEN / 2 + 2 : ld; }
+  __device__ __forceinline__ double at(int j, int c) const { return F64::ld8(S + 8u * (uint32_t)(j * lds() + c)); }
+  __device__ __forceinline__ double nbr(int j, int c, int dir) const {
+    const int QB = W() / 2, Nph = 2 * W();
+    int g = (c < QB ? r * QB + c : (r + 2) * QB + (c - QB)) + dir;  // global column of the neighbour
+    g = g < 0 ? Nph - 1 : (g == Nph ? 0 : g);
+    const int blk = g / QB;
+    const uint32_t a = S + 8u * (uint32_t)(j * lds() + (g - blk * QB) + (blk >= 2 ? QB : 0));
+    return (blk & 1) == r ? F64::ld8(a) : ld_peer8(peer_addr(a, 1 - r));
+  }
+  __device__ __forceinline__ void pair_sync() const { cluster_sync(); }
+  __device__ __forceinline__ int peer_int(const int* p) const {
+    unsigned v;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(peer_addr(saddr(p), 1 - r)));
+    return (int)v;
+  }
+  __device__ __forceinline__ int peer_u8(const unsigned char* p) const {
+    unsigned v;
+    asm volatile("ld.shared::cluster.u8 %0, [%1];" : "=r"(v) : "r"(peer_addr(saddr(p), 1 - r)));
+    return (int)v;
+  }
+};
+
 __device__ __forceinline__ void st_local16(uint32_t a, uint4 v) {
   asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w) : "memory");
 }
@@ -1315,8 +1399,12 @@ template <class P>
 struct LayoutCl {
   uint32_t A, B, lin, ov, tw_th, tw_ph, g_th;
   int2* pairs;
-  int* misc;
+  int* misc;               // [0] pair count, [1] general flag, [2] exponent; hybrid fields: [4] mixed
+                           // circle pairs, [5] some circle fired (over the pair), [6], [7] scratch
   uint32_t rowact;         // shared address of the row flags: a pass transforms row j (1) or not (0)
+  unsigned char* circ;     // hybrid fields: detector flags of this CTA's theta circles [Nphi/4],
+  unsigned char* ring;     //   of the phi rings [Ntheta] (over the pair),
+  unsigned char* thsel;    //   and the table choice of this CTA's theta sequences [(Nphi/4 + 1)/2]
 };
 
 // Shared memory of one CTA of a pair: A (all rows, half the columns), B (half of the rows, the other
@@ -1339,10 +1427,13 @@ __device__ LayoutCl<P> carve_cl(const ShellArgs2& A, unsigned char* base) {
   L.ov = saddr(take(16 * (size_t)max(2 * A.Nth, A.Nph)));
   L.tw_th = saddr(take(16 * 2 * (size_t)A.Nth));
   L.tw_ph = saddr(take(16 * (size_t)A.Nph));
-  L.g_th = saddr(take(8 * (size_t)(A.Nth + 1)));
+  L.g_th = saddr(take(16 * (size_t)(A.Nth + 1)));  // two rows: a hybrid field's Gaussian one second
   L.pairs = reinterpret_cast<int2*>(take(sizeof(int2) * (size_t)(A.Nth / 2 + 1)));
-  L.misc = reinterpret_cast<int*>(take(sizeof(int) * 4));
+  L.misc = reinterpret_cast<int*>(take(sizeof(int) * 8));
   L.rowact = saddr(take((size_t)A.Nth));
+  L.circ = take((size_t)(A.Nph / 4 + A.Nth + (A.Nph / 4 + 1) / 2));
+  L.ring = L.circ + A.Nph / 4;
+  L.thsel = L.ring + A.Nth;
   return L;
 }
 
@@ -1360,10 +1451,11 @@ size_t shell_smem_cl(const ShellArgs2& a) {
   s += up(16 * (size_t)std::max(2 * a.Nth, a.Nph));
   s += up(16 * 2 * (size_t)a.Nth);
   s += up(16 * (size_t)a.Nph);
-  s += up(8 * (size_t)(a.Nth + 1));
+  s += up(16 * (size_t)(a.Nth + 1));
   s += up(sizeof(int2) * (size_t)(a.Nth / 2 + 1));
-  s += up(sizeof(int) * 4);
+  s += up(sizeof(int) * 8);
   s += up((size_t)a.Nth);
+  s += up((size_t)(a.Nph / 4 + a.Nth + (a.Nph / 4 + 1) / 2));
   return s;
 }
 
@@ -1382,8 +1474,9 @@ __device__ __forceinline__ bool cl_own_row(int j, int Nth, int r) {
   return (j >= q * r && j < q * (r + 1)) || (j >= Nth - (r + 1) * q && j < Nth - r * q);
 }
 
-// One shell per cluster pair; Ntheta % 4 == 0, Nphi % 8 == 0.
-template <class P, int LEN>
+// One shell per cluster pair; Ntheta % 4 == 0, Nphi % 8 == 0. HYB: the variant for launches with
+// hybrid fields (forward order only).
+template <class P, int LEN, bool HYB>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512) shell_kernel_cl(ShellArgs2 A, LaunchIO io) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr bool dfp = std::is_same<P, DF>::value;
@@ -1397,6 +1490,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512) shell_kernel_cl
   const int Nth = LEN ? LEN / 2 : A.Nth, Nph = LEN ? LEN : A.Nph, QB = Nph / 4;
   const int ldc = LEN ? LEN / 2 + 2 : (int)cl_ld(A);
   const bool fwd = io.transpose == 0;
+  const bool hyb = HYB && fwd && vi.kind == SPH_FILTER_HYBRID;  // the same on both CTAs of the pair
 
   for (int n = threadIdx.x; n < 2 * Nth; n += blockDim.x)
     P::st16(L.tw_th + 16u * n, static_cast<const typename P::C*>(A.tw_th)[n]);
@@ -1444,14 +1538,28 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512) shell_kernel_cl
     }
     __syncthreads();
   }
+  if (hyb) {
+    // Jameson's detector on the raw FP64 values; ring flags and "a circle fired" come out combined
+    // over the pair, so both CTAs take the same rows and the same theta decision
+    DetHalf<LEN> geo;
+    geo.S = L.A;
+    geo.nth = Nth;
+    geo.nph = Nph;
+    geo.ld = ldc;
+    geo.r = r;
+    detect_shell(geo, vi.parity != 0, A.eps, A.eps_m, A.eps_p, L.circ, L.ring, L.misc);
+    __syncthreads();
+  }
   // rows a pass transforms: every row when the theta pass runs, else the rows of active ring pairs
   // (the same rows on both ranks); only these are converted to pairs, the rest stay FP64
   {
-    const bool th_on = vi.kind == SPH_FILTER_GAUSS || A.lmax[vi.cls * A.Nr + i] < (double)Nth;
+    const bool th_on = vi.kind == SPH_FILTER_GAUSS || A.lmax[vi.cls * A.Nr + i] < (double)Nth || (hyb && L.misc[5] != 0);
     const uint8_t* ri = A.ring_info + ((size_t)vi.cls * A.Nr + i) * Nth;
-    for (int j = threadIdx.x; j < Nth; j += blockDim.x)
+    for (int j = threadIdx.x; j < Nth; j += blockDim.x) {
+      const bool fire = hyb && (L.ring[j] || L.ring[Nth - 1 - j]);
       asm volatile("st.shared.u8 [%0], %1;" ::"r"(L.rowact + (uint32_t)j),
-                   "r"((th_on || ((ri[j] | ri[Nth - 1 - j]) & 1)) ? 1u : 0u));
+                   "r"((th_on || fire || ((ri[j] | ri[Nth - 1 - j]) & 1)) ? 1u : 0u));
+    }
   }
   __syncthreads();
   unsigned emax = 0;
@@ -1488,29 +1596,52 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512) shell_kernel_cl
     }
   }
 
-  // per-shell tables
+  // per-shell tables (a hybrid field's Gaussian theta row after its exponential one)
   const double lmax = A.lmax[vi.cls * A.Nr + i];
-  const bool theta_on = vi.kind == SPH_FILTER_GAUSS || lmax < (double)Nth;
+  const bool theta_on = vi.kind == SPH_FILTER_GAUSS || lmax < (double)Nth || (hyb && L.misc[5] != 0);
   const uint8_t* ring_info = A.ring_info + ((size_t)vi.cls * A.Nr + i) * Nth;
+  const uint8_t* ring_alt = A.ring_info + ((size_t)vi.alt_cls * A.Nr + i) * Nth;
   const size_t gth_base = ((size_t)vi.cls * A.Nr + i) * (Nth + 1);
-  for (int n = threadIdx.x; n <= Nth; n += blockDim.x) P::st8(L.g_th + 8u * n, P::from_tab(A.g_th, gth_base + n));
+  const size_t gth_alt = ((size_t)vi.alt_cls * A.Nr + i) * (Nth + 1);
+  for (int n = threadIdx.x; n < (hyb ? 2 : 1) * (Nth + 1); n += blockDim.x)
+    P::st8(L.g_th + 8u * n, P::from_tab(A.g_th, n <= Nth ? gth_base + n : gth_alt + (n - (Nth + 1))));
   if (threadIdx.x == 0) {
     int np = 0, gen = 0;
     const int q = Nth / 4;
     for (int j = q * r; j < q * (r + 1); ++j) {
       const int jj = Nth - 1 - j;
       const uint8_t a = ring_info[j], b = ring_info[jj];
-      if (!((a | b) & 1)) continue;
-      const int g = (a >> 1) & 1;
+      // hybrid field: a ring whose detector fired takes the Gaussian table (never the identity)
+      const int fa = hyb ? L.ring[j] : 0, fb = hyb ? L.ring[jj] : 0;
+      if (!((a | b) & 1) && !fa && !fb) continue;
+      const int g = fa != fb ? 1 : ((fa ? ring_alt[j] : a) >> 1) & 1;
       gen |= g;
-      L.pairs[np++] = make_int2(j | (g << 30), jj);
+      L.pairs[np++] = make_int2(j | (g << 30) | (fa << 29) | (fb << 28), jj);
     }
     L.misc[0] = np;
     L.misc[1] = gen;
   }
+  if (hyb && threadIdx.x >= 32 && threadIdx.x < 64) {
+    // table of each of this CTA's theta sequences (circles 2b, 2b+1): 0 exponential, 1 Gaussian,
+    // 2 one of each (split multiply); a lone last circle counts twice
+    const int lane = threadIdx.x - 32, hc = Nph / 4, nseq = (hc + 1) / 2;
+    int gth = 0;
+    for (int b0 = 0; b0 < nseq; b0 += 32) {
+      const int b = b0 + lane;
+      int t = 0;
+      if (b < nseq) {
+        const int c1 = L.circ[2 * b], c2 = 2 * b + 1 < hc ? L.circ[2 * b + 1] : c1;
+        t = c1 == c2 ? c1 : 2;
+        L.thsel[b] = (unsigned char)t;
+      }
+      gth |= __any_sync(0xffffffffu, t == 2) ? 1 : 0;
+    }
+    if (lane == 0) L.misc[4] = gth;
+  }
   __syncthreads();
   const int npairs = L.misc[0];
   const bool has_general = L.misc[1] != 0;
+  const bool th_general = hyb && L.misc[4] != 0;
 
   ThetaAcc<P> TA;
   TA.S = L.A;
@@ -1528,9 +1659,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512) shell_kernel_cl
   TA.odd = vi.parity != 0;
   TA.hodd = (Nph / 4) & 1;
   TA.b0 = 0;
-  TA.sel = nullptr;
-  TA.circ = nullptr;
-  TA.hyb = false;  // plans with hybrid fields do not run on CTA pairs
+  TA.sel = L.thsel;
+  TA.circ = L.circ;
+  TA.hyb = hyb;
 
   PhiSplitAcc<P> PA;
   PA.A = L.A;
@@ -1544,6 +1675,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512) shell_kernel_cl
   PA.pairs = L.pairs;
   PA.gtab = A.g_ph;
   PA.gbase = ((size_t)vi.cls * A.Nr + i) * (size_t)Nth * (Nph / 2 + 1);
+  PA.gbase_alt = ((size_t)vi.alt_cls * A.Nr + i) * (size_t)Nth * (Nph / 2 + 1);
+  PA.hyb = hyb;
   PA.ld = ldc;
   PA.N = Nph;
   PA.N8 = Nph & ~7;
@@ -1578,9 +1711,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512) shell_kernel_cl
   };
 
   if (fwd) {
-    if (theta_on) theta_pass_fn<P, LEN, true>(TA, A.f_th, L.tw_th, K, A.batch_th, false);
+    if (theta_on) {
+      if (hyb) theta_pass_fn<P, LEN, true, true>(TA, A.f_th, L.tw_th, K, A.batch_th, th_general);
+      else theta_pass_fn<P, LEN, true>(TA, A.f_th, L.tw_th, K, A.batch_th, false);
+    }
     exchange();
-    if (npairs) phi_split_pass_fn<P, LEN>(PA, npairs, has_general, A.f_ph, L.tw_ph, K, A.batch_ph);
+    if (npairs) {
+      if (hyb) phi_split_pass_fn<P, LEN, true>(PA, npairs, has_general, A.f_ph, L.tw_ph, K, A.batch_ph);
+      else phi_split_pass_fn<P, LEN>(PA, npairs, has_general, A.f_ph, L.tw_ph, K, A.batch_ph);
+    }
   } else {
     if (npairs) phi_split_pass_fn<P, LEN>(PA, npairs, has_general, A.f_ph, L.tw_ph, K, A.batch_ph);
     exchange();
@@ -1610,16 +1749,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512) shell_kernel_cl
   }
 }
 
-template <class P, int LEN>
+template <class P, int LEN, bool HYB>
 cudaError_t launch_cl_impl(const ShellArgs2& a, int threads, size_t smem, const LaunchIO& io, cudaStream_t s) {
   const dim3 grid((unsigned)(2 * io.var_count * a.Nr));
-  shell_kernel_cl<P, LEN><<<grid, threads, smem, s>>>(a, io);
+  shell_kernel_cl<P, LEN, HYB><<<grid, threads, smem, s>>>(a, io);
   return cudaGetLastError();
 }
 
-template <class P, int LEN>
+template <class P, int LEN, bool HYB>
 cudaError_t set_attr_cl_impl(int bytes) {
-  return cudaFuncSetAttribute(shell_kernel_cl<P, LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return cudaFuncSetAttribute(shell_kernel_cl<P, LEN, HYB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 template <class P>

@@ -639,10 +639,15 @@ struct TcPass {
   std::vector<int> copy_runs;      // theta pass: [field, first shell, shells] runs of identity shells
 };
 
+// Scratch set 0 serves sph_filter_apply and the calls built on it; sets 1..3 (allocated on first
+// use) serve the three streams of the host-buffer pipeline, whose chunk launches may overlap.
 struct TcPlan {
   TcPass pass[2];
-  float2* d_scratch = nullptr;
+  float2* d_scratch = nullptr;       // set 0
   uint4* d_akeep = nullptr;
+  float2* d_scratch_pipe = nullptr;  // sets 1..3
+  uint4* d_akeep_pipe = nullptr;
+  size_t scratch_set = 0, akeep_set = 0;  // elements per set
   int akeep_chunks = 0;
   int nsm = 0;
 };
@@ -758,13 +763,14 @@ sph_status tc_setup(sph_filter_plan_s* p) {
   if (cudaDeviceGetAttribute(&T->nsm, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) return SPH_ECUDA;
   const int Hmax = std::max(Lth, Lph) / 2;
   const size_t per_cta = (size_t)tcx::kM * (3 * Hmax + 1);
-  if (cudaMalloc((void**)&T->d_scratch, per_cta * T->nsm * sizeof(float2)) != cudaSuccess) return SPH_ENOMEM;
+  T->scratch_set = per_cta * T->nsm;
+  if (cudaMalloc((void**)&T->d_scratch, T->scratch_set * sizeof(float2)) != cudaSuccess) return SPH_ENOMEM;
   // kept A stages for GEMMs whose outputs take two passes of the K loop
   for (int q = 0; q < 2; ++q)
     for (int o = 0; o < 4; ++o)
       if (T->pass[q].op[o].nh > 1) T->akeep_chunks = std::max(T->akeep_chunks, T->pass[q].op[o].KP / tcx::kKC);
-  if (T->akeep_chunks > 0 &&
-      cudaMalloc((void**)&T->d_akeep, (size_t)T->akeep_chunks * tcx::kStageA * T->nsm) != cudaSuccess)
+  T->akeep_set = (size_t)T->akeep_chunks * (tcx::kStageA / 16) * T->nsm;
+  if (T->akeep_chunks > 0 && cudaMalloc((void**)&T->d_akeep, T->akeep_set * sizeof(uint4)) != cudaSuccess)
     return SPH_ENOMEM;
   if (cudaFuncSetAttribute(tcx::tc_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcx::kSmemBytes) !=
       cudaSuccess)
@@ -782,13 +788,27 @@ void tc_free(sph_filter_plan_s* p) {
   }
   cudaFree(T->d_scratch);
   cudaFree(T->d_akeep);
+  cudaFree(T->d_scratch_pipe);
+  cudaFree(T->d_akeep_pipe);
   delete T;
   p->tc = nullptr;
 }
 
+sph_status tc_reserve_pipeline(sph_filter_plan_s* p) {
+  TcPlan* T = p->tc;
+  if (T->d_scratch_pipe) return SPH_OK;
+  if (cudaMalloc((void**)&T->d_scratch_pipe, 3 * T->scratch_set * sizeof(float2)) != cudaSuccess) return SPH_ENOMEM;
+  if (T->akeep_set && cudaMalloc((void**)&T->d_akeep_pipe, 3 * T->akeep_set * sizeof(uint4)) != cudaSuccess) {
+    cudaFree(T->d_scratch_pipe);
+    T->d_scratch_pipe = nullptr;
+    return SPH_ENOMEM;
+  }
+  return SPH_OK;
+}
+
 namespace {
 cudaError_t launch_pass(sph_filter_plan_s* p, int q, const double* src, double* dst, int var_begin, int var_count,
-                        cudaStream_t s) {
+                        cudaStream_t s, int set) {
   TcPlan* T = p->tc;
   TcPass& P = T->pass[q];
   const long long e0 = P.var_off[(size_t)var_begin], e1 = P.var_off[(size_t)(var_begin + var_count)];
@@ -808,8 +828,8 @@ cudaError_t launch_pass(sph_filter_plan_s* p, int q, const double* src, double* 
   for (int o = 0; o < 4; ++o) a.op[o] = P.op[o];
   a.Ef = P.Ef;
   a.Ei = P.Ei;
-  a.scratch = T->d_scratch;
-  a.akeep = T->d_akeep;
+  a.scratch = set == 0 ? T->d_scratch : T->d_scratch_pipe + (size_t)(set - 1) * T->scratch_set;
+  a.akeep = set == 0 ? T->d_akeep : (T->d_akeep_pipe ? T->d_akeep_pipe + (size_t)(set - 1) * T->akeep_set : nullptr);
   a.akeep_chunks = T->akeep_chunks;
   a.status = p->d_status;
   const long long ntiles = (a.nvec + tcx::kM - 1) / tcx::kM;
@@ -820,7 +840,8 @@ cudaError_t launch_pass(sph_filter_plan_s* p, int q, const double* src, double* 
 }  // namespace
 
 cudaError_t tc_launch(sph_filter_plan_s* p, const double* in, double* out, int transpose, int var_begin,
-                      int var_count, cudaStream_t s) {
+                      int var_count, cudaStream_t s, int set) {
+  if (set < 0 || set > 3 || (set > 0 && !p->tc->d_scratch_pipe)) return cudaErrorInvalidValue;
   const size_t shell = (size_t)p->Nth * p->Nph, field = shell * p->Nr;
   if (!transpose) {
     // theta pass in -> out (identity shells copied), then the phi pass in place (Sec. II.C order)
@@ -835,9 +856,9 @@ cudaError_t tc_launch(sph_filter_plan_s* p, const double* in, double* out, int t
         if (e != cudaSuccess) return e;
       }
     }
-    const cudaError_t e = launch_pass(p, 0, in, out, var_begin, var_count, s);
+    const cudaError_t e = launch_pass(p, 0, in, out, var_begin, var_count, s, set);
     if (e != cudaSuccess) return e;
-    return launch_pass(p, 1, out, out, var_begin, var_count, s);
+    return launch_pass(p, 1, out, out, var_begin, var_count, s, set);
   }
   // transpose: phi pass, then theta pass, both in place on out
   if (in != out) {
@@ -845,9 +866,9 @@ cudaError_t tc_launch(sph_filter_plan_s* p, const double* in, double* out, int t
                                           sizeof(double) * field * var_count, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return e;
   }
-  const cudaError_t e = launch_pass(p, 1, out, out, var_begin, var_count, s);
+  const cudaError_t e = launch_pass(p, 1, out, out, var_begin, var_count, s, set);
   if (e != cudaSuccess) return e;
-  return launch_pass(p, 0, out, out, var_begin, var_count, s);
+  return launch_pass(p, 0, out, out, var_begin, var_count, s, set);
 }
 
 }  // namespace sph

@@ -253,6 +253,12 @@ def hybrid_state_128x64x128() -> Workload:
                     "28 fields, 6 hybrid matter fields with a star surface (1 -> 1e-10), others band-limited")
 
 
+def hybrid_state_256x128x256() -> Workload:
+    """The hybrid 28-field mix on Nr = 256, Ntheta = 128, Nphi = 256 (CTA pairs), seed 11."""
+    return Workload("hybrid28_256x128x256", [grid_28_hybrid(256, 128, 256)], [11],
+                    "28 fields, 6 hybrid matter fields with a star surface (1 -> 1e-10), others band-limited")
+
+
 BATCH_SHAPES = [(16, 32, 64), (32, 64, 96), (48, 96, 128), (64, 128, 256), (96, 192, 384), (128, 256, 512)]
 
 

@@ -72,10 +72,11 @@ def fired(g, x):
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("Nr,Nth,Nph", [(3, 4, 8), (2, 3, 6), (4, 8, 16), (3, 6, 12), (2, 9, 54), (2, 12, 48),
                                         (2, 24, 36), (3, 16, 32), (3, 32, 64), (2, 48, 96), (2, 64, 128),
-                                        (2, 96, 192)])
+                                        (2, 96, 192), (2, 128, 256)])
 def test_star_state_all_lengths(torch_cuda, Nr, Nth, Nph, prec):
     """The 28-field mix with hybrid matter fields on the star state: tiny and ragged shapes (a lone
-    circle when Nphi/2 is odd, a lone middle ring when Ntheta is odd), and every compiled length."""
+    circle when Nphi/2 is odd, a lone middle ring when Ntheta is odd), every compiled length, and
+    128 x 256 shells (a CTA pair per shell)."""
     g, x = star_case(Nr, Nth, Nph)
     y = apply(torch_cuda, g, x, prec)
     err = field_errors(y, oracle_of(g, x))
@@ -103,7 +104,7 @@ def test_mixed_circle_pairs_and_mirror_rings(torch_cuda, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("Nth,Nph", [(12, 24), (16, 32), (32, 64), (64, 128)])
+@pytest.mark.parametrize("Nth,Nph", [(12, 24), (16, 32), (32, 64), (64, 128), (128, 256)])
 def test_decisions_inside_the_screening_band(torch_cuda, prec, Nth, Nph):
     """Cells whose sigma lies within 1e-7 of 0.95, on both sides, in rings and in circles: the
     kernel must take the exact FP64 decision there. A ring (1, x, 1, 1, x, 1, ...) has sigma =
@@ -127,6 +128,45 @@ def test_decisions_inside_the_screening_band(torch_cuda, prec, Nth, Nph):
     assert 0.0 < fr < 1.0 and 0.0 < fc < 1.0  # both decisions occur
     y = apply(torch_cuda, g, x, prec)
     assert field_errors(y, oracle_of(g, x)).max() <= TOL
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_cta_pair_block_edges(torch_cuda, prec):
+    """128 x 256 shells run on a CTA pair: rank r holds the meridian blocks r and r + 2 (64 columns
+    each), so a ring cell at a block edge has its phi neighbour on the other CTA. Each marked row
+    holds a single dip (1, 0.02, 1) (sigma 0.96) at one edge column, and nothing else in the ring
+    reaches 0.95: the ring fires only if the neighbour read across the pair is right."""
+    Nth, Nph = 128, 256
+    g = W.Grid(2, Nth, Nph, [0, 1], [HYB, HYB], [3.0, 3.0], r=np.array([20.5, 60.5]))
+    x = np.ones(g.shape) + 1e-3 * W.few_mode_state(g, seed=41, nmodes=3, mode_max=3, noise=0.0)
+    edges = {5: 63, 20: 64, 35: 127, 50: 128, 70: 191, 85: 192, 100: 255, 115: 0}
+    for j, c in edges.items():
+        x[:, :, j, c] = 0.02
+    for v in range(2):
+        for i in range(2):
+            _, ring = oracle.detect(x[v, i], g.parity[v], g.eps)
+            assert np.nonzero(ring)[0].tolist() == sorted(edges)
+    y = apply(torch_cuda, g, x, prec)
+    assert field_errors(y, oracle_of(g, x)).max() <= TOL
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_full_state_256x128x256_sampled(torch_cuda, prec):
+    """The 28-field hybrid mix on 256 x 128 x 256 (CTA pairs) at full size, sampled shells of every
+    hybrid field inside, across and outside the star, and of other classes."""
+    torch = torch_cuda
+    from paper_2305_01537_gb300 import Plan
+    g = W.grid_28_hybrid(256, 128, 256)
+    x = W.star_state(g, seed=11)
+    plan = Plan.from_grid(g, precision=prec)
+    y = plan.apply(torch.from_numpy(x).cuda())
+    torch.cuda.synchronize()
+    assert plan.sync_status() == 0
+    shells = [(v, i) for v in (14, 17, 24, 25) for i in (6, 30, 80, 140)] + [(0, 100), (20, 7)]
+    ref = oracle.filter_shells(x, shells, g.parity, g.kind, g.L, g.r, g.dr_min, g.floor, eps=g.eps)
+    fmax = {v: max(np.abs(ref[n]).max() for n, s in enumerate(shells) if s[0] == v) for v, _ in shells}
+    err = np.array([np.abs(y[v, i].cpu().numpy() - ref[n]).max() / fmax[v] for n, (v, i) in enumerate(shells)])
+    assert err.max() <= TOL, shells[int(err.argmax())]
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -201,8 +241,8 @@ def test_in_place_fp32_host_and_batch(torch_cuda, prec):
 
 
 def test_unsupported_calls(torch_cuda):
-    """The switch is nonlinear: no adjoint and no fused tanh steps; no tensor-core form; no shells
-    that need a CTA pair."""
+    """The switch is nonlinear: no adjoint and no fused tanh steps; no tensor-core form and no
+    chunked FP64 kernel (lengths with prime factors above 3)."""
     torch = torch_cuda
     from paper_2305_01537_gb300 import Plan, SphFilterError
     g = W.grid_28_hybrid(2, 8, 16)
@@ -213,8 +253,8 @@ def test_unsupported_calls(torch_cuda):
             call()
     with pytest.raises(SphFilterError):
         Plan.from_grid(g, precision=1)
-    with pytest.raises(SphFilterError):
-        Plan.from_grid(W.grid_28_hybrid(2, 128, 256), precision=2)
+    with pytest.raises(SphFilterError):  # Nphi = 2 x 37: the chunked FP64 kernel has no detector
+        Plan.from_grid(W.grid_28_hybrid(2, 8, 74), precision=0)
     # a plan without hybrid fields keeps its adjoint
     g2 = W.grid_28(2, 8, 16)
     Plan.from_grid(g2, precision=2).apply_adjoint(z)

@@ -89,19 +89,46 @@ def test_in_place_and_random_input(torch_cuda):
 
 
 def test_host_entry_and_scaled_fields(torch_cuda):
-    """Fields of very different magnitudes (1e-30 .. 1e30): the slicing scale is per vector."""
+    """Fields of very different magnitudes (1e-30 .. 1e30): the slicing scale is per vector. The
+    host-buffer call runs its field chunks on three streams; repeated, since launches of one plan
+    that overlapped would share the kernel's scratch."""
     torch = torch_cuda
     from paper_2305_01537_gb300 import Plan
     g = W.grid_28(3, 8, 16)
     x = W.band_limited_state(g, seed=5, mode_max=3, noise=0.05)
     x *= np.logspace(-30, 30, 28)[:, None, None, None]
+    ref = oracle_of(g, x)
     plan = Plan.from_grid(g, precision=TC)
     xh = torch.from_numpy(x).pin_memory()
-    out = torch.empty_like(xh).pin_memory()
-    plan.apply_host(xh, out)
+    for _ in range(3):
+        out = torch.empty_like(xh).pin_memory()
+        plan.apply_host(xh, out)
+        torch.cuda.synchronize()
+        assert plan.sync_status() == 0
+        assert field_errors(out.numpy(), ref).max() <= TOL
+
+
+def test_same_plan_on_two_streams(torch_cuda):
+    """The tensor-core kernel keeps per-CTA scratch in the plan: calls of one plan on two streams
+    are chained by the library, so concurrent calls give exactly the single-call results."""
+    torch = torch_cuda
+    from paper_2305_01537_gb300 import Plan
+    g = W.grid_28(8, 32, 64)
+    g.r = np.linspace(0.5, 20.5, 8)
+    x1 = torch.from_numpy(W.band_limited_state(g, seed=71, mode_max=6, noise=0.05)).cuda()
+    x2 = torch.from_numpy(W.band_limited_state(g, seed=72, mode_max=6, noise=0.05)).cuda()
+    plan = Plan.from_grid(g, precision=TC)
+    ref1, ref2 = plan.apply(x1), plan.apply(x2)
     torch.cuda.synchronize()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    for _ in range(10):
+        o1, o2 = torch.empty_like(x1), torch.empty_like(x2)
+        torch.cuda.synchronize()
+        plan.apply(x1, out=o1, stream=s1)
+        plan.apply(x2, out=o2, stream=s2)
+        torch.cuda.synchronize()
+        assert torch.equal(o1, ref1) and torch.equal(o2, ref2)
     assert plan.sync_status() == 0
-    assert field_errors(out.numpy(), oracle_of(g, x)).max() <= TOL
 
 
 def test_unsupported_calls(torch_cuda):
