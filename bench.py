@@ -200,7 +200,7 @@ def dist_setup():
 def single_grid_workload(name):
     return {"state28_128x64x128": W.full_state_128x64x128, "state28_256x128x256": W.full_state_256x128x256,
             "state28_32x128x256": W.state_32x128x256, "hybrid28_128x64x128": W.hybrid_state_128x64x128,
-            "hybrid28_256x128x256": W.hybrid_state_256x128x256}[name]()
+            "hybrid28_256x128x256": W.hybrid_state_256x128x256, "hybrid28_32x128x256": W.hybrid_state_32x128x256}[name]()
 
 
 def cpu_baseline(grid, x, seconds_target=10.0, stride0=16):
@@ -359,7 +359,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="state28_128x64x128",
                     choices=["state28_128x64x128", "state28_256x128x256", "batch6_uneven", "chain8_128x64x128",
-                             "state28_32x128x256", "hybrid28_128x64x128", "hybrid28_256x128x256"])
+                             "state28_32x128x256", "hybrid28_128x64x128", "hybrid28_256x128x256",
+                             "hybrid28_32x128x256"])
     ap.add_argument("--autotune", action="store_true", help="autotune the plan's launch shape before timing")
     ap.add_argument("--inplace", action="store_true",
                     help="filter the state in place (out = in): only the rows a pass transforms are moved")

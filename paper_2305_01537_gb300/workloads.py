@@ -259,6 +259,14 @@ def hybrid_state_256x128x256() -> Workload:
                     "28 fields, 6 hybrid matter fields with a star surface (1 -> 1e-10), others band-limited")
 
 
+def hybrid_state_32x128x256() -> Workload:
+    """The hybrid 28-field mix on the 128 x 256 shells at 32 radii (r = 0.5 .. 31.5, the star's
+    surface crossing r = 2.5 .. 17.5), seed 12: a case small enough for detailed profiles of the
+    CTA-pair kernel's hybrid variant."""
+    return Workload("hybrid28_32x128x256", [grid_28_hybrid(32, 128, 256)], [12],
+                    "28 fields, 6 hybrid matter fields with a star surface (1 -> 1e-10), others band-limited")
+
+
 BATCH_SHAPES = [(16, 32, 64), (32, 64, 96), (48, 96, 128), (64, 128, 256), (96, 192, 384), (128, 256, 512)]
 
 

@@ -209,14 +209,14 @@ def test_full_state_128x64x128_sampled(torch_cuda, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_in_place_fp32_host_and_batch(torch_cuda, prec):
+@pytest.mark.parametrize("Nr,Nth,Nph", [(4, 32, 64), (2, 128, 256)])
+def test_in_place_fp32_host_and_batch(torch_cuda, prec, Nr, Nth, Nph):
     """In place (every row is moved: the choices depend on the data), FP32 storage (the detector
-    sees the widened FP32 values), the host-buffer entry point and a CUDA-graph batch."""
+    sees the widened FP32 values), the host-buffer entry point and a CUDA-graph batch; one CTA and
+    a CTA pair per shell."""
     torch = torch_cuda
     from paper_2305_01537_gb300 import Batch, Plan
-    g = W.grid_28_hybrid(4, 32, 64)
-    g.r = np.linspace(3.5, 30.5, 4)
-    x = W.star_state(g, seed=31)
+    g, x = star_case(Nr, Nth, Nph, seed=31)
     ref = oracle_of(g, x)
     plan = Plan.from_grid(g, precision=prec)
     xd = torch.from_numpy(x).cuda()
