@@ -1178,9 +1178,12 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
       if (dfp && L.rowact[jrow]) emax = max(emax, (unsigned)df_exp_field(x));
     }
   } else if (dfp) {
-    for (int n = threadIdx.x; n < nact * Nph; n += blockDim.x) {
-      const int o = (int)L.arow[n / Nph] * ld + n % Nph;
-      emax = max(emax, (unsigned)df_exp_field(Sd[o]));
+    // value pairs (rows are even in length and 16-byte aligned): one 16-byte load per pair
+    const int h2 = Nph / 2;
+    for (int n = threadIdx.x; n < nact * h2; n += blockDim.x) {
+      const int r = n / h2;
+      const F64::C x = F64::ld16(saddr(buf) + 8u * (uint32_t)((int)L.arow[r] * ld + 2 * (n - r * h2)));
+      emax = max(emax, max((unsigned)df_exp_field(x.re), (unsigned)df_exp_field(x.im)));
     }
   }
   int E = 0;
@@ -1192,9 +1195,12 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
     __syncthreads();
     E = L.misc[2] - 1023;
     const uint32_t sb = saddr(buf);
-    for (int n = threadIdx.x; n < nact * Nph; n += blockDim.x) {
-      const int o = (int)L.arow[n / Nph] * ld + n % Nph;
-      P::st8(sb + 8u * o, to_real<P>(Sd[o], E));
+    const int h2 = Nph / 2;
+    for (int n = threadIdx.x; n < nact * h2; n += blockDim.x) {
+      const int r = n / h2;
+      const uint32_t a = sb + 8u * (uint32_t)((int)L.arow[r] * ld + 2 * (n - r * h2));
+      const F64::C x = F64::ld16(a);
+      P::st16(a, typename P::C{to_real<P>(x.re, E), to_real<P>(x.im, E)});
     }
   }
   __syncthreads();
