@@ -1267,10 +1267,8 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
     for (int c = threadIdx.x; c < na * (Nph / 2); c += blockDim.x) {
       const int jrow = (int)L.arow[c / (Nph / 2)], k = 2 * (c % (Nph / 2));
       const int o = jrow * ld + k;
-      double2 y;
-      y.x = from_real<P>(P::ld8(sb + 8u * o), E);
-      y.y = from_real<P>(P::ld8(sb + 8u * (o + 1)), E);
-      __stcs(dst + (jrow * Nph + k) / 2, y);
+      const typename P::C v = P::ld16(sb + 8u * o);
+      __stcs(dst + (jrow * Nph + k) / 2, make_double2(from_real<P>(v.re, E), from_real<P>(v.im, E)));
     }
     return;
   }
@@ -1283,10 +1281,11 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
       const int o = jrow * ld + n % Nph;
       double2 y;
       if (dfp && !L.rowact[jrow]) {
-        y = make_double2(Sd[o], Sd[o + 1]);
+        const F64::C v = F64::ld16(sb + 8u * o);
+        y = make_double2(v.re, v.im);
       } else {
-        y.x = from_real<P>(P::ld8(sb + 8u * o), E);
-        y.y = from_real<P>(P::ld8(sb + 8u * (o + 1)), E);
+        const typename P::C v = P::ld16(sb + 8u * o);
+        y = make_double2(from_real<P>(v.re, E), from_real<P>(v.im, E));
       }
       if (out16) {
         __stcs(dst + n2, y);
