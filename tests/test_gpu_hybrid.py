@@ -259,3 +259,29 @@ def test_unsupported_calls(torch_cuda):
     g2 = W.grid_28(2, 8, 16)
     Plan.from_grid(g2, precision=2).apply_adjoint(z)
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_autotune_and_allocation_free_call(torch_cuda, prec):
+    """The autotuner times other launch shapes (512 threads, where the detector's walk runs four
+    bands of rows; other FFT batch sizes): the filtered state does not depend on the shape, bit for
+    bit. The allocation-free host call gives the device call's result."""
+    torch = torch_cuda
+    from paper_2305_01537_gb300 import Plan, binding
+    g, x = star_case(3, 64, 128, seed=51)  # 688,128 points: within the allocation-free capacity
+    plan = Plan.from_grid(g, precision=prec)
+    xd = torch.from_numpy(x).cuda()
+    want = plan.apply(xd)
+    torch.cuda.synchronize()
+    assert field_errors(want.cpu().numpy(), oracle_of(g, x)).max() <= TOL
+    plan.autotune(xd, torch.empty_like(xd))
+    assert torch.equal(plan.apply(xd), want)
+    lib = binding.load()
+    xh = torch.from_numpy(x).pin_memory()
+    got = torch.empty_like(xh).pin_memory()
+    st = lib.sph_filter_apply_host_noalloc(plan._h, xh.data_ptr(), got.data_ptr(),
+                                          torch.cuda.current_stream().cuda_stream)
+    assert st == 0
+    torch.cuda.synchronize()
+    assert np.array_equal(got.numpy(), want.cpu().numpy())
+    assert plan.sync_status() == 0
