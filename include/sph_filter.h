@@ -171,8 +171,16 @@ sph_status sph_filter_plan_sync_status(sph_filter_plan plan);
 /* Number of filtered points per application: nvars * Nr * Ntheta * Nphi (0 for NULL). */
 long long sph_filter_plan_points(sph_filter_plan plan);
 
-/* Number of kernel launches one sph_filter_apply enqueues for this plan. */
+/* Number of kernel launches one out-of-place sph_filter_apply enqueues for this plan. A plan whose
+ * shells include some with an identity theta pass (exponential or sharp filter with l_max >=
+ * Ntheta) runs three: a copy of those shells, the shell kernel over the others and a kernel over
+ * their active phi ring pairs. In-place, FP32 and mapped calls may enqueue fewer; see
+ * sph_filter_plan_launch_count for the exact number. 0 for NULL. */
 int sph_filter_plan_launches(sph_filter_plan plan);
+
+/* Kernel launches this plan has enqueued so far, over all its calls and streams (a launch captured
+ * into a CUDA graph counts once, when it is captured; replays do not add to it). 0 for NULL. */
+long long sph_filter_plan_launch_count(sph_filter_plan plan);
 
 /* Static description of a status code. */
 const char* sph_filter_status_string(sph_status status);

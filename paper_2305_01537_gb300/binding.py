@@ -28,7 +28,7 @@ EXPORTED = (
     "sph_filter_apply_host", "sph_filter_plan_sync_status", "sph_filter_plan_points",
     "sph_filter_plan_launches", "sph_filter_status_string", "sph_filter_batch_create",
     "sph_filter_batch_destroy", "sph_filter_batch_apply", "sph_filter_batch_capture", "sph_filter_batch_launch",
-    "sph_filter_plan_autotune", "sph_filter_apply_host_noalloc",
+    "sph_filter_plan_autotune", "sph_filter_apply_host_noalloc", "sph_filter_plan_launch_count",
 )
 
 
@@ -71,6 +71,7 @@ def load() -> ctypes.CDLL:
         "sph_filter_plan_sync_status": ([P], I),
         "sph_filter_plan_points": ([P], LL),
         "sph_filter_plan_launches": ([P], I),
+        "sph_filter_plan_launch_count": ([P], LL),
         "sph_filter_status_string": ([I], ctypes.c_char_p),
         "sph_filter_batch_create": ([ctypes.POINTER(P), I, P], I),
         "sph_filter_batch_destroy": ([P], None),
@@ -144,6 +145,11 @@ class Plan:
     @property
     def launches(self) -> int:
         return int(load().sph_filter_plan_launches(self._h))
+
+    @property
+    def launch_count(self) -> int:
+        """Kernel launches this plan has enqueued so far (graph captures count once)."""
+        return int(load().sph_filter_plan_launch_count(self._h))
 
     def close(self) -> None:
         if getattr(self, "_h", None):

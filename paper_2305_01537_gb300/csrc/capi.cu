@@ -239,6 +239,49 @@ sph_status setup_v2(sph_filter_plan_s* p) {
   p->threads2 = threads;
   p->smem2 = smem;
   p->use_v2 = true;
+  if (!p->cluster) {
+    // sparse shells: exponential or sharp filter with l_max >= Ntheta (the theta pass keeps every
+    // mode); their active ring pairs become units
+    std::vector<int> dense, sparse, units;
+    p->dense_off.assign((size_t)p->nvars + 1, 0);
+    p->sparse_off.assign((size_t)p->nvars + 1, 0);
+    p->units_off.assign((size_t)p->nvars + 1, 0);
+    for (int v = 0; v < p->nvars; ++v) {
+      const int c = p->var_cls[(size_t)v], kind = p->kind[(size_t)v];
+      for (int i = 0; i < Nr; ++i) {
+        const bool sp = (kind == SPH_FILTER_EXP || kind == SPH_FILTER_SHARP) && !(p->h_lmax[(size_t)c * Nr + i] < (double)Nth);
+        if (!sp) {
+          dense.push_back(i * p->nvars + v);  // the shell kernel's grid index over all variables
+          continue;
+        }
+        sparse.push_back(v * Nr + i);
+        for (int j = 0; j < (Nth + 1) / 2; ++j) {
+          const size_t rb = o_ring + ((size_t)c * Nr + i) * Nth;
+          if ((buf[rb + j] | buf[rb + (Nth - 1 - j)]) & 1) units.push_back((v * Nr + i) * Nth + j);
+        }
+      }
+      p->dense_off[(size_t)v + 1] = (int)dense.size();
+      p->sparse_off[(size_t)v + 1] = (int)sparse.size();
+      p->units_off[(size_t)v + 1] = (int)units.size();
+    }
+    p->smem_units = units_smem_bytes(a, p->precision);
+    // (32-bit unit codes and multiplier offsets)
+    const bool fits = (long long)p->nvars * Nr * Nth < (1ll << 31) &&
+                      (long long)p->ncls * Nr * Nth * (p->Nph / 2 + 1) < (1ll << 32);
+    if (!sparse.empty() && fits && p->smem_units <= (size_t)max_smem_optin(p->device)) {
+      auto up_list = [](int** d, const std::vector<int>& h) {
+        if (cudaMalloc((void**)d, sizeof(int) * std::max<size_t>(h.size(), 1)) != cudaSuccess) return SPH_ENOMEM;
+        if (!h.empty() && cudaMemcpy(*d, h.data(), sizeof(int) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+          return SPH_ECUDA;
+        return SPH_OK;
+      };
+      sph_status st = up_list(&p->d_dense, dense);
+      if (st == SPH_OK) st = up_list(&p->d_sparse, sparse);
+      if (st == SPH_OK) st = up_list(&p->d_units, units);
+      if (st != SPH_OK) return st;
+      p->split = true;
+    }
+  }
   return SPH_OK;
 }
 
@@ -264,6 +307,9 @@ void free_plan(sph_filter_plan_s* p) {
   cudaFree(p->d_tw_ph);
   cudaFree(p->d_status);
   cudaFree(p->d_tabs);
+  cudaFree(p->d_dense);
+  cudaFree(p->d_sparse);
+  cudaFree(p->d_units);
   tc_free(p);
   if (p->tc_ev) cudaEventDestroy(p->tc_ev);
   cudaFree(p->d_stage_in);
@@ -323,6 +369,7 @@ sph_status launch_plan_vars(sph_filter_plan_s* p, const void* in, const void* au
     if (e == cudaSuccess)
       e = tc_launch(p, static_cast<const double*>(in), static_cast<double*>(out), transpose, var_begin, var_count,
                     (cudaStream_t)stream, tc_set);
+    if (e == cudaSuccess) p->launched += p->launches;
     if (e == cudaSuccess && chain) {
       e = cudaEventRecord(p->tc_ev, (cudaStream_t)stream);
       p->tc_ev_recorded = e == cudaSuccess;
@@ -338,10 +385,44 @@ sph_status launch_plan_vars(sph_filter_plan_s* p, const void* in, const void* au
     return SPH_EUNSUPPORTED;
   }
   LaunchIO io{in,        aux,       out, map_in, map_out, transpose, is_f32, ((uintptr_t)in % 16) == 0 ? 1 : 0,
-              var_begin, var_count, hybrid};
-  cudaError_t e = !p->use_v2 ? launch_plain(*p, io, (cudaStream_t)stream)
-                  : p->cluster ? launch_shell_cl(p->args2, p->precision, p->threads2, p->smem2, io, (cudaStream_t)stream)
-                               : launch_shell(p->args2, p->precision, p->threads2, p->smem2, io, (cudaStream_t)stream);
+              var_begin, var_count, hybrid, nullptr, 0};
+  cudaError_t e = cudaSuccess;
+  const bool split = p->split && !is_f32 && map_in == kMapNone && map_out == kOutNone && ((uintptr_t)in % 16) == 0 &&
+                     ((uintptr_t)out % 16) == 0;
+  if (split) {
+    // sparse shells: copied (out of place), then their active ring pairs filtered by the units
+    // kernel; dense shells: the shell kernel over their list (both orders: a sparse shell's only
+    // pass is the symmetric phi pass)
+    const int vb = var_begin, ve = var_begin + var_count;
+    const int d0 = p->dense_off[(size_t)vb], d1 = p->dense_off[(size_t)ve];
+    const int s0 = p->sparse_off[(size_t)vb], s1 = p->sparse_off[(size_t)ve];
+    const int u0 = p->units_off[(size_t)vb], u1 = p->units_off[(size_t)ve];
+    int n = 0;
+    if (in != out && s1 > s0) {
+      e = launch_copy_shells(static_cast<const double*>(in), static_cast<double*>(out), p->d_sparse + s0, s1 - s0,
+                             (size_t)p->Nth * p->Nph, (cudaStream_t)stream);
+      ++n;
+    }
+    if (e == cudaSuccess && d1 > d0) {
+      LaunchIO dense = io;
+      dense.var_begin = 0;
+      dense.var_count = p->nvars;
+      dense.list = p->d_dense + d0;
+      dense.nlist = d1 - d0;
+      e = launch_shell(p->args2, p->precision, p->threads2, p->smem2, dense, (cudaStream_t)stream);
+      ++n;
+    }
+    if (e == cudaSuccess && u1 > u0) {
+      e = launch_units(p->args2, p->precision, p->smem_units, io, p->d_units + u0, u1 - u0, (cudaStream_t)stream);
+      ++n;
+    }
+    if (e == cudaSuccess) p->launched += n;
+  } else {
+    e = !p->use_v2 ? launch_plain(*p, io, (cudaStream_t)stream)
+        : p->cluster ? launch_shell_cl(p->args2, p->precision, p->threads2, p->smem2, io, (cudaStream_t)stream)
+                     : launch_shell(p->args2, p->precision, p->threads2, p->smem2, io, (cudaStream_t)stream);
+    if (e == cudaSuccess) p->launched += 1;
+  }
   if (cur != p->device) cudaSetDevice(cur);
   return e == cudaSuccess ? SPH_OK : SPH_ECUDA;
 }
@@ -508,7 +589,7 @@ sph_status sph_filter_plan_create(sph_filter_plan* out, int Nr, int Ntheta, int 
     a.tw_ph = p->d_tw_ph;
     a.status = p->d_status;
   }
-  p->launches = 1;
+  p->launches = p->split ? 3 : 1;  // split: shell copy, dense shells, units (out of place)
   *out = p;
   return SPH_OK;
 }
@@ -631,6 +712,8 @@ long long sph_filter_plan_points(sph_filter_plan plan) {
 }
 
 int sph_filter_plan_launches(sph_filter_plan plan) { return plan ? plan->launches : 0; }
+
+long long sph_filter_plan_launch_count(sph_filter_plan plan) { return plan ? plan->launched.load() : 0; }
 
 const char* sph_filter_status_string(sph_status s) {
   switch (s) {

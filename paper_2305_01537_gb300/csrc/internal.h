@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <mutex>
 #include <vector>
@@ -63,6 +64,8 @@ struct LaunchIO {
   int var_begin;      // fields [var_begin, var_begin + var_count) are filtered (pointers are to
   int var_count;      // the whole state)
   int hybrid;         // some field of the launch takes the hybrid filter (every row is loaded)
+  const int* list;    // grid indices (i * var_count + v - var_begin) of the launch's shells, or null for all
+  int nlist;          // entries of list
 };
 
 // Arguments of the staged shell kernel (shell_kernel.cuh). Tables hold FP64 values, or
@@ -139,6 +142,37 @@ size_t shell_smem_cl_bytes(const ShellArgs2& a, int precision);
 cudaError_t launch_shell_cl(const ShellArgs2& a, int precision, int threads, size_t smem, const LaunchIO& io,
                             cudaStream_t s);
 
+// Units kernel (ring pairs of sparse shells, single-CTA plans): per (precision, length) in the
+// non-hybrid instantiation objects; the shell copy for out-of-place calls.
+template <int DFP, int LEN>
+cudaError_t launch_units_inst(const ShellArgs2& a, size_t smem, const LaunchIO& io, const int* units, int nunits,
+                              cudaStream_t s);
+template <int DFP, int LEN>
+cudaError_t set_attr_units_inst(int bytes);
+#define SPH_DECLARE_UNITS_INST(D, L)                                                                              \
+  template <>                                                                                                     \
+  cudaError_t launch_units_inst<D, L>(const ShellArgs2&, size_t, const LaunchIO&, const int*, int, cudaStream_t); \
+  template <>                                                                                                     \
+  cudaError_t set_attr_units_inst<D, L>(int);
+SPH_DECLARE_UNITS_INST(0, 0)
+SPH_DECLARE_UNITS_INST(0, 32)
+SPH_DECLARE_UNITS_INST(0, 64)
+SPH_DECLARE_UNITS_INST(0, 96)
+SPH_DECLARE_UNITS_INST(0, 128)
+SPH_DECLARE_UNITS_INST(0, 192)
+SPH_DECLARE_UNITS_INST(1, 0)
+SPH_DECLARE_UNITS_INST(1, 32)
+SPH_DECLARE_UNITS_INST(1, 64)
+SPH_DECLARE_UNITS_INST(1, 96)
+SPH_DECLARE_UNITS_INST(1, 128)
+SPH_DECLARE_UNITS_INST(1, 192)
+#undef SPH_DECLARE_UNITS_INST
+size_t units_smem_bytes(const ShellArgs2& a, int precision);
+cudaError_t launch_units(const ShellArgs2& a, int precision, size_t smem, const LaunchIO& io, const int* units,
+                         int nunits, cudaStream_t s);
+cudaError_t launch_copy_shells(const double* in, double* out, const int* list, int nshells, size_t shell_values,
+                               cudaStream_t s);
+
 size_t shell_smem_bytes(const ShellArgs2& a, int precision);
 int fixed_length(const ShellArgs2& a);
 cudaError_t launch_shell(const ShellArgs2& a, int precision, int threads, size_t smem, const LaunchIO& io,
@@ -166,10 +200,21 @@ struct sph_filter_plan_s {
   sph::ShellArgs args{};
   size_t smem_bytes = 0;
   int launches = 1;
+  std::atomic<long long> launched{0};  // kernel launches enqueued so far (captures count once)
 
   // staged shell kernel (used when the shape fits it)
   bool use_v2 = false;
   bool cluster = false;       // a 2-CTA cluster filters each shell
+  // Split launch (single-CTA plans): shells whose theta pass is the identity ("sparse") are copied
+  // in -> out and only their active ring pairs are filtered, by the units kernel, several shells'
+  // pairs per CTA; the other ("dense") shells run the shell kernel from a list. Per field v, its
+  // entries are [off[v], off[v + 1]) of each list.
+  bool split = false;
+  int* d_dense = nullptr;     // v * Nr + i
+  int* d_sparse = nullptr;    // v * Nr + i
+  int* d_units = nullptr;     // (v * Nr + i) * Ntheta + j: ring pair (j, Ntheta - 1 - j), one active
+  std::vector<int> dense_off, sparse_off, units_off;
+  size_t smem_units = 0;
   sph::ShellArgs2 args2{};
   int threads2 = 0;
   size_t smem2 = 0;

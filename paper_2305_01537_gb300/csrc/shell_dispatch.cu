@@ -54,6 +54,45 @@ cudaError_t launch_shell_cl(const ShellArgs2& a, int precision, int threads, siz
   return fixed ? launch_shell_cl_inst<0, 256, 0>(a, threads, smem, io, s) : launch_shell_cl_inst<0, 0, 0>(a, threads, smem, io, s);
 }
 
+size_t units_smem_bytes(const ShellArgs2& a, int) { return shellk::units_smem(a); }
+
+template <int DFP>
+static cudaError_t launch_units_p(const ShellArgs2& a, size_t smem, const LaunchIO& io, const int* units, int n,
+                                  cudaStream_t s) {
+  switch (fixed_length(a)) {
+    case 32: return launch_units_inst<DFP, 32>(a, smem, io, units, n, s);
+    case 64: return launch_units_inst<DFP, 64>(a, smem, io, units, n, s);
+    case 96: return launch_units_inst<DFP, 96>(a, smem, io, units, n, s);
+    case 128: return launch_units_inst<DFP, 128>(a, smem, io, units, n, s);
+    case 192: return launch_units_inst<DFP, 192>(a, smem, io, units, n, s);
+    case 256: return cudaErrorInvalidValue;  // 128 x 256 shells run on CTA pairs, without units
+    default: return launch_units_inst<DFP, 0>(a, smem, io, units, n, s);
+  }
+}
+
+cudaError_t launch_units(const ShellArgs2& a, int precision, size_t smem, const LaunchIO& io, const int* units,
+                         int nunits, cudaStream_t s) {
+  if (nunits <= 0) return cudaSuccess;
+  return precision == SPH_PREC_F32X2 ? launch_units_p<1>(a, smem, io, units, nunits, s)
+                                     : launch_units_p<0>(a, smem, io, units, nunits, s);
+}
+
+// Copies whole shells in -> out (the sparse shells of an out-of-place call; the units kernel then
+// overwrites their active rows): one CTA per listed shell, 16-byte pieces.
+__global__ void __launch_bounds__(256) copy_shells_kernel(const double2* __restrict__ in, double2* __restrict__ out,
+                                                          const int* list, int shell_pairs) {
+  const size_t base = (size_t)list[blockIdx.x] * (size_t)shell_pairs;
+  for (int c = threadIdx.x; c < shell_pairs; c += blockDim.x) __stcs(out + base + c, __ldcs(in + base + c));
+}
+
+cudaError_t launch_copy_shells(const double* in, double* out, const int* list, int nshells, size_t shell_values,
+                               cudaStream_t s) {
+  if (nshells <= 0) return cudaSuccess;
+  copy_shells_kernel<<<(unsigned)nshells, 256, 0, s>>>(reinterpret_cast<const double2*>(in),
+                                                       reinterpret_cast<double2*>(out), list, (int)(shell_values / 2));
+  return cudaGetLastError();
+}
+
 template <int DFP>
 static cudaError_t set_attr_p(int bytes) {
   cudaError_t e = cudaSuccess;
@@ -68,6 +107,9 @@ static cudaError_t set_attr_p(int bytes) {
   both(set_attr_inst<DFP, 128, 0>, set_attr_inst<DFP, 128, 1>);
   both(set_attr_inst<DFP, 192, 0>, set_attr_inst<DFP, 192, 1>);
   both(set_attr_inst<DFP, 256, 0>, nullptr);
+  both(set_attr_units_inst<DFP, 0>, set_attr_units_inst<DFP, 32>);
+  both(set_attr_units_inst<DFP, 64>, set_attr_units_inst<DFP, 96>);
+  both(set_attr_units_inst<DFP, 128>, set_attr_units_inst<DFP, 192>);
   both(set_attr_cl_inst<DFP, 0, 0>, set_attr_cl_inst<DFP, 0, 1>);
   both(set_attr_cl_inst<DFP, 256, 0>, set_attr_cl_inst<DFP, 256, 1>);
   return e;

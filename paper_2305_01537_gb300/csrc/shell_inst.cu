@@ -36,6 +36,19 @@ cudaError_t set_attr_inst<SPH_SHELL_DF, SPH_SHELL_LEN, SPH_SHELL_HYB>(int bytes)
 }
 #endif
 
+#if SPH_SHELL_HYB == 0 && SPH_SHELL_LEN != 256
+template <>
+cudaError_t launch_units_inst<SPH_SHELL_DF, SPH_SHELL_LEN>(const ShellArgs2& a, size_t smem, const LaunchIO& io,
+                                                         const int* units, int nunits, cudaStream_t s) {
+  return shellk::launch_units_impl<InstPolicy, SPH_SHELL_LEN>(a, smem, io, units, nunits, s);
+}
+
+template <>
+cudaError_t set_attr_units_inst<SPH_SHELL_DF, SPH_SHELL_LEN>(int bytes) {
+  return shellk::set_attr_units_impl<InstPolicy, SPH_SHELL_LEN>(bytes);
+}
+#endif
+
 #if SPH_SHELL_LEN == 0 || SPH_SHELL_LEN == 256
 template <>
 cudaError_t launch_shell_cl_inst<SPH_SHELL_DF, SPH_SHELL_LEN, SPH_SHELL_HYB>(const ShellArgs2& a, int threads,

@@ -1315,7 +1315,8 @@ template <class P, int LEN, bool HYB>
 __global__ void __launch_bounds__(512) shell_kernel(ShellArgs2 A, LaunchIO io) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Layout<P> L = carve<P>(A, smem_raw);
-  const int sidx = blockIdx.x;
+  // a launch over a list of shells reads its shell index there (same encoding as the grid's)
+  const int sidx = io.list ? __ldg(io.list + blockIdx.x) : (int)blockIdx.x;
   // the shell's asynchronous copy first, then the twiddles (16-byte table entries copied as they
   // are); the tables in filter_shell are fetched while these are in flight. An in-place call
   // copies only the rows a pass transforms, once filter_shell knows them.
@@ -1334,6 +1335,171 @@ __global__ void __launch_bounds__(512) shell_kernel(ShellArgs2 A, LaunchIO io) {
   filter_shell<P, LEN, HYB>(A, io, L, L.buf, sidx, K);
 }
 
+
+// ------------------------------------------------------------------ sparse shells: ring-pair units
+
+// A shell whose theta pass is the identity (exponential or sharp filter, l_max >= Ntheta) changes
+// only in its active phi rings. The units kernel filters the active ring pairs of many such shells:
+// a CTA stages kUnits pairs (rows 2u and 2u + 1 of a small row buffer, u < kUnits), each with its
+// own power-of-two scale, and runs the phi pass on them with the shell kernel's stages; the copy
+// kernel moves the shells' other rows (out-of-place calls). Several such CTAs fit an SM, where a
+// whole-shell CTA would run a few pairs with most of its threads idle.
+constexpr int kUnits = 8;
+constexpr int kUnitThreads = 256;
+
+// PhiAcc over the row buffer: the pair list is (2u | general << 30, 2u + 1), and row_tab[r] is the
+// element offset of row r's multipliers in the global table. A lone middle ring (Ntheta odd) is
+// paired with a zero row that takes its multipliers (its output is zero and is not stored).
+template <class P>
+struct PhiUnitsAcc : PhiAcc<P> {
+  using T = typename P::T;
+  using Seq = typename PhiAcc<P>::Seq;
+  const unsigned* row_tab;
+  __device__ __forceinline__ T row_mult(int r, int m) const {
+    return P::from_tab(this->gtab, (size_t)row_tab[r] + (m <= this->hN ? m : this->N - m));
+  }
+  __device__ __forceinline__ T mult(const Seq& s, int m) const { return row_mult(s.j1, m); }
+  __device__ __forceinline__ void mult2(const Seq& s, int m, T& f1, T& f2) const {
+    f1 = row_mult(s.j1, m);
+    f2 = row_mult(s.j2, m);
+  }
+};
+
+__host__ __device__ __forceinline__ size_t units_smem(const ShellArgs2& a) {
+  auto up = [](size_t x) { return (x + 15) / 16 * 16; };
+  size_t s = up(8 * (size_t)(2 * kUnits) * a.ldS);  // rows
+  s += up(16 * (size_t)kUnits * a.Nph);              // FFT scratch
+  s += up(16 * (size_t)a.Nph);                       // twiddles
+  s += up(sizeof(int2) * kUnits);                    // pair list
+  s += up(sizeof(unsigned) * 2 * kUnits);            // row_tab
+  s += up(sizeof(int) * (kUnits + 4));               // per-unit exponents, flags
+  return s;
+}
+
+template <class P, int LEN>
+__global__ void __launch_bounds__(kUnitThreads) units_kernel(ShellArgs2 A, LaunchIO io, const int* units, int nunits) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr bool dfp = std::is_same<P, DF>::value;
+  const int Nth = LEN ? LEN / 2 : A.Nth, Nph = LEN ? LEN : A.Nph, ld = LEN ? LEN + 2 : A.ldS;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    unsigned char* p = smem_raw + off;
+    off = (off + bytes + 15) / 16 * 16;
+    return p;
+  };
+  unsigned char* rows = take(8 * (size_t)(2 * kUnits) * ld);
+  const uint32_t S = saddr(rows);
+  const uint32_t lin = saddr(take(16 * (size_t)kUnits * Nph));
+  const uint32_t tw = saddr(take(16 * (size_t)Nph));
+  int2* pairs = reinterpret_cast<int2*>(take(sizeof(int2) * kUnits));
+  unsigned* row_tab = reinterpret_cast<unsigned*>(take(sizeof(unsigned) * 2 * kUnits));
+  int* ue = reinterpret_cast<int*>(take(sizeof(int) * (kUnits + 4)));  // [u] exponent, [kUnits] general
+  const int u0 = blockIdx.x * kUnits, nu = min(kUnits, nunits - u0);
+  const int h2 = Nph / 2;
+
+  // the pairs' rows (16-byte pieces), then the twiddles
+  for (int c = threadIdx.x; c < nu * 2 * h2; c += blockDim.x) {
+    const int r = c / h2, k2 = c - r * h2, u = r >> 1;
+    const int e = units[u0 + u], j = e % Nth, sh = e / Nth;  // sh = v * Nr + i
+    const int row = (r & 1) ? Nth - 1 - j : j;
+    if ((r & 1) && row == j) {  // lone middle ring: a zero partner row
+      F64::st16(S + (uint32_t)(r * ld + 2 * k2) * 8u, F64::C{0.0, 0.0});
+      continue;
+    }
+    const double* src = static_cast<const double*>(io.in) + ((size_t)sh * Nth + row) * Nph + 2 * k2;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(S + (uint32_t)(r * ld + 2 * k2) * 8u), "l"(src)
+                 : "memory");
+  }
+  const typename P::C* twph_g = static_cast<const typename P::C*>(A.tw_ph);
+  for (int n = threadIdx.x; n < Nph; n += blockDim.x)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tw + 16u * n), "l"(twph_g + n) : "memory");
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  if (threadIdx.x == 0) ue[kUnits] = 0;
+  __syncthreads();
+  if (threadIdx.x < nu) {
+    const int u = threadIdx.x;
+    const int e = units[u0 + u], j = e % Nth, sh = e / Nth, v = sh / A.Nr, i = sh - v * A.Nr, jj = Nth - 1 - j;
+    const int cls = A.var[v].cls;
+    const uint8_t* ri = A.ring_info + ((size_t)cls * A.Nr + i) * Nth;
+    const int g = jj != j ? (ri[j] >> 1) & 1 : 0;  // bit 1: the two rings' multipliers differ
+    pairs[u] = make_int2(2 * u | (g << 30), 2 * u + 1);
+    const unsigned base = (unsigned)(((size_t)cls * A.Nr + i) * (size_t)Nth) * (unsigned)(Nph / 2 + 1);
+    row_tab[2 * u] = base + (unsigned)j * (Nph / 2 + 1);
+    row_tab[2 * u + 1] = base + (unsigned)jj * (Nph / 2 + 1);  // jj == j for a lone ring
+    if (g) atomicOr(&ue[kUnits], 1);
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncthreads();
+  // compensated FP32: one scale per unit (its rows' largest exponent), conversion in place
+  if constexpr (dfp) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int u = warp; u < nu; u += blockDim.x >> 5) {
+      const int nr = 2;
+      unsigned em = 0;
+      for (int c = lane; c < nr * h2; c += 32) {
+        const int r = 2 * u + c / h2;
+        const F64::C x = F64::ld16(S + 8u * (uint32_t)(r * ld + 2 * (c % h2)));
+        em = max(em, max((unsigned)df_exp_field(x.re), (unsigned)df_exp_field(x.im)));
+      }
+      em = __reduce_max_sync(0xffffffffu, em);
+      const int E = (int)em - 1023;
+      if (lane == 0) ue[u] = E;
+      for (int c = lane; c < nr * h2; c += 32) {
+        const int r = 2 * u + c / h2;
+        const uint32_t a = S + 8u * (uint32_t)(r * ld + 2 * (c % h2));
+        const F64::C x = F64::ld16(a);
+        P::st16(a, typename P::C{to_real<P>(x.re, E), to_real<P>(x.im, E)});
+      }
+    }
+    __syncthreads();
+  }
+  Consts<P> K;
+  K.c8 = P::from_tab(A.consts, 0);
+  K.s3 = P::from_tab(A.consts, 1);
+  PhiUnitsAcc<P> PA;
+  PA.S = S;
+  PA.ov = 0;
+  PA.lin = lin;
+  PA.pairs = pairs;
+  PA.gtab = A.g_ph;
+  PA.gbase = 0;
+  PA.gbase_alt = 0;
+  PA.hyb = false;
+  PA.ld = ld;
+  PA.N = Nph;
+  PA.N8 = Nph & ~7;
+  PA.hN = Nph / 2;
+  PA.hN8 = (Nph / 2) & ~7;
+  PA.nh = Nph / 2 + 1;
+  PA.b0 = 0;
+  PA.row_tab = row_tab;
+  PA.template fix<LEN>();
+  run_pass<P, PhiUnitsAcc<P>, LEN>(PA, Nph, nu, A.f_ph, tw, K, ue[kUnits] != 0);
+  // store the filtered rows (the last stage synchronised the block)
+  for (int c = threadIdx.x; c < nu * 2 * h2; c += blockDim.x) {
+    const int r = c / h2, k2 = c - r * h2, u = r >> 1;
+    const int e = units[u0 + u], j = e % Nth, sh = e / Nth;
+    const int row = (r & 1) ? Nth - 1 - j : j;
+    if ((r & 1) && row == j) continue;  // the zero partner of a lone ring
+    const int E = dfp ? ue[u] : 0;
+    const typename P::C y = P::ld16(S + 8u * (uint32_t)(r * ld + 2 * k2));
+    double2* dst = reinterpret_cast<double2*>(static_cast<double*>(io.out) + ((size_t)sh * Nth + row) * Nph) + k2;
+    __stcs(dst, make_double2(from_real<P>(y.re, E), from_real<P>(y.im, E)));
+  }
+}
+
+template <class P, int LEN>
+cudaError_t launch_units_impl(const ShellArgs2& a, size_t smem, const LaunchIO& io, const int* units, int nunits,
+                              cudaStream_t s) {
+  const dim3 grid((unsigned)((nunits + kUnits - 1) / kUnits));
+  units_kernel<P, LEN><<<grid, kUnitThreads, smem, s>>>(a, io, units, nunits);
+  return cudaGetLastError();
+}
+
+template <class P, int LEN>
+cudaError_t set_attr_units_impl(int bytes) {
+  return cudaFuncSetAttribute(units_kernel<P, LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
 
 // ------------------------------------------------------------------ cluster-pair kernel (large shells)
 
@@ -1785,7 +1951,7 @@ size_t shell_smem(const ShellArgs2& a) {
 
 template <class P, int LEN, bool HYB>
 cudaError_t launch_impl(const ShellArgs2& a, int threads, size_t smem, const LaunchIO& io, cudaStream_t s) {
-  const dim3 grid((unsigned)(io.var_count * a.Nr));
+  const dim3 grid((unsigned)(io.list ? io.nlist : io.var_count * a.Nr));
   shell_kernel<P, LEN, HYB><<<grid, threads, smem, s>>>(a, io);
   return cudaGetLastError();
 }
