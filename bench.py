@@ -44,7 +44,8 @@ DF_PEAK_TFLOPS = F32_INSTR_PER_S / DF_INSTR_PER_FLOP / 1e12
 
 KERNEL_FAMILIES = {
     # CUDA sources whose device code each kernel family compiles from
-    "plain": ["shell_kernel.cuh", "shell_inst.cu", "shell_dispatch.cu", "filter_plain.cu", "df32.h"],
+    "plain": ["shell_kernel.cuh", "shell_inst.cu", "shell_dispatch.cu", "filter_plain.cu", "df32.h",
+              "capi.cu"],  # capi.cu: which kernels an application launches (the split)
     "tc": ["tc.cu", "df32.h"],
 }
 

@@ -278,6 +278,10 @@ sph_status setup_v2(sph_filter_plan_s* p) {
       sph_status st = up_list(&p->d_dense, dense);
       if (st == SPH_OK) st = up_list(&p->d_sparse, sparse);
       if (st == SPH_OK) st = up_list(&p->d_units, units);
+      if (st == SPH_OK && (cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess ||
+                           cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                           cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess))
+        st = SPH_ECUDA;
       if (st != SPH_OK) return st;
       p->split = true;
     }
@@ -310,6 +314,9 @@ void free_plan(sph_filter_plan_s* p) {
   cudaFree(p->d_dense);
   cudaFree(p->d_sparse);
   cudaFree(p->d_units);
+  if (p->side) cudaStreamDestroy(p->side);
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  if (p->ev_join) cudaEventDestroy(p->ev_join);
   tc_free(p);
   if (p->tc_ev) cudaEventDestroy(p->tc_ev);
   cudaFree(p->d_stage_in);
@@ -392,29 +399,44 @@ sph_status launch_plan_vars(sph_filter_plan_s* p, const void* in, const void* au
   if (split) {
     // sparse shells: copied (out of place), then their active ring pairs filtered by the units
     // kernel; dense shells: the shell kernel over their list (both orders: a sparse shell's only
-    // pass is the symmetric phi pass)
+    // pass is the symmetric phi pass). The two sets of shells are disjoint, so when both have work
+    // the copy and the units kernel run on the side stream while the shell kernel runs here.
     const int vb = var_begin, ve = var_begin + var_count;
     const int d0 = p->dense_off[(size_t)vb], d1 = p->dense_off[(size_t)ve];
     const int s0 = p->sparse_off[(size_t)vb], s1 = p->sparse_off[(size_t)ve];
     const int u0 = p->units_off[(size_t)vb], u1 = p->units_off[(size_t)ve];
+    const bool copy = in != out && s1 > s0, dense_work = d1 > d0, side_work = copy || u1 > u0;
+    const bool fork = dense_work && side_work;
+    std::lock_guard<std::mutex> lock(p->split_mu);
+    cudaStream_t s_main = (cudaStream_t)stream, aux_s = fork ? p->side : s_main;
     int n = 0;
-    if (in != out && s1 > s0) {
-      e = launch_copy_shells(static_cast<const double*>(in), static_cast<double*>(out), p->d_sparse + s0, s1 - s0,
-                             (size_t)p->Nth * p->Nph, (cudaStream_t)stream);
-      ++n;
+    if (fork) {
+      e = cudaEventRecord(p->ev_fork, s_main);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(aux_s, p->ev_fork, 0);
     }
-    if (e == cudaSuccess && d1 > d0) {
+    if (e == cudaSuccess && dense_work) {
       LaunchIO dense = io;
       dense.var_begin = 0;
       dense.var_count = p->nvars;
       dense.list = p->d_dense + d0;
       dense.nlist = d1 - d0;
-      e = launch_shell(p->args2, p->precision, p->threads2, p->smem2, dense, (cudaStream_t)stream);
+      e = launch_shell(p->args2, p->precision, p->threads2, p->smem2, dense, s_main);
+      ++n;
+    }
+    if (e == cudaSuccess && copy) {
+      e = launch_copy_shells(static_cast<const double*>(in), static_cast<double*>(out), p->d_sparse + s0, s1 - s0,
+                             (size_t)p->Nth * p->Nph, aux_s);
       ++n;
     }
     if (e == cudaSuccess && u1 > u0) {
-      e = launch_units(p->args2, p->precision, p->smem_units, io, p->d_units + u0, u1 - u0, (cudaStream_t)stream);
+      e = launch_units(p->args2, p->precision, p->smem_units, io, p->d_units + u0, u1 - u0, aux_s);
       ++n;
+    }
+    if (fork) {
+      // join even after an error, so that the caller's stream (or capture) is never left forked
+      cudaError_t ej = cudaEventRecord(p->ev_join, aux_s);
+      if (ej == cudaSuccess) ej = cudaStreamWaitEvent(s_main, p->ev_join, 0);
+      if (e == cudaSuccess) e = ej;
     }
     if (e == cudaSuccess) p->launched += n;
   } else {

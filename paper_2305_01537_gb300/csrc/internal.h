@@ -209,8 +209,14 @@ struct sph_filter_plan_s {
   // in -> out and only their active ring pairs are filtered, by the units kernel, several shells'
   // pairs per CTA; the other ("dense") shells run the shell kernel from a list. Per field v, its
   // entries are [off[v], off[v + 1]) of each list.
+  // The copy and the units kernel run on a side stream of the plan, beside the shell kernel on
+  // the caller's stream: forked from it and joined back by events (split_mu orders the calls that
+  // share them).
   bool split = false;
-  int* d_dense = nullptr;     // v * Nr + i
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  std::mutex split_mu;
+  int* d_dense = nullptr;     // i * nvars + v (the shell kernel's grid index over all fields)
   int* d_sparse = nullptr;    // v * Nr + i
   int* d_units = nullptr;     // (v * Nr + i) * Ntheta + j: ring pair (j, Ntheta - 1 - j), one active
   std::vector<int> dense_off, sparse_off, units_off;

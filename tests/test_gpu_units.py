@@ -176,3 +176,53 @@ def test_units_with_scales_apart(torch_cuda, prec):
     for jr in range(16):
         err = np.abs(y[:, :, jr] - ref[:, :, jr]).max() / np.abs(ref[:, :, jr]).max()
         assert err <= TOL, (jr, err)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_same_plan_on_two_streams(torch_cuda, prec):
+    """Calls of one split plan on two streams, each forking its copy and units kernels onto the
+    plan's side stream: every result is the filter of its own input."""
+    import torch
+    from paper_2305_01537_gb300 import Plan
+    g = mixed_grid(12, 32, 64)
+    xs = [W.random_state(g.shape, seed=40 + k) for k in range(4)]
+    refs = [oracle.filter(x, g.parity, g.kind, g.L, g.r, g.dr_min, g.floor) for x in xs]
+    plan = Plan.from_grid(g, precision=prec)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    xd = [torch.from_numpy(x).cuda() for x in xs]
+    torch.cuda.synchronize()
+    for rep in range(3):
+        outs = [torch.empty_like(x) for x in xd]
+        for k in range(4):
+            plan.apply(xd[k], out=outs[k], stream=streams[k % 2])
+        torch.cuda.synchronize()
+        assert plan.sync_status() == 0
+        for k in range(4):
+            assert field_errors(outs[k].cpu().numpy(), refs[k]).max() <= TOL, (rep, k)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_split_plan_in_cuda_graph(torch_cuda, prec):
+    """A split call captured into a CUDA graph (the fork onto the side stream and the join are
+    captured as graph edges) and replayed on new inputs."""
+    import torch
+    from paper_2305_01537_gb300 import Plan
+    g = mixed_grid(10, 32, 64)
+    plan = Plan.from_grid(g, precision=prec)
+    x = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        plan.apply(x, out=y, stream=s)  # warm-up outside the capture
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        plan.apply(x, out=y, stream=s)
+    for seed in (1, 2):
+        xh = W.random_state(g.shape, seed=seed)
+        x.copy_(torch.from_numpy(xh))
+        graph.replay()
+        torch.cuda.synchronize()
+        ref = oracle.filter(xh, g.parity, g.kind, g.L, g.r, g.dr_min, g.floor)
+        assert field_errors(y.cpu().numpy(), ref).max() <= TOL
