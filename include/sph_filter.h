@@ -24,6 +24,12 @@
  *    plan are allowed. (The tensor-core form keeps per-CTA scratch in the plan: the library orders
  *    its launches of one plan one after the other across streams, except inside a CUDA-graph
  *    capture, whose launches are ordered by the graph.)
+ *  - A plan with shells whose theta pass is the identity (see sph_filter_plan_launches) runs part
+ *    of an FP64 call on a stream it owns: the call forks that stream from `stream` with an event
+ *    and joins it back with another before returning, so work enqueued on `stream` afterwards
+ *    sees the whole result, as with any call. The calls of one plan share that stream, so their
+ *    forked parts run one after the other. A CUDA-graph capture records the fork and the join as
+ *    graph dependencies.
  */
 #ifndef SPH_FILTER_H
 #define SPH_FILTER_H
