@@ -278,8 +278,12 @@ sph_status setup_v2(sph_filter_plan_s* p) {
       sph_status st = up_list(&p->d_dense, dense);
       if (st == SPH_OK) st = up_list(&p->d_sparse, sparse);
       if (st == SPH_OK) st = up_list(&p->d_units, units);
-      if (st == SPH_OK && (cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess ||
+      int prio_low = 0, prio_high = 0;
+      if (st == SPH_OK && (cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) != cudaSuccess ||
+                           cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess ||
+                           cudaStreamCreateWithPriority(&p->side_copy, cudaStreamNonBlocking, prio_high) != cudaSuccess ||
                            cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                           cudaEventCreateWithFlags(&p->ev_copy, cudaEventDisableTiming) != cudaSuccess ||
                            cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess))
         st = SPH_ECUDA;
       if (st != SPH_OK) return st;
@@ -315,7 +319,9 @@ void free_plan(sph_filter_plan_s* p) {
   cudaFree(p->d_sparse);
   cudaFree(p->d_units);
   if (p->side) cudaStreamDestroy(p->side);
+  if (p->side_copy) cudaStreamDestroy(p->side_copy);
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  if (p->ev_copy) cudaEventDestroy(p->ev_copy);
   if (p->ev_join) cudaEventDestroy(p->ev_join);
   tc_free(p);
   if (p->tc_ev) cudaEventDestroy(p->tc_ev);
@@ -400,7 +406,8 @@ sph_status launch_plan_vars(sph_filter_plan_s* p, const void* in, const void* au
     // sparse shells: copied (out of place), then their active ring pairs filtered by the units
     // kernel; dense shells: the shell kernel over their list (both orders: a sparse shell's only
     // pass is the symmetric phi pass). The two sets of shells are disjoint, so when both have work
-    // the copy and the units kernel run on the side stream while the shell kernel runs here.
+    // the copy (high-priority side stream) and then the units kernel (normal-priority side stream)
+    // run beside the shell kernel on the caller's stream.
     const int vb = var_begin, ve = var_begin + var_count;
     const int d0 = p->dense_off[(size_t)vb], d1 = p->dense_off[(size_t)ve];
     const int s0 = p->sparse_off[(size_t)vb], s1 = p->sparse_off[(size_t)ve];
@@ -409,10 +416,11 @@ sph_status launch_plan_vars(sph_filter_plan_s* p, const void* in, const void* au
     const bool fork = dense_work && side_work;
     std::lock_guard<std::mutex> lock(p->split_mu);
     cudaStream_t s_main = (cudaStream_t)stream, aux_s = fork ? p->side : s_main;
+    cudaStream_t copy_s = fork ? p->side_copy : s_main;
     int n = 0;
     if (fork) {
       e = cudaEventRecord(p->ev_fork, s_main);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(aux_s, p->ev_fork, 0);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(copy ? copy_s : aux_s, p->ev_fork, 0);
     }
     if (e == cudaSuccess && dense_work) {
       LaunchIO dense = io;
@@ -425,8 +433,15 @@ sph_status launch_plan_vars(sph_filter_plan_s* p, const void* in, const void* au
     }
     if (e == cudaSuccess && copy) {
       e = launch_copy_shells(static_cast<const double*>(in), static_cast<double*>(out), p->d_sparse + s0, s1 - s0,
-                             (size_t)p->Nth * p->Nph, aux_s);
+                             (size_t)p->Nth * p->Nph, copy_s);
       ++n;
+    }
+    if (fork && copy) {
+      // the units kernel overwrites rows of the copied shells: it waits for the copy (joined even
+      // after an error, like the final join below)
+      cudaError_t ec = cudaEventRecord(p->ev_copy, copy_s);
+      if (ec == cudaSuccess) ec = cudaStreamWaitEvent(aux_s, p->ev_copy, 0);
+      if (e == cudaSuccess) e = ec;
     }
     if (e == cudaSuccess && u1 > u0) {
       e = launch_units(p->args2, p->precision, p->smem_units, io, p->d_units + u0, u1 - u0, aux_s);

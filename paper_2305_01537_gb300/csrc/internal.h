@@ -209,12 +209,13 @@ struct sph_filter_plan_s {
   // in -> out and only their active ring pairs are filtered, by the units kernel, several shells'
   // pairs per CTA; the other ("dense") shells run the shell kernel from a list. Per field v, its
   // entries are [off[v], off[v + 1]) of each list.
-  // The copy and the units kernel run on a side stream of the plan, beside the shell kernel on
+  // The copy and the units kernel run on side streams of the plan, beside the shell kernel on
   // the caller's stream: forked from it and joined back by events (split_mu orders the calls that
-  // share them).
+  // share them). The copy, bound by memory, runs on a high-priority stream so that it overlaps the
+  // shell kernel's arithmetic early; the units kernel follows it on a normal-priority stream.
   bool split = false;
-  cudaStream_t side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t side = nullptr, side_copy = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_copy = nullptr, ev_join = nullptr;
   std::mutex split_mu;
   int* d_dense = nullptr;     // i * nvars + v (the shell kernel's grid index over all fields)
   int* d_sparse = nullptr;    // v * Nr + i
