@@ -354,6 +354,60 @@ def run_chain(args):
     return 0
 
 
+def run_constraints(args):
+    """The algebraic-constraint map after filtering (Sec. II.C) on a 13-field state (h 11..33, A
+    11..33, lapse) of 256 x 64 x 128 points (218 MB, larger than L2), in place; the theta-filtered
+    shells are those with l_max < Ntheta for the metric fields' filter (exponential, L = 3)."""
+    import numpy as np
+    import torch
+    from paper_2305_01537_gb300 import enforce_constraints
+    Nr, Nth, Nph = 256, 64, 128
+    rng = np.random.default_rng(21)
+    x = rng.standard_normal((13, Nr, Nth, Nph))
+    x[:6] *= 0.05
+    x[12] = rng.uniform(0.0, 1.0, (Nr, Nth, Nph))
+    r = np.arange(Nr) + 0.5
+    flags = (np.maximum(2.0, 2.0 * r * 3.0) < Nth).astype(np.uint8)
+    hv, av, al = list(range(6)), list(range(6, 12)), 12
+    x_host = torch.from_numpy(x).pin_memory()
+    xd = x_host.cuda()
+    fd = torch.from_numpy(flags).cuda()
+    stream = torch.cuda.current_stream()
+    points = Nr * Nth * Nph
+    bh = flags.astype(bool)[:, None, None] & (x[12] < 0.3)
+    n_bh = int(bh.sum())
+    # algorithmic bytes: standard points read 13 and write 12 values, modified ones read 7 and write 1
+    bytes_per_step = 8.0 * ((points - n_bh) * 25 + n_bh * 8)
+    with ClockSampler(0) as clk:
+        t0 = time.time()
+        ms = _timed(lambda: enforce_constraints(xd, hv, av, al, fd, 0.3, stream), args.steps, args.warmup, stream)
+        clk.mark(t0, time.time())
+    out_host = torch.empty_like(x_host).pin_memory()
+
+    def e2e_step():
+        xd.copy_(x_host, non_blocking=True)
+        enforce_constraints(xd, hv, av, al, fd, 0.3, stream)
+        out_host.copy_(xd, non_blocking=True)
+
+    e2e_ms = _timed(e2e_step, args.steps, args.warmup, stream)
+    peaks, src = measured_peaks()
+    gbs = bytes_per_step * args.steps / (ms * 1e-3) / 1e9
+    print(json.dumps({
+        "metric": "constraint-map Gpoints/s (Sec. II.C algebraic constraints after filtering, FP64)",
+        "value": points * args.steps / (ms * 1e-3) / 1e9, "unit": "Gpoints/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "constraints_256x64x128", "Nr": Nr, "Ntheta": Nth, "Nphi": Nph, "fields": 13,
+                   "modified_form_points": n_bh, "l2": f"state ({8 * 13 * points / 1e6:.0f} MB) larger than L2; no flush"},
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": gbs / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
+                     "kernel": "constraint_kernel", "bytes_per_launch": bytes_per_step},
+        "e2e": {"value": points * args.steps / (e2e_ms * 1e-3) / 1e9, "unit": "Gpoints/s",
+                "h2d_bytes_per_step": 8 * 13 * points, "d2h_bytes_per_step": 8 * 13 * points},
+        "gpu_launches": args.steps, "clocks": clk.summary()}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -365,7 +419,7 @@ def main():
     ap.add_argument("--workload", default="state28_128x64x128",
                     choices=["state28_128x64x128", "state28_256x128x256", "batch6_uneven", "chain8_128x64x128",
                              "state28_32x128x256", "hybrid28_128x64x128", "hybrid28_256x128x256",
-                             "hybrid28_32x128x256"])
+                             "hybrid28_32x128x256", "constraints_256x64x128"])
     ap.add_argument("--autotune", action="store_true", help="autotune the plan's launch shape before timing")
     ap.add_argument("--inplace", action="store_true",
                     help="filter the state in place (out = in): only the rows a pass transforms are moved")
@@ -378,6 +432,8 @@ def main():
         return run_batch(args)
     if args.workload == "chain8_128x64x128":
         return run_chain(args)
+    if args.workload == "constraints_256x64x128":
+        return run_constraints(args)
 
     import torch
     import torch.distributed as dist

@@ -188,6 +188,31 @@ int sph_filter_plan_launches(sph_filter_plan plan);
  * into a CUDA graph counts once, when it is captured; replays do not add to it). 0 for NULL. */
 long long sph_filter_plan_launch_count(sph_filter_plan plan);
 
+/* Algebraic constraints applied after filtering (Sec. II.C, "Filtering spacetime fields in the
+ * presence of BHs": the constraints det(gamma_bar) = det(gamma_hat) and gamma_bar^{ij} A_bar_ij = 0
+ * and the substitutions that enforce them), in place on a state, point by point:
+ *  - standard form: with m = delta + h, the metric becomes det(m)^(-1/3) m (so det = 1) and A loses
+ *    m tr / 3, tr = sum_ab (m^-1)_ab A_ab (its trace in the metric);
+ *  - modified form, at points of shells flagged in theta_filtered whose lapse is below alpha_bh
+ *    (strictly): h_11 is solved from det(m) = 1 with the other components kept, A is kept.
+ * Components are orthonormal-basis components of the conformal metric perturbation h and of the
+ * conformal extrinsic curvature A (gamma_bar_ij = R_i R_j (delta_ij + h_ij) for the spherical
+ * scale factors R = (1, r, r sin theta), which cancel from both constraints).
+ * Arguments:
+ *  - state: device FP64 state [nvars][Nr][Ntheta][Nphi] (layout of the filter calls), modified in
+ *    place; fields other than the 13 named below are not touched.
+ *  - h_vars, a_vars: host arrays of 6 field indices each, in the order 11, 12, 13, 22, 23, 33;
+ *    alpha_var: the lapse field. All 13 must be distinct and in [0, nvars).
+ *  - theta_filtered: device array of Nr bytes, nonzero for the shells where the theta filter is
+ *    active (e.g. l_max < Ntheta for the metric fields' filter), or NULL for none (standard form
+ *    everywhere). alpha_bh: the lapse threshold of the modified form (0.3 in the paper).
+ * Returns SPH_EINVAL for a NULL or host state, bad sizes, indices out of range or repeated, or a
+ * non-finite alpha_bh (nothing is enqueued); SPH_ECUDA if the launch fails. Asynchronous on
+ * `stream`. A point whose det(m) is not positive gives non-finite values (no physical metric). */
+sph_status sph_enforce_constraints(double* state, int nvars, int Nr, int Ntheta, int Nphi, const int* h_vars,
+                                   const int* a_vars, int alpha_var, const unsigned char* theta_filtered,
+                                   double alpha_bh, sph_stream_t stream);
+
 /* Static description of a status code. */
 const char* sph_filter_status_string(sph_status status);
 

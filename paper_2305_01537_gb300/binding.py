@@ -29,6 +29,7 @@ EXPORTED = (
     "sph_filter_plan_launches", "sph_filter_status_string", "sph_filter_batch_create",
     "sph_filter_batch_destroy", "sph_filter_batch_apply", "sph_filter_batch_capture", "sph_filter_batch_launch",
     "sph_filter_plan_autotune", "sph_filter_apply_host_noalloc", "sph_filter_plan_launch_count",
+    "sph_enforce_constraints",
 )
 
 
@@ -72,6 +73,7 @@ def load() -> ctypes.CDLL:
         "sph_filter_plan_points": ([P], LL),
         "sph_filter_plan_launches": ([P], I),
         "sph_filter_plan_launch_count": ([P], LL),
+        "sph_enforce_constraints": ([P, I, I, I, I, P, P, I, P, ctypes.c_double, P], I),
         "sph_filter_status_string": ([I], ctypes.c_char_p),
         "sph_filter_batch_create": ([ctypes.POINTER(P), I, P], I),
         "sph_filter_batch_destroy": ([P], None),
@@ -275,3 +277,28 @@ class Batch:
 def _is_f32(t) -> bool:
     import torch
     return t.dtype == torch.float32
+
+
+def enforce_constraints(state, h_vars: Sequence[int], a_vars: Sequence[int], alpha_var: int,
+                        theta_filtered=None, alpha_bh: float = 0.3, stream=None):
+    """sph_enforce_constraints, in place on a CUDA float64 state [nvars, Nr, Ntheta, Nphi].
+
+    h_vars, a_vars: 6 field indices each (11, 12, 13, 22, 23, 33); theta_filtered: a CUDA uint8 (or
+    bool) tensor of Nr flags, or None. Returns the state."""
+    import torch
+    if not state.is_cuda or state.dtype != torch.float64 or not state.is_contiguous() or state.dim() != 4:
+        raise ValueError("expected a contiguous CUDA float64 state [nvars, Nr, Ntheta, Nphi]")
+    if len(h_vars) != 6 or len(a_vars) != 6:
+        raise ValueError("h_vars and a_vars need 6 field indices each")
+    nvars, Nr, Nth, Nph = state.shape
+    flags = 0
+    if theta_filtered is not None:
+        if not theta_filtered.is_cuda or theta_filtered.numel() != Nr or theta_filtered.element_size() != 1 \
+                or not theta_filtered.is_contiguous():
+            raise ValueError("theta_filtered must be a contiguous CUDA byte tensor of Nr flags")
+        flags = theta_filtered.data_ptr()
+    hv = (ctypes.c_int * 6)(*[int(k) for k in h_vars])
+    av = (ctypes.c_int * 6)(*[int(k) for k in a_vars])
+    _check(load().sph_enforce_constraints(state.data_ptr(), nvars, Nr, Nth, Nph, hv, av, int(alpha_var), flags,
+                                          float(alpha_bh), _stream_handle(stream)), "sph_enforce_constraints")
+    return state
