@@ -6,7 +6,8 @@ imports nothing from the product package.
 
 The arithmetic lives in ``sph_oracle.c`` (plain C, naive O(N^2) DFTs, FP64). The same source
 compiled with ``-DORACLE_LONG_DOUBLE`` gives an extended-precision copy used only to bound the
-oracle's own rounding error. This file builds both with gcc and marshals numpy arrays.
+oracle's own rounding error. This file builds both with gcc and marshals numpy arrays. The
+algebraic-constraint map applied after filtering (same section) is ``oracle.constraints`` (numpy).
 """
 from __future__ import annotations
 
