@@ -5,10 +5,14 @@ One step = one application of the whole filter (theta pass, then phi pass) to ev
 28-field state of the Nr=128, Ntheta=64, Nphi=128 workload (29,360,128 points, FP64 in and out,
 470 MB of I/O: larger than the 126 MB L2, so no flush is needed between steps).
 
-Prints one JSON line. `value` is filtered points per second over all ranks (Gpoints/s), timed on
-the device with CUDA events around K steps after W warm-up steps, inputs already in HBM. `e2e`
-is the same metric through the host-buffer C-ABI call (sph_filter_apply_host), with the
-host->device copy of the state and the device->host copy of the result inside every step.
+Prints one JSON line. `value` is filtered points per second over all ranks (Gpoints/s) of the
+plan's FP64 arithmetic (--precision selects another), timed on the device with CUDA events around
+K steps after W warm-up steps, inputs already in HBM. `e2e` is the same metric through the
+host-buffer C-ABI call (sph_filter_apply_host), with the host->device copy of the state and the
+device->host copy of the result inside every step, next to the measured host-copy ceiling.
+`variants` holds the other arithmetic forms (compensated FP32 pairs, the split-precision
+tensor-core form) timed the same way on the same state, each with its largest per-field error
+against the oracle on the oracle's sample of shells.
 
 --impl reference times the oracle (the plain CPU definition) on the host cores instead.
 Multi-GPU (torchrun): every rank filters its own copy of the state (independent shards, no
@@ -34,12 +38,21 @@ sys.path.insert(0, ROOT)
 from paper_2305_01537_gb300 import workloads as W  # noqa: E402
 
 HBM_FALLBACK_GBS = 6800.0
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
-# Compensated FP32 pairs: FP32 instruction rate (152 SMs x 128 lanes x 2.07 GHz) divided by the FP32
-# instructions one FP64-equivalent flop of the radix-8 butterfly costs (866 / 98 = 8.8)
-F32_INSTR_PER_S = 152 * 128 * 2.07e9
+# ALU roofs measured on this GPU model (GB300, 152 SMs) with an FMA-chain throughput probe: 8
+# independent FMA chains per thread, 8 CTAs of 256 threads per SM, CUDA-event timing, the SM clock
+# read from clock64 over the same kernel (1.8-2.06 GHz). FP64 FMA: 0.626 T/s (2.0-2.2 per SM per
+# clock); FP32 FMA: 38.2 T/s; INT32 IMAD: 20.0 T/s (64 per SM per clock). tcgen05.mma kind::i8 is not
+# available on sm_103a (ptxas rejects it), so no integer tensor-core rate exists.
+FP64_FMA_PER_S = 0.626e12
+FP32_FMA_PER_S = 38.2e12
+FP64_PEAK_TFLOPS = 2 * FP64_FMA_PER_S / 1e12
+FP64_PEAK_SOURCE = "measured FP64 FMA rate (FMA-chain probe on GB300): 0.626 T FMA/s x 2 flop"
+# Compensated FP32 pairs: the measured FP32 FMA issue rate divided by the FP32 instructions one
+# FP64-equivalent flop of the radix-8 butterfly costs (866 / 98 = 8.8)
 DF_INSTR_PER_FLOP = 866.0 / 98.0
-DF_PEAK_TFLOPS = F32_INSTR_PER_S / DF_INSTR_PER_FLOP / 1e12
+DF_PEAK_TFLOPS = FP32_FMA_PER_S / DF_INSTR_PER_FLOP / 1e12
+DF_PEAK_SOURCE = ("FP64-equivalent rate of compensated FP32 pairs: measured FP32 FMA rate (38.2 T/s, FMA-chain "
+                  "probe on GB300) / 8.8 FP32 instructions per FP64-equivalent flop of the radix-8 butterfly")
 
 
 KERNEL_FAMILIES = {
@@ -161,19 +174,27 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self._proc.kill()
 
-    def summary(self):
-        rows = [r for (t, r) in self.rows if self.window is None or self.window[0] <= t <= self.window[1] + 0.15]
+    def summary(self, window=None):
+        """Median SM clock, max clock, throttle reasons and power over the samples taken inside
+        `window` (wall-clock (t0, t1), default the marked one). When the window is shorter than the
+        sampling interval and holds no sample, the whole run's samples (warm-up, timed regions and
+        the end-to-end and variant runs around them) are reported instead, and `scope` says so."""
+        window = window or self.window
+        scope = "timed region"
+        rows = [r for (t, r) in self.rows if window is None or window[0] <= t <= window[1] + 0.15]
         if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        self.rows = rows
-        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
-        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+            rows = [r for (_, r) in self.rows]
+            scope = "whole run (the timed region is shorter than the 100 ms sampling interval)"
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[4 + k].lower() == "active"})
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[4 + k].lower() == "active"})
+        pw = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows),
-                "power_w_max": max(float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit())
-                if any(r[2].replace(".", "").isdigit() for r in self.rows) else None}
+                "reasons": reasons, "samples": len(rows), "scope": scope,
+                "power_w_max": max(pw) if pw else None}
 
 
 def combine_ranks(times_ms, units_per_rank: float, steps: int, device=None):
@@ -206,7 +227,8 @@ def single_grid_workload(name):
 
 def cpu_baseline(grid, x, seconds_target=10.0, stride0=16):
     """The oracle as it stands, on all host cores, over a stratified sample of shells (every s-th
-    radial shell of every field), grown until it has run for about `seconds_target` seconds."""
+    radial shell of every field), grown until it has run for about `seconds_target` seconds.
+    Returns (record, radial indices of the sample, the oracle's output on the sample)."""
     import oracle
     threads = oracle.max_threads()
     stride = stride0
@@ -216,16 +238,28 @@ def cpu_baseline(grid, x, seconds_target=10.0, stride0=16):
         idx = np.arange(0, grid.Nr, stride)
         xs = np.ascontiguousarray(x[:, idx])
         t0 = time.perf_counter()
-        oracle.filter(xs, grid.parity, grid.kind, grid.L, grid.r[idx], grid.dr_min, grid.floor, eps=grid.eps)
+        ref = oracle.filter(xs, grid.parity, grid.kind, grid.L, grid.r[idx], grid.dr_min, grid.floor, eps=grid.eps)
         dt = time.perf_counter() - t0
         total_pts, total_t = xs.size, dt
         sample_shells = xs.shape[0] * xs.shape[1]
         if dt >= seconds_target / 4 or stride == 1:
             break
         stride = max(1, stride // 4)
-    return {"value": total_pts / total_t / 1e9, "unit": "Gpoints/s", "cores": threads, "kind": "oracle",
-            "sample": f"{sample_shells} shells (every {stride}th radial shell of all {grid.nvars} fields), "
-                      f"{total_pts} points in {total_t:.2f} s"}
+    rec = {"value": total_pts / total_t / 1e9, "unit": "Gpoints/s", "cores": threads, "kind": "oracle",
+           "sample": f"{sample_shells} shells (every {stride}th radial shell of all {grid.nvars} fields), "
+                     f"{total_pts} points in {total_t:.2f} s"}
+    return rec, idx, ref
+
+
+def sample_error(y, idx, ref) -> float:
+    """Largest per-field normalised max-norm error of the device result y (torch, [nvars][Nr][..])
+    on the sampled radial shells idx against the oracle's output ref on them."""
+    ys = y[:, idx].cpu().numpy()
+    err = 0.0
+    for v in range(ref.shape[0]):
+        den = max(float(np.abs(ref[v]).max()), 1e-300)
+        err = max(err, float(np.abs(ys[v] - ref[v]).max()) / den)
+    return err
 
 
 def run_reference(args):
@@ -408,13 +442,106 @@ def run_constraints(args):
     return 0
 
 
+PRECISIONS = ("f64", "f32x2", "tc")
+DTYPE_NAME = {"f64": "f64", "f32x2": "f32x2", "tc": "bf16x_split"}
+
+
+def roofline_for(precision, g, avg_kernel_s, points, peaks, src, traffic, label):
+    """Roofline object of one application: the FP64 pipe for the FP64 form, the FP32 instruction rate
+    (through the compensated arithmetic's FP32 instructions per flop) for the FP32-pair form, the bf16
+    tensor pipe for the split-precision form."""
+    flops = algorithmic_flops(g)
+    tflops = flops / avg_kernel_s / 1e12
+    if precision == "f64":
+        return {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": tflops / FP64_PEAK_TFLOPS, "traffic": traffic, "peak_source": FP64_PEAK_SOURCE,
+                "kernel": label, "flops_per_launch": flops}
+    if precision == "f32x2":
+        return {"bound": "alu", "achieved": tflops, "peak": DF_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": tflops / DF_PEAK_TFLOPS, "traffic": traffic, "peak_source": DF_PEAK_SOURCE,
+                "kernel": label, "flops_per_launch": flops}
+    tc_flops = tc_tensor_flops(g)
+    tc_tflops = tc_flops / avg_kernel_s / 1e12
+    peak = peaks["bf16_tflops"]
+    return {"bound": "tensor", "achieved": tc_tflops, "peak": peak, "unit": "TFLOP/s", "frac": tc_tflops / peak,
+            "traffic": traffic, "peak_source": f"bf16_tflops (burst) of {src}", "kernel": label,
+            "flops_per_launch": tc_flops}
+
+
+def time_plan(plan, x, y, steps, warmup, stream):
+    """W untimed applications, then K timed ones with one event pair per application on the
+    launching stream. Returns (total ms, per-application ms list, kernel launches in the timed
+    region)."""
+    import torch
+    for _ in range(warmup):
+        plan.apply(x, out=y)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    launched0 = plan.launch_count
+    t_start.record(stream)
+    for k in range(steps):
+        evs[k][0].record(stream)
+        plan.apply(x, out=y)
+        evs[k][1].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    return t_start.elapsed_time(t_end), [a.elapsed_time(b) for a, b in evs], plan.launch_count - launched0
+
+
+def host_copy_ceiling(x_host, stream_a, stream_b, reps=3):
+    """Measured host<->device copy rates for the state's bytes (pinned host memory): host to device
+    alone, device to host alone, and both directions at once on two streams (the bound of an
+    end-to-end step that moves the state in and the result out). GB/s, best of `reps`."""
+    import torch
+    dev = torch.empty_like(x_host, device="cuda")
+    dev2 = torch.empty_like(x_host, device="cuda")
+    back = torch.empty_like(x_host).pin_memory()
+    nbytes = x_host.numel() * x_host.element_size()
+
+    def best(fn):
+        ms = []
+        for _ in range(reps + 1):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream_a)
+            fn()
+            stream_a.wait_stream(stream_b)
+            e1.record(stream_a)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return min(ms[1:])
+
+    def h2d():
+        with torch.cuda.stream(stream_a):
+            dev.copy_(x_host, non_blocking=True)
+
+    def d2h():
+        with torch.cuda.stream(stream_a):
+            back.copy_(dev2, non_blocking=True)
+
+    def both():
+        stream_b.wait_stream(stream_a)
+        with torch.cuda.stream(stream_a):
+            dev.copy_(x_host, non_blocking=True)
+        with torch.cuda.stream(stream_b):
+            back.copy_(dev2, non_blocking=True)
+
+    t_h2d, t_d2h, t_both = best(h2d), best(d2h), best(both)
+    return {"bytes_each_way": nbytes, "h2d_gbs": nbytes / t_h2d / 1e6, "d2h_gbs": nbytes / t_d2h / 1e6,
+            "both_ways_ms": t_both, "both_ways_gbs_each": nbytes / t_both / 1e6}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="f32x2", choices=["f64", "f32x2", "tc"])
+    ap.add_argument("--precision", default="f64", choices=list(PRECISIONS),
+                    help="arithmetic of the headline line (FP64 by default); the others are timed as variants")
+    ap.add_argument("--no-variants", action="store_true", help="time the headline precision only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="state28_128x64x128",
                     choices=["state28_128x64x128", "state28_256x128x256", "batch6_uneven", "chain8_128x64x128",
@@ -443,14 +570,20 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    prec = {"f64": SPH_PREC_F64, "f32x2": SPH_PREC_F32X2, "tc": SPH_PREC_SPLIT_TC}[args.precision]
+    prec_code = {"f64": SPH_PREC_F64, "f32x2": SPH_PREC_F32X2, "tc": SPH_PREC_SPLIT_TC}
 
     wl = single_grid_workload(args.workload)
     g = wl.grids[0]
+    if W.HYBRID in g.kind:
+        variants = [p for p in ("f64", "f32x2") if p != args.precision]  # no hybrid tensor-core form
+    else:
+        variants = [p for p in PRECISIONS if p != args.precision]
+    if args.no_variants or world > 1:
+        variants = []
     x_host = torch.from_numpy(wl.state()).pin_memory()
     x = x_host.cuda()
     y = x if args.inplace else torch.empty_like(x)
-    plan = Plan.from_grid(g, precision=prec)
+    plan = Plan.from_grid(g, precision=prec_code[args.precision])
     if args.autotune:
         plan.autotune(x, y)
     stream = torch.cuda.current_stream()
@@ -460,35 +593,19 @@ def main():
             dist.barrier()
 
     clk = ClockSampler(local).__enter__()
-    time.sleep(0.5)  # let nvidia-smi start sampling before the timed region
+    time.sleep(0.5)  # let nvidia-smi start sampling before the warm-up
     for _ in range(args.warmup):
         plan.apply(x, out=y)
     torch.cuda.synchronize()
-
-    # device-resident timing: one event pair per launch on the launching stream
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier()
     torch.cuda.synchronize()
-    launched0 = plan.launch_count
     wall0 = time.time()
-    if True:
-        t_start = torch.cuda.Event(enable_timing=True)
-        t_end = torch.cuda.Event(enable_timing=True)
-        t_start.record(stream)
-        for k in range(args.steps):
-            evs[k][0].record(stream)
-            plan.apply(x, out=y)
-            evs[k][1].record(stream)
-        t_end.record(stream)
-        torch.cuda.synchronize()
-        barrier()
+    elapsed_ms, kernel_ms, launched = time_plan(plan, x, y, args.steps, 0, stream)
+    barrier()
     wall1 = time.time()
-    launched = plan.launch_count - launched0
     clk.mark(wall0, wall1)
-    clk.__exit__(None, None, None)
-    elapsed_ms = t_start.elapsed_time(t_end)
-    kernel_ms = [a.elapsed_time(b) for a, b in evs]
     assert plan.sync_status() == 0
+    y_primary = y.clone() if (world == 1 and not args.no_cpu_baseline and not args.inplace) else None
 
     # end to end through the host-buffer entry point
     out_host = torch.empty_like(x_host).pin_memory()
@@ -504,6 +621,23 @@ def main():
     torch.cuda.synchronize()
     barrier()
     e2e_ms = e0.elapsed_time(e1)
+    copies = host_copy_ceiling(x_host, stream, torch.cuda.Stream()) if rank == 0 else None
+
+    # the other precisions on the same state, for the same line (rank 0 alone, N = 1)
+    var_runs = {}
+    for p in variants:
+        vplan = Plan.from_grid(g, precision=prec_code[p])
+        vy = x.clone() if args.inplace else torch.empty_like(x)
+        xin = vy if args.inplace else x
+        v_elapsed, v_kernel_ms, v_launched = time_plan(vplan, xin, vy, args.steps, args.warmup, stream)
+        assert vplan.sync_status() == 0
+        if args.inplace:  # the timed applications filtered in place repeatedly: recompute once for the error
+            vy.copy_(x)
+            vplan.apply(vy, out=vy)
+            torch.cuda.synchronize()
+        var_runs[p] = (vplan, vy, v_elapsed, v_kernel_ms, v_launched)
+    wall_end = time.time()
+    clk.__exit__(None, None, None)
 
     points = g.points
     (elapsed_ms, e2e_ms), (rate, e2e_rate) = combine_ranks([elapsed_ms, e2e_ms], points, args.steps, device="cuda")
@@ -511,55 +645,41 @@ def main():
     e2e_value = e2e_rate / 1e9
     if rank == 0:
         peaks, src = measured_peaks()
-        avg_kernel_s = statistics.mean(kernel_ms) * 1e-3
-        bytes_per_launch = 16.0 * points
-        hbm_gbs = bytes_per_launch / avg_kernel_s / 1e9
-        flops = algorithmic_flops(g)
-        tflops = flops / avg_kernel_s / 1e12
-        traffic = None
+        traffic_rec = {}
         tp = os.path.join(ROOT, "profiles", "traffic.json")
         if os.path.exists(tp):
             with open(tp) as f:
-                rec = json.load(f)
-            fam = "tc" if args.precision == "tc" else "plain"
-            frec = rec.get("families", {}).get(fam, {})
+                traffic_rec = json.load(f)
+
+        def traffic_for(p):
+            fam = "tc" if p == "tc" else "plain"
+            frec = traffic_rec.get("families", {}).get(fam, {})
             if frec.get("sources_sha256_16") == kernel_sources_hash(fam):
-                traffic = frec.get(f"{args.precision}:{wl.name}")
-        def split_label(p):
-            if plan.launches < 3:
-                return f"shell_kernel<{p}>"
-            return (f"one application: shell_kernel<{p}> over the shells with a theta pass, units_kernel<{p}> "
+                return frec.get(f"{p}:{wl.name}")
+            return None
+
+        def label_for(p, pl):
+            if p == "tc":
+                return "tc kernels of one application (theta and phi passes, copies of identity shells)"
+            name = {"f64": "F64", "f32x2": "DF"}[p]
+            if pl.launches < 3:
+                return f"shell_kernel<{name}>"
+            return (f"one application: shell_kernel<{name}> over the shells with a theta pass, units_kernel<{name}> "
                     "over the active ring pairs of the others" + ("" if args.inplace else ", copy_shells_kernel"))
 
-        if args.precision == "f64":
-            roof = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
-                    "peak_source": "FP64 FMA: 152 SMs x 2/clk x 2 flop x 2.07 GHz (recipe's 1.25 TFLOP/s)",
-                    "kernel": split_label("F64"), "flops_per_launch": flops}
-        elif args.precision == "f32x2":
-            roof = {"bound": "alu", "achieved": tflops, "peak": DF_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": tflops / DF_PEAK_TFLOPS, "traffic": traffic,
-                    "peak_source": "FP64-equivalent rate of compensated FP32 pairs: 152 SMs x 128 FP32 lanes x "
-                                   "2.07 GHz / 8.8 FP32 instructions per FP64-equivalent flop",
-                    "kernel": split_label("DF"), "flops_per_launch": flops}
-        else:
-            tc_flops = tc_tensor_flops(g)
-            tc_tflops = tc_flops / avg_kernel_s / 1e12
-            peak = peaks["bf16_tflops"]
-            roof = {"bound": "tensor", "achieved": tc_tflops, "peak": peak, "unit": "TFLOP/s",
-                    "frac": tc_tflops / peak, "traffic": traffic,
-                    "peak_source": f"bf16_tflops (burst) of {src}",
-                    "kernel": "tc_pass_kernel (theta and phi launches of one application, with the copies "
-                              "of identity shells)",
-                    "flops_per_launch": tc_flops}
+        avg_kernel_s = statistics.mean(kernel_ms) * 1e-3
+        hbm_gbs = 16.0 * points / avg_kernel_s / 1e9
+        roof = roofline_for(args.precision, g, avg_kernel_s, points, peaks, src, traffic_for(args.precision),
+                            label_for(args.precision, plan))
         if W.HYBRID in g.kind:
             roof["flops_note"] = ("hybrid fields counted as exponential ones: a lower bound (the rings and "
                                   "circles where the detector fires are transformed too)")
+        ceiling = points / (copies["both_ways_ms"] * 1e-3) / 1e9
         line = {
             "metric": "filtered Gpoints/s (theta+phi double FFT filter, FP64 I/O)",
             "value": value, "unit": "Gpoints/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"f64": "f64", "f32x2": "f32x2", "tc": "bf16x_split"}[args.precision],
+            "vs_baseline": None, "dtype": DTYPE_NAME[args.precision],
             "data": "synthetic",
             "config": {"workload": wl.name, "Nr": g.Nr, "Ntheta": g.Ntheta, "Nphi": g.Nphi, "nvars": g.nvars,
                        "precision": args.precision,
@@ -570,12 +690,33 @@ def main():
                     "peak_source": src, "bytes_per_point": 16},
             "roofline": roof,
             "e2e": {"value": e2e_value, "unit": "Gpoints/s", "h2d_bytes_per_step": 8 * points,
-                    "d2h_bytes_per_step": 8 * points},
+                    "d2h_bytes_per_step": 8 * points, "host_copies": copies,
+                    "copy_ceiling_gpoints": ceiling, "frac_of_copy_ceiling": e2e_value / ceiling},
             "gpu_launches": launched,
             "clocks": clk.summary(),
         }
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(g, x_host.numpy(), stride0=16 if g.Nr <= 128 else 64)
+            cpu, idx, ref = cpu_baseline(g, x_host.numpy(), stride0=16 if g.Nr <= 128 else 64)
+            line["cpu_baseline"] = cpu
+            if y_primary is not None:
+                line["max_err_vs_oracle"] = sample_error(y_primary, idx, ref)
+        else:
+            idx = ref = None
+        if var_runs:
+            line["variants"] = {}
+            for p, (vplan, vy, v_elapsed, v_kernel_ms, v_launched) in var_runs.items():
+                v_avg = statistics.mean(v_kernel_ms) * 1e-3
+                v_gbs = 16.0 * points / v_avg / 1e9
+                line["variants"][p] = {
+                    "value": points * args.steps / (v_elapsed * 1e-3) / 1e9, "unit": "Gpoints/s",
+                    "ms_per_step": v_elapsed / args.steps, "dtype": DTYPE_NAME[p],
+                    "hbm_frac": v_gbs / peaks["hbm_gbs"],
+                    "roofline": roofline_for(p, g, v_avg, points, peaks, src, traffic_for(p), label_for(p, vplan)),
+                    "max_err_vs_oracle": sample_error(vy, idx, ref) if ref is not None else None,
+                    "err_sample": cpu["sample"] if ref is not None else None,
+                    "gpu_launches": v_launched,
+                    "clocks": clk.summary((wall1, wall_end)),
+                }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
