@@ -13,8 +13,9 @@
  *  - A state is `nvars * Nr * Ntheta * Nphi` contiguous values in the layout
  *    [var][shell i][theta index j][phi index k], k fastest. theta_j = (j + 1/2) pi / Ntheta
  *    (cell centred), phi_k = 2 pi k / Nphi. Nphi must be even (the phi + pi pairing).
- *  - Device pointers are caller-owned CUDA device memory on the plan's device. `in == out`
- *    (in place) is allowed; any other overlap is rejected with SPH_EALIAS.
+ *  - Device pointers are caller-owned CUDA device memory on the plan's device (memory of another
+ *    device is rejected with SPH_EINVAL). `in == out` (in place) is allowed; any other overlap is
+ *    rejected with SPH_EALIAS.
  *  - Calls are asynchronous on `stream` (NULL = the legacy default stream) and return after
  *    enqueueing. Argument errors are returned immediately and nothing is enqueued. Errors a
  *    kernel detects on the device are latched in the plan and reported by
@@ -153,16 +154,20 @@ sph_status sph_filter_apply_host(sph_filter_plan plan, const double* host_in, do
                                  sph_stream_t stream);
 
 /* Same as sph_filter_apply_host, but allocates no device memory: the device copies of the input
- * and the output live in a fixed array inside the library (32 MiB on every GPU that loads it,
- * held until the process exits). The paper has no counterpart; this is for callers that cannot
+ * and the output live in a fixed array inside the library (32 MiB on every GPU where this call has
+ * run, held until the process exits). The paper has no counterpart; this is for callers that cannot
  * let a library allocate device memory, e.g. a framework whose own allocator has reserved the
  * whole device at start-up, or code that must not risk the device synchronisation that
  * cudaMalloc/cudaFree may cause. No cudaMalloc, cudaFree or allocating library routine is called.
  * Limits and behaviour:
  *  - The state may have at most 2,097,152 points (nvars * Nr * Ntheta * Nphi); larger states are
  *    rejected with SPH_EINVAL before anything is enqueued.
- *  - The first call on a device looks up the array's device address on that device (a one-time
- *    set-up); make that first call before any stream capture.
+ *  - The array's device memory is committed on a device by the first call there (the code holding
+ *    the array is loaded lazily, at that call), and that first call may synchronise the device.
+ *    A caller whose allocator reserves the whole device should make one call (a small plan will
+ *    do) before reserving it, and every caller should make the first call before any stream
+ *    capture. Each call looks up the array's address on the current device again, so a
+ *    cudaDeviceReset between calls does not leave a stale address.
  *  - Every call uses the same array, and nothing in it needs to start at zero (each call overwrites
  *    what it reads). Calls whose work overlaps on the GPU (e.g. on two streams) race on the array;
  *    order them on one stream or synchronise between them.
@@ -206,7 +211,8 @@ long long sph_filter_plan_launch_count(sph_filter_plan plan);
  *  - theta_filtered: device array of Nr bytes, nonzero for the shells where the theta filter is
  *    active (e.g. l_max < Ntheta for the metric fields' filter), or NULL for none (standard form
  *    everywhere). alpha_bh: the lapse threshold of the modified form (0.3 in the paper).
- * Returns SPH_EINVAL for a NULL or host state, bad sizes, indices out of range or repeated, or a
+ * Returns SPH_EINVAL for a NULL or host state, a state or flag array on a device other than the
+ * current one, bad sizes, indices out of range or repeated, or a
  * non-finite alpha_bh (nothing is enqueued); SPH_ECUDA if the launch fails. Asynchronous on
  * `stream`. A point whose det(m) is not positive gives non-finite values (no physical metric). */
 sph_status sph_enforce_constraints(double* state, int nvars, int Nr, int Ntheta, int Nphi, const int* h_vars,

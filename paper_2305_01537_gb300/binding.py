@@ -129,6 +129,8 @@ class Plan:
         _check(lib.sph_filter_plan_create(ctypes.byref(h), self.Nr, self.Ntheta, self.Nphi, self.nvars,
                                           self._parity.ctypes.data, ctypes.byref(prm)), "sph_filter_plan_create")
         self._h = h
+        import torch
+        self.device = torch.cuda.current_device()  # the device sph_filter_plan_create bound the plan to
         self.precision = int(precision)
 
     @classmethod
@@ -169,10 +171,14 @@ class Plan:
         import torch
         if not (x.is_cuda and x.dtype == dtype and x.is_contiguous() and tuple(x.shape) == self.shape):
             raise ValueError(f"expected a contiguous CUDA {dtype} tensor of shape {self.shape}")
+        if x.device.index != self.device:
+            raise ValueError(f"the tensor is on cuda:{x.device.index}, the plan on cuda:{self.device}")
         if out is None:
-            out = torch.empty_like(x)
-        elif not (out.is_cuda and out.dtype == dtype and out.is_contiguous() and tuple(out.shape) == self.shape):
-            raise ValueError("out must match the input")
+            with torch.cuda.device(self.device):
+                out = torch.empty_like(x)
+        elif not (out.is_cuda and out.dtype == dtype and out.is_contiguous() and tuple(out.shape) == self.shape
+                  and out.device.index == self.device):
+            raise ValueError("out must match the input (shape, dtype, layout and device)")
         return out
 
     def _call(self, fname, x, out, stream, aux=None):
@@ -180,11 +186,12 @@ class Plan:
         dtype = torch.float32 if fname.endswith("_f32") else torch.float64
         out = self._io(x, out, dtype)
         fn = getattr(load(), fname)
-        if aux is None:
-            st = fn(self._h, x.data_ptr(), out.data_ptr(), _stream_handle(stream))
-        else:
-            self._io(aux, aux, dtype)
-            st = fn(self._h, x.data_ptr(), aux.data_ptr(), out.data_ptr(), _stream_handle(stream))
+        with torch.cuda.device(self.device):
+            if aux is None:
+                st = fn(self._h, x.data_ptr(), out.data_ptr(), _stream_handle(stream))
+            else:
+                self._io(aux, aux, dtype)
+                st = fn(self._h, x.data_ptr(), aux.data_ptr(), out.data_ptr(), _stream_handle(stream))
         _check(st, fname)
         return out
 
@@ -297,8 +304,13 @@ def enforce_constraints(state, h_vars: Sequence[int], a_vars: Sequence[int], alp
                 or not theta_filtered.is_contiguous():
             raise ValueError("theta_filtered must be a contiguous CUDA byte tensor of Nr flags")
         flags = theta_filtered.data_ptr()
+    if theta_filtered is not None and theta_filtered.device != state.device:
+        raise ValueError("theta_filtered must be on the state's device")
     hv = (ctypes.c_int * 6)(*[int(k) for k in h_vars])
     av = (ctypes.c_int * 6)(*[int(k) for k in a_vars])
-    _check(load().sph_enforce_constraints(state.data_ptr(), nvars, Nr, Nth, Nph, hv, av, int(alpha_var), flags,
-                                          float(alpha_bh), _stream_handle(stream)), "sph_enforce_constraints")
+    with torch.cuda.device(state.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(state.device)
+        _check(load().sph_enforce_constraints(state.data_ptr(), nvars, Nr, Nth, Nph, hv, av, int(alpha_var), flags,
+                                              float(alpha_bh), _stream_handle(stream)), "sph_enforce_constraints")
     return state

@@ -334,10 +334,22 @@ void free_plan(sph_filter_plan_s* p) {
   delete p;
 }
 
+// True if ptr is device memory of a GPU other than `device` (the kernels run on the plan's device and
+// would otherwise read or write a peer's memory).
+bool on_other_device(const void* ptr, int device) {
+  cudaPointerAttributes attr{};
+  if (cudaPointerGetAttributes(&attr, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return attr.type == cudaMemoryTypeDevice && attr.device != device;
+}
+
 sph_status check_io(const sph_filter_plan_s* p, const void* in, const void* out, size_t elem) {
   if (!p || !in || !out) return SPH_EINVAL;
   const size_t bytes = elem * (size_t)p->nvars * p->Nr * p->Nth * p->Nph;
   if (overlaps_partially(in, out, bytes)) return SPH_EALIAS;
+  if (on_other_device(in, p->device) || on_other_device(out, p->device)) return SPH_EINVAL;
   return SPH_OK;
 }
 

@@ -93,16 +93,20 @@ extern "C" sph_status sph_enforce_constraints(double* state, int nvars, int Nr, 
       if (idx[k] == idx[n]) return SPH_EINVAL;  // the 13 fields must be distinct
   }
   const long long shell_points = (long long)Ntheta * Nphi, plane = (long long)Nr * shell_points;
-  cudaPointerAttributes attr{};
-  if (cudaPointerGetAttributes(&attr, state) != cudaSuccess) return SPH_ECUDA;
-  if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) return SPH_EINVAL;
-  if (theta_filtered) {
-    if (cudaPointerGetAttributes(&attr, theta_filtered) != cudaSuccess) return SPH_ECUDA;
-    if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) return SPH_EINVAL;
-  }
+  // both arrays must live on the current device: the kernel runs there and would otherwise touch
+  // another GPU's memory
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return SPH_ECUDA;
+  cudaPointerAttributes attr{};
+  if (cudaPointerGetAttributes(&attr, state) != cudaSuccess) return SPH_ECUDA;
+  if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) return SPH_EINVAL;
+  if (attr.type == cudaMemoryTypeDevice && attr.device != dev) return SPH_EINVAL;
+  if (theta_filtered) {
+    if (cudaPointerGetAttributes(&attr, theta_filtered) != cudaSuccess) return SPH_ECUDA;
+    if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) return SPH_EINVAL;
+    if (attr.type == cudaMemoryTypeDevice && attr.device != dev) return SPH_EINVAL;
+  }
   const long long want = (plane + 255) / 256, cap = 8LL * sms;
   const unsigned grid = (unsigned)(want < cap ? want : cap);
   constraint_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(state, v, theta_filtered, plane, shell_points, alpha_bh);

@@ -6,11 +6,13 @@
 // (and a late allocation would fail or fragment its pool); code that must not synchronise the
 // device at that point cannot afford cudaMalloc/cudaFree either, since they may synchronise.
 //
-// The array is a file-scope __device__ variable of 32 MiB, so every GPU that loads this library
-// holds it until the process exits. Host code cannot use the variable's name as a device address;
-// the address is obtained once per device with cudaGetSymbolAddress.
+// The array is a file-scope __device__ variable of 32 MiB. With lazy module loading (the CUDA
+// default), a device gets that memory when this file's module is first loaded there, which is the
+// first call of this entry point on that device (the first cudaGetSymbolAddress below); it is then
+// held until the process exits. Host code cannot use the variable's name as a device address; the
+// address is looked up with cudaGetSymbolAddress, on every call (cheap once the module is loaded), so
+// that a cudaDeviceReset between calls cannot leave a stale address behind.
 #include <cstdint>
-#include <mutex>
 
 #include "internal.h"
 
@@ -21,20 +23,11 @@ constexpr long long kNoAllocMaxPoints = 1LL << 21;  // 2,097,152 points = 16 MiB
 
 static __device__ __align__(256) double g_noalloc_stage[2 * kNoAllocMaxPoints];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-double* g_stage_ptr[kMaxDevices] = {};
-
-// Device address of the staging array on `device` (which must be current); set up on first use.
-sph_status stage_address(int device, double** out) {
-  if (device < 0 || device >= kMaxDevices) return SPH_EUNSUPPORTED;
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_stage_ptr[device]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_stage) != cudaSuccess || !p) return SPH_ECUDA;
-    g_stage_ptr[device] = static_cast<double*>(p);
-  }
-  *out = g_stage_ptr[device];
+// Device address of the staging array on the current device.
+sph_status stage_address(double** out) {
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_stage) != cudaSuccess || !p) return SPH_ECUDA;
+  *out = static_cast<double*>(p);
   return SPH_OK;
 }
 
@@ -49,7 +42,7 @@ extern "C" sph_status sph_filter_apply_host_noalloc(sph_filter_plan plan, const 
   if (cudaGetDevice(&cur) != cudaSuccess) return SPH_ECUDA;
   if (cur != plan->device && cudaSetDevice(plan->device) != cudaSuccess) return SPH_ECUDA;
   double* stage = nullptr;
-  sph_status st = stage_address(plan->device, &stage);
+  sph_status st = stage_address(&stage);
   if (st == SPH_OK) {
     double* d_in = stage;
     double* d_out = stage + kNoAllocMaxPoints;
