@@ -324,7 +324,6 @@ void free_plan(sph_filter_plan_s* p) {
   if (p->ev_copy) cudaEventDestroy(p->ev_copy);
   if (p->ev_join) cudaEventDestroy(p->ev_join);
   tc_free(p);
-  if (p->tc_ev) cudaEventDestroy(p->tc_ev);
   cudaFree(p->d_stage_in);
   cudaFree(p->d_stage_out);
   for (cudaStream_t s : p->pipe)
@@ -384,21 +383,11 @@ sph_status launch_plan_vars(sph_filter_plan_s* p, const void* in, const void* au
       if (cur != p->device) cudaSetDevice(cur);
       return SPH_EUNSUPPORTED;
     }
-    // one launch with the main scratch set at a time, whatever the stream; a stream being captured
-    // into a graph orders its own work and is not chained, nor are the pipeline's own sets
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    cudaError_t e = cudaStreamIsCapturing((cudaStream_t)stream, &cap);
-    std::lock_guard<std::mutex> lock(p->tc_mu);
-    const bool chain = e == cudaSuccess && cap == cudaStreamCaptureStatusNone && tc_set == 0;
-    if (e == cudaSuccess && chain && p->tc_ev_recorded) e = cudaStreamWaitEvent((cudaStream_t)stream, p->tc_ev, 0);
-    if (e == cudaSuccess)
-      e = tc_launch(p, static_cast<const double*>(in), static_cast<double*>(out), transpose, var_begin, var_count,
-                    (cudaStream_t)stream, tc_set);
-    if (e == cudaSuccess) p->launched += p->launches;
-    if (e == cudaSuccess && chain) {
-      e = cudaEventRecord(p->tc_ev, (cudaStream_t)stream);
-      p->tc_ev_recorded = e == cudaSuccess;
-    }
+    // the form keeps no state between launches, so calls on any streams may overlap
+    int nl = 0;
+    const cudaError_t e = tc_launch(p, static_cast<const double*>(in), static_cast<double*>(out), transpose, var_begin,
+                                    var_count, (cudaStream_t)stream, tc_set, &nl);
+    if (e == cudaSuccess) p->launched += nl;
     if (cur != p->device) cudaSetDevice(cur);
     return e == cudaSuccess ? SPH_OK : SPH_ECUDA;
   }
@@ -575,7 +564,6 @@ sph_status sph_filter_plan_create(sph_filter_plan* out, int Nr, int Ntheta, int 
   }
   if (p->precision == SPH_PREC_SPLIT_TC) {
     st = tc_setup(p);
-    if (st == SPH_OK && cudaEventCreateWithFlags(&p->tc_ev, cudaEventDisableTiming) != cudaSuccess) st = SPH_ECUDA;
     if (st != SPH_OK) {
       free_plan(p);
       return st;

@@ -234,14 +234,8 @@ struct sph_filter_plan_s {
   double2* d_tw_ph = nullptr;
   unsigned* d_status = nullptr;
 
-  // split-precision tensor-core form (SPH_PREC_SPLIT_TC). Its kernels keep per-CTA scratch in the
-  // plan's global memory, so launches of one plan on different streams with the main scratch set are
-  // chained: each waits for tc_ev, recorded after the previous one (under tc_mu). The host-buffer
-  // pipeline's streams have scratch sets of their own.
+  // split-precision tensor-core form (SPH_PREC_SPLIT_TC)
   sph::TcPlan* tc = nullptr;
-  std::mutex tc_mu;
-  cudaEvent_t tc_ev = nullptr;
-  bool tc_ev_recorded = false;
 
   // staging buffers and pipeline streams of sph_filter_apply_host (created on first use)
   double* d_stage_in = nullptr;
@@ -256,13 +250,14 @@ long double filter_value(int kind, long double al, long double lmax);
 
 // Split-precision tensor-core form (tc.cu): tables at plan creation, release, and one application
 // (theta then phi pass, or the reverse for the transpose) of the fields [var_begin, var_begin +
-// var_count) from in to out (in == out allowed), with per-CTA scratch set `set` (0: the plan's
-// main set; 1..3: the host-buffer pipeline's streams, reserved by tc_reserve_pipeline).
+// var_count) from in to out (in == out allowed). The form keeps no state between launches (its
+// working set lives in each CTA's shared and tensor memory), so calls may overlap on any streams;
+// `set` is unused. *nlaunch (if not null) receives the number of kernels enqueued.
 sph_status tc_setup(sph_filter_plan_s* p);
 void tc_free(sph_filter_plan_s* p);
 sph_status tc_reserve_pipeline(sph_filter_plan_s* p);
 cudaError_t tc_launch(sph_filter_plan_s* p, const double* in, double* out, int transpose, int var_begin,
-                      int var_count, cudaStream_t s, int set);
+                      int var_count, cudaStream_t s, int set, int* nlaunch = nullptr);
 
 // Enqueue one filter application of a plan (validates pointers; see sph_filter_apply).
 sph_status launch_plan(sph_filter_plan_s* p, const void* in, const void* aux, void* out, int map_in, int map_out,

@@ -1,31 +1,32 @@
 // Split-precision tensor-core form of the double FFT filter (SPH_PREC_SPLIT_TC).
 //
-// Each pass of Sec. II.C is a real, symmetric, circulant operator on a vector of length L: a
-// doubled great circle (L = 2 Ntheta, with the field's parity sign across the pole) for the theta
-// pass, a ring (L = Nphi) for the phi pass. Only the removed part H c = c - M c is computed here,
-// with H = F^-1 diag(1 - f) F, and the pass writes c - H c in FP64. The DFT F and its inverse are
-// dense matrices shared by every vector of a length, so they run as tcgen05 GEMMs over 128 vectors
-// at a time; the per-vector multipliers 1 - f(|m|, cutoff) are applied between the two GEMMs.
+// Each pass of Sec. II.C applies to every vector c of length L (a doubled great circle, L =
+// 2 Ntheta, with the field's parity sign across the pole; or a ring, L = Nphi) the symmetric
+// circulant H = F^-1 diag(mu) F that removes the filtered part of each Fourier mode (mu_m = 1 -
+// f(|m|, cutoff)), and writes c - H c. Only H c is computed from low-precision products, and the
+// subtraction from the field is exact fixed-point arithmetic on 56-bit integers.
 //
-// Real DFT split (exact algebra, no approximation): with H = L/2, u_q = c_q + c_{L-q}
-// (u_0 = c_0, u_H = c_H) and v_q = c_q - c_{L-q},
-//   X_c[m] = sum_{q=0}^{H} u_q cos(2 pi m q / L),            m = 0 .. H
-//   X_s[m] = sum_{q=1}^{H-1} v_q sin(2 pi m q / L),          m = 1 .. H-1
-//   y_e[k] = (1/L) sum_{m=0}^{H} w_m h_m X_c[m] cos(2 pi m k / L),  w_0 = w_H = 1, else 2
-//   y_o[k] = (2/L) sum_{m=1}^{H-1} h_m X_s[m] sin(2 pi m k / L)
-//   (H c)_k = y_e[k] + y_o[k],  (H c)_{L-k} = y_e[k] - y_o[k].
-// Four GEMMs (CF, SF, CI, SI) with at most H outputs each; the Nyquist terms X_c[H] and y_e[H]
-// (alternating sums) are summed exactly in 64-bit integers on the CUDA cores.
-//
-// Exact products from BF16 (Ozaki-style splitting): every operand value v, scaled by a power of two
-// so that |v| <= 1/2, is written as six balanced base-256 digits, v = sum_a d_a 256^-(a+1) with
-// |d_a| <= 128, each slice d_a 256^-(a+1) exact in BF16. A slice-pair product is exact. The tensor
-// core adds the products of one MMA and the accumulator after aligning them to the largest one and
-// truncating, so the sums are exact only while every addend is an integer in the accumulator's
-// unit and the total stays below 2^24 units: each diagonal a + b = t (t = 0..5, all pairs of one
-// scale, at most 6 x 129 x 2^14 < 2^24 units for K <= 160) therefore has an accumulator of its
-// own. Pairs with a + b >= 6 are dropped (2^-48 of the result). The six accumulators are summed in
-// compensated FP32 pairs, then converted to FP64 with integer operations.
+// One CTA filters 64 vectors of one length at a time (a tile), persistent over the pass's tiles:
+//  1. load: the vectors are read from HBM into a shared-memory store of 64-bit fixed-point
+//     integers (each vector on its own power-of-two scale);
+//  2. symmetry split (tc_plan.cu): in-place sum/difference stages turn each vector into the
+//     coordinates of its symmetry blocks; each level's two halves share one operator, so they fill
+//     the 128 rows of one GEMM (64 vectors x 2 halves);
+//  3. per block GEMM pair: the coordinates of the 128 rows, brought to 46 bits by a per-row shift,
+//     are written as six balanced base-256 digits (each exact in BF16) into tensor memory, the A
+//     operand of tcgen05.mma (kind::f16); the block's orthonormal mode basis U, as six digit slices,
+//     is the B operand, copied to shared memory by the bulk-copy engine. The 21 digit pairs with
+//     a + b <= 5 are multiplied; each diagonal a + b = t sums integers of one scale, exactly (< 2^22
+//     units) in its own FP32 accumulator (t = 0 .. 3); the two smallest (4 and 5) share one, the
+//     diagonal-5 sum scaled by 2^-8 by the MMA's input scaling when diagonal 4 starts. The five
+//     accumulators are combined into a 64-bit integer, multiplied by the vector's mu_m (a 62-bit
+//     fixed-point fraction), rescaled per row and sliced again as the A operand of the second GEMM
+//     (U^T). Its result is subtracted from the stored coordinates;
+//  4. the stages are undone in place and the results written back to HBM in FP64.
+// Accuracy: every integer step is exact; the errors are the input's rounding to the store (2^-(F+1)
+// of the vector's largest value), the dropped digit pairs a + b >= 6 and the truncation to 46 bits
+// at the two slicings (about 2^-44 of each row's largest value each), and the rounding of W back to
+// the store's unit.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -34,88 +35,58 @@
 #include <new>
 #include <vector>
 
-#include "df32.h"
 #include "internal.h"
+#include "tc2_host.h"
 
 namespace sph {
 namespace tcx {
 
-constexpr int kM = 128;            // vectors per tile (MMA M)
-constexpr int kKC = 32;            // K values per pipeline chunk (two MMA K-steps of 16)
-constexpr int kS = 6;              // slices per operand
-constexpr int kAcc = 6;            // accumulators: one per diagonal a + b = 0 .. 5
-constexpr int kMaxNPh = 80;        // GEMM N per launch of the K loop (6 x 80 <= 512 TMEM columns)
-constexpr int kMaxL = 256;
-constexpr uint32_t kStageA = kS * kM * kKC * 2;       // 49152 bytes
-constexpr uint32_t kStageB = kS * kMaxNPh * kKC * 2;  // 30720 bytes
-constexpr uint32_t kStage = kStageA + kStageB;        // 79872 bytes (a multiple of 1024)
-constexpr int kThr = 512;          // threads per CTA (4 warps per tensor-memory lane quarter)
-constexpr long long kWaitLimit = 1LL << 20;           // bounded mbarrier polls (seconds at most)
+constexpr long long kWaitLimit = 1LL << 24;  // bounded mbarrier polls (about a second at most)
+constexpr int kMaxChunks = 4;                // 8-value chunks per thread and row in the mid step
 
-enum Op { kCF = 0, kSF = 1, kCI = 2, kSI = 3 };
-
-// Offset (elements) of (row, k) in a ROWS x kKC operand chunk stored K-major without swizzle:
-// 8-row x 8-element core matrices of 128 contiguous bytes; LBO (next core matrix along K) = 128 B,
-// SBO (next group of 8 rows) = (kKC / 8) * 128 B. Rows [8g, 8g + 8) are contiguous.
-__host__ __device__ inline uint32_t kmaj_elem(int row, int k) {
-  return (uint32_t)((row >> 3) * (kKC / 8) * 64 + (k >> 3) * 64 + (row & 7) * 8 + (k & 7));
-}
-
-struct OpTab {
-  const uint16_t* tab;  // [KP / kKC][kS][NP][kKC] BF16 slices, core-matrix layout per (chunk, slice)
-  int N, K;             // valid output and reduction sizes
-  int NPh, nh;          // outputs per pass of the K loop (multiple of 16) and passes; NP = NPh * nh
-  int KP;               // padded K (multiple of kKC)
-};
-
-struct TcArgs {
-  int pass;                 // 0: theta (doubled circles), 1: phi (rings)
-  int L;                    // vector length
-  int Nr, Nth, Nph;
-  const double* src;        // state read by the pass
-  double* dst;              // state written (may equal src); only active vectors are written
-  const int* list;          // theta: active shells v*Nr+i; phi: active rings (v*Nr+i)*Nth+j
-  long long nvec;           // theta: entries * Nph/2; phi: entries
-  const float2* h;          // 1 - f as FP32 pairs: theta [ncls][Nr][Nth+1]; phi [ncls][Nr][Nth][Nph/2+1]
-  const VarInfo* var;
-  OpTab op[4];
-  int Ef, Ei;               // operator scales: forward (CF, SF) = 2^Ef * slices, inverse 2^Ei
-  float2* scratch;          // per CTA: Yc [kM][H+1], Ys [kM][H-1], ye [kM][H+1]
-  uint4* akeep;             // per CTA: the A stages of a GEMM's first output half, [KP / kKC][kStageA / 16]
-  int akeep_chunks;         // chunks per CTA in akeep (0 when no GEMM has two output halves)
-  unsigned* status;
-};
-
-struct Row {
-  size_t base;              // offset of element 0 of the vector in the state
-  const float2* h;          // multipliers of the vector's modes 0 .. H
-  int neg;                  // theta: second half carries the parity sign -1
-  int ex;                   // input scale exponent
-  int ey;                   // spectrum scale exponent
+struct RowInfo {
+  long long base;                  // offset of the vector's element 0 in the state (circle: meridian k)
+  const unsigned long long* mu;    // the vector's multipliers mu_m 2^62, m = 0 .. L/2
+  int neg;                         // theta circles of odd fields: the second meridian carries -1
   int valid;
 };
 
-struct Smem {
-  Row row[kM];
-  int emax[kM];                // biased exponent maxima (FP64 input, FP32 spectrum)
-  unsigned long long nyq[kM];  // exact Nyquist sums (two's complement) of the CF and CI operands
-  unsigned long long bar[2];
+struct TcArgs {
+  int pass;                        // 0: theta (doubled circles), 1: phi (rings)
+  int Nr, Nth, Nph;
+  const double* src;
+  double* dst;                     // may equal src; only the pass's vectors are written
+  const int* list;                 // theta: active shells v*Nr+i; phi: active rings (v*Nr+i)*Nth+j
+  long long nvec;                  // theta: entries * Nph/2; phi: entries
+  const unsigned long long* mu;    // theta: [ncls][Nr][Nth+1]; phi: [ncls][Nr][Nth][Nph/2+1]
+  const VarInfo* var;
+  const unsigned char* ops;        // operator blob (global), layout of PassDesc
+  const int16_t* maps;             // index maps (global)
+  PassDesc d;
+  unsigned* status;
+};
+
+struct Ctl {
+  RowInfo row[kV];
+  int vexp[kV];                    // largest biased FP64 exponent of each vector
+  int rowbl[kM];                   // bit length of the largest |value| of a GEMM row
+  int sh_in[kM], sh_mid[kM];       // per-row shifts of the two slicings
+  unsigned long long op_bar, mma_bar;
   uint32_t tslot;
   int abort;
 };
 
-constexpr uint32_t kSmemBytes = 2 * kStage + ((sizeof(Smem) + 127) / 128) * 128;
-
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
+// Shared-memory matrix descriptor of a K-major operand without swizzle (core matrices of 8 rows x
+// 16 bytes; next along K 128 bytes on; next 8-row group (K/8) 128 bytes on).
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, int K) {
   uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)(128 >> 4) << 16;                 // LBO: next core matrix along K
-  d |= (uint64_t)(((kKC / 8) * 128) >> 4) << 32;   // SBO: next group of 8 rows
-  d |= (uint64_t)1 << 46;                          // descriptor version
-  return d;                                        // base offset 0, no swizzle
+  d |= (uint64_t)(128 >> 4) << 16;
+  d |= (uint64_t)(((K / 8) * 128) >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
 }
-
 // kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both K-major, M = 128.
 __device__ __forceinline__ uint32_t make_idesc(int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
@@ -134,557 +105,621 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   return false;
 }
 
-// v * 2^(48 - E) rounded to an integer (|result| < 2^47 when |v| < 2^(E-1)).
-__device__ __forceinline__ long long fx64(double d, int E) {
-  const long long b = __double_as_longlong(d);
-  const int e = (int)((b >> 52) & 0x7FF);
-  const int sh = 1027 + E - e;
-  if (e == 0 || sh >= 62) return 0;
-  const long long m = (b & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
-  const long long t = sh >= 1 ? ((m >> (sh - 1)) + 1) >> 1 : (1LL << 47) - 1;  // sh < 1 cannot occur for a valid E
-  return b < 0 ? -t : t;
+// Bulk copy (TMA engine) of `bytes` (multiple of 16) from global to shared memory, completing on
+// the mbarrier; issued by one thread after arming the barrier with the byte count.
+__device__ __forceinline__ void bulk_load(void* sdst, const void* gsrc, uint32_t bytes, uint32_t bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+  const char* g = static_cast<const char*>(gsrc);
+  uint32_t s = su32(sdst);
+  for (uint32_t off = 0; off < bytes; off += 16384) {
+    const uint32_t n = bytes - off < 16384 ? bytes - off : 16384;
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(s + off),
+        "l"(g + off), "r"(n), "r"(bar)
+        : "memory");
+  }
 }
-__device__ __forceinline__ long long fx32(float f, int E) {
-  const int b = __float_as_int(f);
-  const int e = (b >> 23) & 0xFF;
-  const int sh = 102 + E - e;
-  if (e == 0 || sh >= 40) return 0;
-  const long long m = (long long)((b & 0x7FFFFF) | 0x800000);
-  const long long t = sh >= 1 ? ((m >> (sh - 1)) + 1) >> 1 : (sh > -24 ? (m << (-sh)) : (1LL << 47) - 1);
+
+// round(x 2^(F - ex)) of the FP64 bit pattern b for |x| < 2^ex, with base = 1075 - F + ex
+// (zero and subnormal inputs give 0).
+__device__ __forceinline__ long long to_fixed(long long b, int base) {
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e == 0) return 0;
+  const long long m = (b & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+  const int sh = base - e;
+  long long t;
+  if (sh <= 0) t = m << (-sh);  // -sh <= 3 since |x| < 2^ex and F <= 56
+  else if (sh >= 62) t = 0;
+  else t = ((m >> (sh - 1)) + 1) >> 1;
   return b < 0 ? -t : t;
 }
 
-// Six BF16 slices of eight fixed-point values: slice a holds d_a 256^-(a+1), the balanced digits
-// of t 2^-48 (t + 0x808080808080 has base-256 digits d_a + 128; the top one is not masked, so it
-// may be 256 when |t| approaches 2^47). Each slice value is built exactly from its byte: the float
-// with exponent field 150 - 8(a+1) and the byte as low mantissa bits is (2^23 + byte) 2^-8(a+1).
-__device__ __forceinline__ void slice8(const long long t[8], uint4 out[kS]) {
-  uint32_t w[kS][4];
+// v 2^expo as FP64 (round half away from zero on the dropped bits; 0 on underflow).
+__device__ __forceinline__ double from_fixed(long long v, int expo) {
+  if (v == 0) return 0.0;
+  const unsigned long long sgn = v < 0 ? 0x8000000000000000ULL : 0ULL;
+  unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+  const int lz = __clzll((long long)a);
+  a <<= lz;
+  unsigned long long r = (a >> 11) + ((a >> 10) & 1ULL);
+  int be = 63 - lz + expo + 1023;
+  if (r >> 53) {
+    r >>= 1;
+    ++be;
+  }
+  if (be <= 0) return __longlong_as_double((long long)sgn);
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) | (r & 0xFFFFFFFFFFFFFULL)));
+}
+
+// Exact FP32 integer (|f| < 2^22) to int; a fractional f is rounded to nearest.
+__device__ __forceinline__ int f2i(float f) { return __float_as_int(__fadd_rn(f, 12582912.0f)) - 0x4B400000; }
+
+// The GEMM result from the five accumulators: sum_t acc_t 2^(80 - 8t - Pb), acc 4 holding diagonal 4
+// plus diagonal 5 / 256.
+__device__ __forceinline__ long long combine5(float a0, float a1, float a2, float a3, float a4, int Pb) {
+  const long long hi = (long long)(f2i(a0) * 256 + f2i(a1));
+  const long long lo = (long long)(f2i(a2) * 256 + f2i(a3));
+  return (hi << (72 - Pb)) + (lo << (56 - Pb)) + ((long long)f2i(a4) << (48 - Pb));
+}
+
+// d mu / 2^62 (floor), mu <= 2^62.
+__device__ __forceinline__ long long mul_mu(long long d, unsigned long long mu) {
+  const long long hi = __mul64hi(d, (long long)mu);
+  const unsigned long long lo = (unsigned long long)d * mu;
+  return (long long)(((unsigned long long)hi << 2) | (lo >> 62));
+}
+
+__device__ __forceinline__ long long shift_round(long long v, int s) {  // v 2^s, rounded
+  if (s >= 0) return v << s;
+  return (v + (1LL << (-s - 1))) >> (-s);
+}
+
+__device__ __forceinline__ int bitlen(unsigned long long v) { return v ? 64 - __clzll((long long)v) : 0; }
+
+// Digit byte k of x as the float (byte - 128): the float 2^23 + byte built with a byte permute.
+__device__ __forceinline__ float digit_f(uint32_t x, int k) {
+  return __fsub_rn(__uint_as_float(__byte_perm(x, 0x4B000000u, 0x7540u + (uint32_t)k)), 8388736.0f);
+}
+
+// Six BF16 digit slices of eight values (|v| <= 2^46): w[a][i] packs values 2i, 2i + 1 of slice a.
+__device__ __forceinline__ void slice8(const long long v[8], uint32_t w[kS][4]) {
 #pragma unroll
-  for (int p = 0; p < 4; ++p) {
-    float f[kS][2];
-#pragma unroll
-    for (int hh = 0; hh < 2; ++hh) {
-      const long long tb = t[2 * p + hh] + 0x808080808080LL;
-      const uint32_t lo = (uint32_t)tb, hi = (uint32_t)(tb >> 32);
-      const uint32_t byte[kS] = {hi >> 8, hi & 0xFFu, lo >> 24, (lo >> 16) & 0xFFu, (lo >> 8) & 0xFFu, lo & 0xFFu};
-#pragma unroll
-      for (int a = 0; a < kS; ++a) {
-        const int ef = 150 - 8 * (a + 1);
-        f[a][hh] = __fsub_rn(__int_as_float((ef << 23) | (int)byte[a]), __int_as_float((ef << 23) | 128));
-      }
-    }
+  for (int i = 0; i < 4; ++i) {
+    const unsigned long long t0 = (unsigned long long)(v[2 * i] + 0x808080808080LL);
+    const unsigned long long t1 = (unsigned long long)(v[2 * i + 1] + 0x808080808080LL);
+    const uint32_t l0 = (uint32_t)t0, h0 = (uint32_t)(t0 >> 32), l1 = (uint32_t)t1, h1 = (uint32_t)(t1 >> 32);
+    const uint32_t x0[kS] = {h0, h0, l0, l0, l0, l0}, x1[kS] = {h1, h1, l1, l1, l1, l1};
+    const int byte[kS] = {1, 0, 3, 2, 1, 0};
 #pragma unroll
     for (int a = 0; a < kS; ++a) {
-      const __nv_bfloat162 v = __floats2bfloat162_rn(f[a][0], f[a][1]);
-      w[a][p] = *reinterpret_cast<const uint32_t*>(&v);
+      const __nv_bfloat162 p = __floats2bfloat162_rn(digit_f(x0[a], byte[a]), digit_f(x1[a], byte[a]));
+      w[a][i] = *reinterpret_cast<const uint32_t*>(&p);
     }
   }
-#pragma unroll
-  for (int a = 0; a < kS; ++a) out[a] = make_uint4(w[a][0], w[a][1], w[a][2], w[a][3]);
 }
 
-// Compensated FP32 pair helpers (Knuth TwoSum, FMA-based exact product).
-__device__ __forceinline__ df df_renorm(float s, float e) {
-  const float hi = __fadd_rn(s, e);
-  return df{hi, __fsub_rn(e, __fsub_rn(hi, s))};
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t w[4]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "r"(w[0]), "r"(w[1]),
+               "r"(w[2]), "r"(w[3])
+               : "memory");
 }
-__device__ __forceinline__ df two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-  return df{s, e};
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float f[8]) {
+  uint32_t v[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) f[i] = __uint_as_float(v[i]);
 }
-// D0 + ... + D5 (each exact; D_t is about 2^-8t of D0): the leading three summed without error,
-// the tail (below 2^-24 of the result) with ordinary additions.
-__device__ __forceinline__ df combine6(const float d[kAcc]) {
-  const df s = two_sum(d[0], d[1]);
-  const df a = two_sum(s.lo, d[2]);
-  const float tail = __fadd_rn(a.lo, __fadd_rn(d[3], __fadd_rn(d[4], d[5])));
-  const df f = two_sum(s.hi, a.hi);
-  return df_renorm(f.hi, __fadd_rn(f.lo, tail));
-}
-__device__ __forceinline__ df df_mul(df a, df b) {
-  const float p = __fmul_rn(a.hi, b.hi);
-  float e = __fmaf_rn(a.hi, b.hi, -p);
-  e = __fmaf_rn(a.hi, b.lo, e);
-  e = __fmaf_rn(a.lo, b.hi, e);
-  return df_renorm(p, e);
-}
-__device__ __forceinline__ df df_add(df a, df b) {
-  const df s = two_sum(a.hi, b.hi);
-  return df_renorm(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
-}
-__device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // Offset of element q of a vector: theta circles run down meridian k, then back up meridian
 // k + Nphi/2 (Sec. II.C double covering); rings are contiguous.
-__device__ __forceinline__ size_t elem(const TcArgs& A, size_t base, int q) {
+__device__ __forceinline__ long long elem_off(const TcArgs& A, long long base, int q) {
   if (A.pass == 0)
-    return q < A.Nth ? base + (size_t)q * A.Nph : base + (size_t)(2 * A.Nth - 1 - q) * A.Nph + A.Nph / 2;
+    return q < A.Nth ? base + (long long)q * A.Nph : base + (long long)(2 * A.Nth - 1 - q) * A.Nph + A.Nph / 2;
   return base + q;
 }
-// The parity sign of element q applies (theta circles of odd fields, second half).
-__device__ __forceinline__ bool flip(const TcArgs& A, const Row& R, int q) { return R.neg && q >= A.Nth; }
-// Element q as a fixed-point integer at scale E (the sign applied to the integer).
-__device__ __forceinline__ long long load_fx(const TcArgs& A, const Row& R, int q, int E) {
-  const long long t = fx64(A.src[elem(A, R.base, q)], E);
-  return flip(A, R, q) ? -t : t;
-}
-// Writes c_q - hc for element q: the stored value is s (c_q - hc) = x_stored - s hc with s the
-// parity sign, so the sign goes on hc with an integer operation and one FP64 subtraction remains.
-__device__ __forceinline__ void update_c(const TcArgs& A, const Row& R, int q, double hc) {
-  const size_t o = elem(A, R.base, q);
-  const long long sb = flip(A, R, q) ? (long long)0x8000000000000000ULL : 0LL;
-  A.dst[o] = A.src[o] - __longlong_as_double(__double_as_longlong(hc) ^ sb);
-}
 
-struct Ctx {
+struct Kern {
   const TcArgs& A;
-  Smem& S;
-  unsigned char* stage;
+  Ctl& C;
+  unsigned char* opbuf;      // operator buffer (shared)
+  long long* store;          // [kV][pitch] fixed-point store
+  const int16_t* maps;       // index maps (shared)
+  int pitch;
   uint32_t tmem;
-  float2* Yc;   // [kM][H+1]: h X_c[m], m = 0 .. H
-  float2* Ys;   // [kM][H-1]: h X_s[m + 1]
-  float2* Ye;   // [kM][H+1]: y_e[k]
-  uint4* akeep; // this CTA's copies of the first half's A stages
-  unsigned G;   // chunks issued so far by this CTA
+  int tid, warp, lane, lq, cp, WQ, r, h, v;   // thread role in the GEMM phases: row r = 32 lq + lane
+  uint32_t op_phase, mma_phase;
 };
 
-// Eight consecutive K values of GEMM operand A (vector data) for row r, as fixed-point integers;
-// *nyq gets their contribution to the Nyquist sum of the CF or CI operand.
-__device__ __forceinline__ void gather8(Ctx& C, int op, int r, int k0, long long t[8], long long* nyq) {
-  const TcArgs& A = C.A;
-  const Row& R = C.S.row[r];
-  const int L = A.L, H = L / 2;
-  *nyq = 0;
-#pragma unroll
-  for (int i = 0; i < 8; ++i) t[i] = 0;
-  if (!R.valid) return;
-  if (op == kCF) {
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int q = k0 + i;
-      if (q <= H) {
-        long long u = load_fx(A, R, q, R.ex);
-        if (q != 0 && q != H) u += load_fx(A, R, L - q, R.ex);
-        t[i] = u;
-        *nyq += (q & 1) ? -u : u;  // cos(pi q)
-      }
-    }
-  } else if (op == kSF) {
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int q = k0 + i + 1;
-      if (q < H) t[i] = load_fx(A, R, q, R.ex) - load_fx(A, R, L - q, R.ex);
-    }
-  } else {
-    const float2* src = op == kCI ? C.Yc + (size_t)r * (H + 1) : C.Ys + (size_t)r * (H - 1);
-    const int K = op == kCI ? H + 1 : H - 1;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int m = k0 + i;
-      if (m < K) {
-        const float2 y = src[m];
-        t[i] = fx32(y.x, R.ey) + fx32(y.y, R.ey);
-        if (op == kCI) {
-          const long long wt = (m == 0 || m == H) ? t[i] : 2 * t[i];  // w_m cos(pi m)
-          *nyq += (m & 1) ? -wt : wt;
-        }
-      }
-    }
-  }
-}
-
-// One pass of the K loop of a GEMM over 128 vectors for outputs [half NPh, (half + 1) NPh):
-// accumulator t (diagonal a + b = t) in tensor-memory columns [t NPh, (t + 1) NPh). Returns false
-// if a wait ran out.
-__device__ bool gemm(Ctx& C, int op, int half) {
-  const TcArgs& A = C.A;
-  const OpTab& T = A.op[op];
-  const int nk = T.KP / kKC;
-  const int NP = T.NPh * T.nh;
-  const int tid = threadIdx.x;
-  const uint32_t idesc = make_idesc(T.NPh);
-  bool init[kAcc] = {false, false, false, false, false, false};
-  for (int kc = 0; kc < nk; ++kc) {
-    const unsigned G = C.G++;
-    const int s = (int)(G & 1u);
-    unsigned char* sa = C.stage + (size_t)s * kStage;
-    unsigned char* sb = sa + kStageA;
-    // stage s is free once the MMAs of chunk G - 2 are done; each thread waits by itself (no block
-    // barrier here, so the warps that do not issue MMAs start this chunk during the issue), and a
-    // wait that runs out is acted on at the barrier below
-    const bool waited = G < 2 || mbar_wait(su32(&C.S.bar[s]), ((G - 2) >> 1) & 1u);
-    // operand A: six slices of the vector data. A GEMM with two output halves produces them in
-    // its first half and keeps a copy; the second half copies the stage back instead.
-    uint4* keep = T.nh > 1 ? C.akeep + (size_t)kc * (kStageA / 16) : nullptr;
-    if (half == 0) {
-      for (int task = tid; task < kM * (kKC / 8); task += kThr) {
-        const int r = task & (kM - 1), g = task / kM;
-        long long t[8], nyq;
-        gather8(C, op, r, kc * kKC + g * 8, t, &nyq);
-        if (nyq != 0) atomicAdd(&C.S.nyq[r], (unsigned long long)nyq);
-        uint4 w[kS];
-        slice8(t, w);
-#pragma unroll
-        for (int a = 0; a < kS; ++a) {
-          const uint32_t o = a * kM * kKC * 2 + 2 * kmaj_elem(r, g * 8);
-          *reinterpret_cast<uint4*>(sa + o) = w[a];
-          if (keep) keep[o / 16] = w[a];
-        }
-      }
-    } else {
-      for (int i = tid; i < (int)(kStageA / 16); i += kThr) reinterpret_cast<uint4*>(sa)[i] = keep[i];
-    }
-    // operand B: the chunk's six operator slices, rows of this half (contiguous 8-row groups)
-    {
-      const int per_slice = T.NPh * kKC * 2 / 16;
-      for (int i = tid; i < kS * per_slice; i += kThr) {
-        const int b = i / per_slice, j = i - b * per_slice;
-        const uint4* src = reinterpret_cast<const uint4*>(T.tab + ((size_t)(kc * kS + b) * NP + half * T.NPh) * kKC);
-        reinterpret_cast<uint4*>(sb + (size_t)b * T.NPh * kKC * 2)[j] = __ldg(src + j);
-      }
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    if (!__syncthreads_and(waited ? 1 : 0)) return false;
-    if (tid == kThr - 32) {  // lane 0 of the last warp issues the chunk's MMAs
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a0 = su32(sa), b0 = su32(sb);
-#pragma unroll
-      for (int ks = 0; ks < kKC / 16; ++ks) {
-#pragma unroll
-        for (int a = 0; a < kS; ++a) {
-#pragma unroll
-          for (int b = 0; a + b < kAcc; ++b) {
-            const int acc = a + b;
-            const uint32_t d = C.tmem + (uint32_t)(acc * T.NPh);
-            const uint64_t da = make_desc(a0 + (uint32_t)(a * kM * kKC * 2 + ks * 256));
-            const uint64_t db = make_desc(b0 + (uint32_t)(b * T.NPh * kKC * 2 + ks * 256));
-            const uint32_t en = init[acc] ? 1u : 0u;
-            asm volatile(
-                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-                "l"(da), "l"(db), "r"(idesc), "r"(en));
-            init[acc] = true;
-          }
-        }
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       su32(&C.S.bar[s]))
-                   : "memory");
-    }
-  }
-  // wait for the last chunk (its commit covers every earlier MMA of this thread)
-  const unsigned last = C.G - 1;
-  if (!__syncthreads_and(mbar_wait(su32(&C.S.bar[last & 1u]), (last >> 1) & 1u) ? 1 : 0)) return false;
+// Issue the MMAs of one GEMM: D (columns N) = A (tensor memory, K) x B^T (shared, N x K), 21 digit
+// pairs, 5 accumulators; then commit to the MMA barrier. One thread.
+__device__ void issue_gemm(Kern& k, int K, int N) {
+  const PassDesc& d = k.A.d;
+  const uint32_t idesc = make_idesc(N);
+  const uint32_t sliceB = (uint32_t)(N * K * 2);
+  const uint32_t b0 = su32(k.opbuf);
+  const uint32_t acc0 = k.tmem + (uint32_t)(3 * d.KA);
+  const int nks = K / 16;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  return true;
+#pragma unroll 1
+  for (int t = 5; t >= 0; --t) {
+    const int acc = t >= 4 ? 4 : t;
+    const uint32_t dcol = acc0 + (uint32_t)(acc * d.NA);
+#pragma unroll 1
+    for (int s = 0; s < nks; ++s)
+#pragma unroll 1
+      for (int a = 0; a <= t; ++a) {
+        const int b = t - a;
+        if (b >= kS || a >= kS) continue;
+        const bool first = s == 0 && a == 0 && (t == 5 || t <= 3);
+        const bool scaled = s == 0 && a == 0 && t == 4;
+        const uint32_t acol = k.tmem + (uint32_t)(a * (d.KA / 2) + s * 8);
+        const uint64_t bd = make_desc(b0 + (uint32_t)b * sliceB + (uint32_t)s * 256, K);
+        const uint32_t en = first ? 0u : 1u;
+        if (scaled)
+          asm volatile(
+              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p, 8;\n\t}" ::"r"(dcol),
+              "r"(acol), "l"(bd), "r"(idesc), "r"(en));
+        else
+          asm volatile(
+              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(dcol),
+              "r"(acol), "l"(bd), "r"(idesc), "r"(en));
+      }
+  }
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(&k.C.mma_bar))
+               : "memory");
 }
 
-// Eight columns of the six accumulators for this thread's tensor-memory lane.
-__device__ __forceinline__ void tmem_ld6(uint32_t taddr, int NPh, float d[kAcc][8]) {
-  uint32_t v[kAcc][8];
-#pragma unroll
-  for (int acc = 0; acc < kAcc; ++acc)
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(v[acc][0]), "=r"(v[acc][1]), "=r"(v[acc][2]), "=r"(v[acc][3]), "=r"(v[acc][4]),
-                   "=r"(v[acc][5]), "=r"(v[acc][6]), "=r"(v[acc][7])
-                 : "r"(taddr + (uint32_t)(acc * NPh)));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int acc = 0; acc < kAcc; ++acc)
-#pragma unroll
-    for (int i = 0; i < 8; ++i) d[acc][i] = __uint_as_float(v[acc][i]);
+// Runs one GEMM: waits for the operator, issues (thread 0), waits for completion (all threads).
+// Returns false if a wait ran out.
+__device__ bool run_gemm(Kern& k, int K, int N) {
+  // A operand written by every thread: make it visible to the tensor core
+  tmem_wait_st();
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  bool ok = true;
+  if (k.tid == 0) {
+    ok = mbar_wait(su32(&k.C.op_bar), k.op_phase & 1u);
+    if (ok) issue_gemm(k, K, N);
+    else atomicExch(&k.C.abort, 1);
+  }
+  k.op_phase++;
+  __syncthreads();
+  if (k.C.abort) return false;
+  ok = mbar_wait(su32(&k.C.mma_bar), k.mma_phase & 1u);
+  k.mma_phase++;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  return __syncthreads_and(ok ? 1 : 0) != 0;
 }
 
-// Epilogue of one pass of a GEMM. Warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (one vector
-// each) and the 8-column groups w / 4, w / 4 + 4, ... of the pass's output columns.
-__device__ void epilogue(Ctx& C, int op, int half) {
-  const TcArgs& A = C.A;
-  const OpTab& T = A.op[op];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int quarter = warp & 3, side = warp >> 2;
-  const int r = 32 * quarter + lane;
-  const Row& R = C.S.row[r];
-  const int L = A.L, H = L / 2;
-  const uint32_t taddr = C.tmem + ((uint32_t)(32 * quarter) << 16);
-  const int c_begin = side * 8, c_end = T.NPh, c_step = (kThr / 128) * 8;
-  const int S2 = R.ex + A.Ef + R.ey + A.Ei;  // output scale of the inverse GEMMs
-  int emax = 0;
-  for (int c0 = c_begin; c0 < c_end; c0 += c_step) {
-    float d[kAcc][8];
-    tmem_ld6(taddr + (uint32_t)c0, T.NPh, d);
-    if (!R.valid) continue;
+// Slices 8 values of row r into the A region at K offset k0 (6 slices).
+__device__ __forceinline__ void put_a(const Kern& k, const long long vals[8], int k0) {
+  uint32_t w[kS][4];
+  slice8(vals, w);
+  const uint32_t lane_base = k.tmem + ((uint32_t)(32 * k.lq) << 16);
+#pragma unroll
+  for (int a = 0; a < kS; ++a) tmem_st4(lane_base + (uint32_t)(a * (k.A.d.KA / 2) + k0 / 2), w[a]);
+}
+
+// Prologue: the GEMM's input coordinates of row r, brought to 46 bits, as the A operand.
+__device__ void prologue(Kern& k, const GemmDesc& g) {
+  const int16_t* kin = k.maps + g.kin_off + k.h * g.Kc;
+  const bool act = k.C.row[k.v].valid && (k.h == 0 || g.rows2);
+  const long long* srow = k.store + (size_t)k.v * k.pitch;
+  unsigned long long orv = 0;
+  const int nch = g.Kc / 8;
+  if (act)
+    for (int c = k.cp; c < nch; c += k.WQ)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int idx = kin[8 * c + i];
+        const long long x = idx >= 0 ? srow[idx] : 0;
+        orv |= (unsigned long long)(x ^ (x >> 63));
+      }
+  if (orv) atomicMax(&k.C.rowbl[k.r], bitlen(orv));
+  __syncthreads();
+  const int bl = k.C.rowbl[k.r];
+  const int sh = bl ? 46 - bl : 0;
+  for (int c = k.cp; c < nch; c += k.WQ) {
+    long long vals[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const int n = half * T.NPh + c0 + i;
-      if (n >= T.N) continue;
-      float dd[kAcc];
+      const int idx = act ? kin[8 * c + i] : -1;
+      vals[i] = idx >= 0 ? shift_round(srow[idx], sh) : 0;
+    }
+    put_a(k, vals, 8 * c);
+  }
+  __syncthreads();  // every thread has read rowbl
+  if (k.cp == 0) {
+    k.C.sh_in[k.r] = sh;
+    k.C.rowbl[k.r] = 0;
+  }
+}
+
+// Mid step: forward GEMM result -> times mu_m -> rescaled per row -> the inverse GEMM's A operand.
+__device__ void mid_step(Kern& k, const GemmDesc& g) {
+  const int16_t* mode = k.maps + g.mode_off + k.h * g.Km;
+  const bool act = k.C.row[k.v].valid && (k.h == 0 || g.rows2);
+  const unsigned long long* mu = k.C.row[k.v].mu;
+  const int coff = g.concat ? k.h * g.Km : 0;
+  const uint32_t lane_base = k.tmem + ((uint32_t)(32 * k.lq) << 16);
+  const uint32_t accb = lane_base + (uint32_t)(3 * k.A.d.KA);
+  const int nch = g.Km / 8;
+  long long y[kMaxChunks][8];
+  unsigned long long orv = 0;
 #pragma unroll
-      for (int acc = 0; acc < kAcc; ++acc) dd[acc] = d[acc][i];
-      const df z = combine6(dd);
-      if (op == kCF || op == kSF) {
-        const int m = op == kCF ? n : n + 1;
-        const float2 hm = R.h[m];
-        const df y = df_mul(z, df{hm.x, hm.y});
-        const float2 yv = make_float2(y.hi, y.lo);
-        if (op == kCF) C.Yc[(size_t)r * (H + 1) + n] = yv;
-        else C.Ys[(size_t)r * (H - 1) + n] = yv;
-        emax = max(emax, (__float_as_int(y.hi) >> 23) & 0xFF);
-      } else if (op == kCI) {
-        const int k = n;
-        if (k == 0) update_c(A, R, 0, df_to_double(z, S2));
-        else C.Ye[(size_t)r * (H + 1) + k] = make_float2(z.hi, z.lo);  // read by the SI epilogue
-      } else {
-        const int k = n + 1;
-        const float2 e = C.Ye[(size_t)r * (H + 1) + k];
-        const df ye{e.x, e.y};
-        const double hp = df_to_double(df_add(ye, z), S2);
-        const double hm = df_to_double(df_add(ye, df_neg(z)), S2);
-        update_c(A, R, k, hp);
-        update_c(A, R, L - k, hm);
+  for (int ci = 0; ci < kMaxChunks; ++ci) {
+    const int c = k.cp + ci * k.WQ;
+    if (c < nch) {
+      float f[5][8];
+#pragma unroll
+      for (int t = 0; t < 5; ++t) tmem_ld8(accb + (uint32_t)(t * k.A.d.NA + coff + 8 * c), f[t]);
+      tmem_wait_ld();
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int m = act ? mode[8 * c + i] : -1;
+        long long yy = 0;
+        if (m >= 0) {
+          const long long dd = combine5(f[0][i], f[1][i], f[2][i], f[3][i], f[4][i], g.Pb);
+          yy = mul_mu(dd, __ldg(mu + m));
+        }
+        y[ci][i] = yy;
+        orv |= (unsigned long long)(yy ^ (yy >> 63));
       }
     }
   }
-  // Nyquist terms from the exact integer sums (one thread per vector, once per GEMM)
-  if (side == 0 && half == 0 && R.valid && (op == kCF || op == kCI)) {
-    const long long sum = (long long)C.S.nyq[r];
-    if (op == kCF) {
-      // X_c[H] in GEMM units: sum 2^-48 (data scale) 2^-Ef (operator scale)
-      const df z = df_from_double((double)sum, 48 + A.Ef);
-      const float2 hH = R.h[H];
-      const df y = df_mul(z, df{hH.x, hH.y});
-      C.Yc[(size_t)r * (H + 1) + H] = make_float2(y.hi, y.lo);
-      emax = max(emax, (__float_as_int(y.hi) >> 23) & 0xFF);
-    } else {
-      // y_e[H] = (1/L) sum_m w_m cos(pi m) h_m X_c[m], in GEMM units 2^-48 2^-Ei
-      const df z = df_from_double((double)sum / (double)L, 48 + A.Ei);
-      update_c(A, R, H, df_to_double(z, S2));
+  if (orv) atomicMax(&k.C.rowbl[k.r], bitlen(orv));
+  __syncthreads();
+  const int bl = k.C.rowbl[k.r];
+  const int sm = bl ? 46 - bl : 0;
+#pragma unroll
+  for (int ci = 0; ci < kMaxChunks; ++ci) {
+    const int c = k.cp + ci * k.WQ;
+    if (c < nch) {
+      long long vals[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) vals[i] = shift_round(y[ci][i], sm);
+      put_a(k, vals, 8 * c);
     }
   }
-  if (op == kCF || op == kSF) atomicMax(&C.S.emax[r], emax);
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (k.cp == 0) {
+    k.C.sh_mid[k.r] = sm;
+    k.C.rowbl[k.r] = 0;
+  }
 }
 
-__global__ void __launch_bounds__(kThr, 1) tc_pass_kernel(TcArgs A) {
+// Epilogue: the inverse GEMM's result W (units 2^-(sh_in + sh_mid) of the store) subtracted from the
+// stored coordinates.
+__device__ void epilogue(Kern& k, const GemmDesc& g) {
+  const int16_t* kin = k.maps + g.kin_off + k.h * g.Kc;
+  const bool act = k.C.row[k.v].valid && (k.h == 0 || g.rows2);
+  const int coff = g.concat ? k.h * g.Kc : 0;
+  const uint32_t lane_base = k.tmem + ((uint32_t)(32 * k.lq) << 16);
+  const uint32_t accb = lane_base + (uint32_t)(3 * k.A.d.KA);
+  const int tot = -(k.C.sh_in[k.r] + k.C.sh_mid[k.r]);
+  long long* srow = k.store + (size_t)k.v * k.pitch;
+  const int nch = g.Kc / 8;
+  for (int c = k.cp; c < nch; c += k.WQ) {
+    float f[5][8];
+#pragma unroll
+    for (int t = 0; t < 5; ++t) tmem_ld8(accb + (uint32_t)(t * k.A.d.NA + coff + 8 * c), f[t]);
+    tmem_wait_ld();
+    if (!act) continue;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int idx = kin[8 * c + i];
+      if (idx < 0) continue;
+      const long long w = combine5(f[0][i], f[1][i], f[2][i], f[3][i], f[4][i], g.Pb);
+      srow[idx] -= shift_round(w, tot);
+    }
+  }
+}
+
+// In-place level stage (forward) on the first n entries of every vector's store.
+__device__ void level_fwd(Kern& k, int n, bool convert) {
+  const int q = n / 4;
+  const int ntask = kV * q;
+  for (int t = k.tid; t < ntask; t += blockDim.x) {
+    int v, p;
+    if (k.A.pass == 0) { v = t % kV; p = t / kV; }
+    else { p = t % q; v = t / q; }
+    long long* s = k.store + (size_t)v * k.pitch;
+    long long vp = s[p], vq = s[p + n / 2], vr = s[n / 2 - 1 - p], vs = s[n - 1 - p];
+    if (convert) {
+      const int base = 53 - k.A.d.F + k.C.vexp[v];
+      vp = to_fixed(vp, base);
+      vq = to_fixed(vq, base);
+      vr = to_fixed(vr, base);
+      vs = to_fixed(vs, base);
+    }
+    const long long e0 = vp + vq, z0 = vp - vq, e1 = vr + vs, z1 = vr - vs;
+    s[p] = e0;
+    s[n / 2 - 1 - p] = e1;
+    s[n / 2 + p] = z0 - z1;
+    s[n - 1 - p] = z0 + z1;
+  }
+}
+
+__device__ void base_fwd(Kern& k, int nb, bool convert) {
+  const int hb = nb / 2;
+  const int ntask = kV * hb;
+  for (int t = k.tid; t < ntask; t += blockDim.x) {
+    int v, p;
+    if (k.A.pass == 0) { v = t % kV; p = t / kV; }
+    else { p = t % hb; v = t / hb; }
+    long long* s = k.store + (size_t)v * k.pitch;
+    long long a = s[p], b = s[nb - 1 - p];
+    if (convert) {
+      const int base = 53 - k.A.d.F + k.C.vexp[v];
+      a = to_fixed(a, base);
+      b = to_fixed(b, base);
+    }
+    s[p] = a + b;
+    s[nb - 1 - p] = a - b;
+  }
+}
+
+// Writes value x (scaled by 2^expo) of position q of vector v to the destination state.
+__device__ __forceinline__ void put_out(const Kern& k, int v, int q, long long x, int expo) {
+  const RowInfo& R = k.C.row[v];
+  double y = from_fixed(x, expo);
+  if (k.A.pass == 0 && R.neg && q >= k.A.Nth) y = -y;
+  k.A.dst[elem_off(k.A, R.base, q)] = y;
+}
+
+// Inverse base stage: values become 2 v; `out` writes them to the destination (no levels).
+__device__ void base_inv(Kern& k, int nb, bool out) {
+  const int hb = nb / 2;
+  const int ntask = kV * hb;
+  for (int t = k.tid; t < ntask; t += blockDim.x) {
+    int v, p;
+    if (k.A.pass == 0) { v = t % kV; p = t / kV; }
+    else { p = t % hb; v = t / hb; }
+    long long* s = k.store + (size_t)v * k.pitch;
+    const long long a = s[p], b = s[nb - 1 - p];
+    if (out) {
+      if (!k.C.row[v].valid) continue;
+      const int expo = (k.C.vexp[v] - 1022) - k.A.d.F - 1;
+      put_out(k, v, p, a + b, expo);
+      put_out(k, v, nb - 1 - p, a - b, expo);
+    } else {
+      s[p] = a + b;
+      s[nb - 1 - p] = a - b;
+    }
+  }
+}
+
+// Inverse level stage for the level of length n, with the T-even part scaled by 2^sc (sc >= 1);
+// results scaled by 2^(sc + 1). `out` writes them to the destination (outermost level).
+__device__ void level_inv(Kern& k, int n, int sc, bool out) {
+  const int q = n / 4;
+  const int ntask = kV * q;
+  for (int t = k.tid; t < ntask; t += blockDim.x) {
+    int v, p;
+    if (k.A.pass == 0) { v = t % kV; p = t / kV; }
+    else { p = t % q; v = t / q; }
+    long long* s = k.store + (size_t)v * k.pitch;
+    const long long E0 = s[p], E1 = s[n / 2 - 1 - p], a = s[n / 2 + p], o = s[n - 1 - p];
+    const long long zp = (o + a) << (sc - 1), zq = (o - a) << (sc - 1);
+    const long long y0 = E0 + zp, y1 = E0 - zp, y2 = E1 + zq, y3 = E1 - zq;
+    if (out) {
+      if (!k.C.row[v].valid) continue;
+      const int expo = (k.C.vexp[v] - 1022) - k.A.d.F - (sc + 1);
+      put_out(k, v, p, y0, expo);
+      put_out(k, v, p + n / 2, y1, expo);
+      put_out(k, v, n / 2 - 1 - p, y2, expo);
+      put_out(k, v, n - 1 - p, y3, expo);
+    } else {
+      s[p] = y0;
+      s[p + n / 2] = y1;
+      s[n / 2 - 1 - p] = y2;
+      s[n - 1 - p] = y3;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(512, 1) tc_pass_kernel(const __grid_constant__ TcArgs A) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  Smem& S = *reinterpret_cast<Smem*>(smem + 2 * kStage);
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int L = A.L, H = L / 2;
+  const PassDesc& d = A.d;
+  const int L = d.L;
+  const int pitch = L + 1;
+  unsigned char* opbuf = smem;
+  long long* store = reinterpret_cast<long long*>(smem + ((d.op_max + 1023) / 1024) * 1024);
+  int16_t* maps = reinterpret_cast<int16_t*>(store + (size_t)kV * pitch);
+  Ctl& C = *reinterpret_cast<Ctl*>(reinterpret_cast<unsigned char*>(maps) + ((d.nmap * 2 + 15) / 16) * 16);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&S.tslot)),
-                 "r"(512));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&C.tslot)),
+                 "r"(d.tmem_cols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&S.bar[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&S.bar[1])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&C.op_bar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&C.mma_bar)));
     asm volatile("fence.mbarrier_init.release.cluster;");
-    S.abort = 0;
+    C.abort = 0;
   }
+  for (int i = tid; i < d.nmap; i += blockDim.x) maps[i] = A.maps[i];
+  for (int i = tid; i < kM; i += blockDim.x) C.rowbl[i] = 0;
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  Ctx C{A, S, smem, S.tslot, nullptr, nullptr, nullptr, nullptr, 0u};
-  C.Yc = A.scratch + (size_t)kM * (3 * H + 1) * blockIdx.x;
-  C.Ys = C.Yc + (size_t)kM * (H + 1);
-  C.Ye = C.Ys + (size_t)kM * (H - 1);
-  C.akeep = A.akeep + (size_t)A.akeep_chunks * (kStageA / 16) * blockIdx.x;
-  const long long ntiles = (A.nvec + kM - 1) / kM;
+  Kern k{A, C, opbuf, store, maps, pitch, C.tslot, tid, warp, lane, warp & 3, warp >> 2, (int)(blockDim.x / 128),
+         0, 0, 0, 0u, 0u};
+  k.r = 32 * k.lq + lane;
+  k.h = k.r >> 6;
+  k.v = k.r & (kV - 1);
+  const long long ntiles = (A.nvec + kV - 1) / kV;
   bool ok = true;
   for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-    // vector set-up: row r <- vector tile * 128 + r
-    if (tid < kM) {
-      Row R{};
-      const long long vg = tile * kM + tid;
+    // the first operator of the tile (the buffer is free: the previous tile's GEMMs completed)
+    if (tid == 0) bulk_load(opbuf, A.ops + d.g[0].fwd_off, d.g[0].fwd_bytes, su32(&C.op_bar));
+    if (tid < kV) {
+      RowInfo R{};
+      const long long vg = tile * kV + tid;
       R.valid = vg < A.nvec;
       if (R.valid) {
         if (A.pass == 0) {
           const int half = A.Nph / 2;
           const int shell = A.list[vg / half];
-          const int k = (int)(vg % half);
-          const int v = shell / A.Nr, i = shell - v * A.Nr;
-          const VarInfo vi = A.var[v];
-          R.base = (size_t)shell * A.Nth * A.Nph + k;
-          R.h = A.h + ((size_t)vi.cls * A.Nr + i) * (A.Nth + 1);
+          const int kk = (int)(vg % half);
+          const int vv = shell / A.Nr, i = shell - vv * A.Nr;
+          const VarInfo vi = A.var[vv];
+          R.base = (long long)shell * A.Nth * A.Nph + kk;
+          R.mu = A.mu + ((size_t)vi.cls * A.Nr + i) * (A.Nth + 1);
           R.neg = vi.parity;
         } else {
           const int ring = A.list[vg];
           const int j = ring % A.Nth, vi_ = ring / A.Nth;
-          const int v = vi_ / A.Nr, i = vi_ - v * A.Nr;
-          const VarInfo vi = A.var[v];
-          R.base = (size_t)ring * A.Nph;
-          R.h = A.h + (((size_t)vi.cls * A.Nr + i) * A.Nth + j) * (H + 1);
+          const int vv = vi_ / A.Nr, i = vi_ - vv * A.Nr;
+          const VarInfo vi = A.var[vv];
+          R.base = (long long)ring * A.Nph;
+          R.mu = A.mu + (((size_t)vi.cls * A.Nr + i) * A.Nth + j) * (A.Nph / 2 + 1);
           R.neg = 0;
         }
       }
-      S.row[tid] = R;
-      S.emax[tid] = 0;
-      S.nyq[tid] = 0ull;
+      C.row[tid] = R;
+      C.vexp[tid] = 0;
     }
     __syncthreads();
-    // input scale: largest FP64 exponent over the vector; lanes run along contiguous memory (the
-    // vector index for theta circles, the ring for rings)
+    // load: raw FP64 values (parity sign applied) and each vector's largest exponent
     if (A.pass == 0) {
-      const int r = tid & (kM - 1), part = tid / kM, np = kThr / kM;
-      const Row& R = S.row[r];
+      const int v = tid % kV;
+      const RowInfo& R = C.row[v];
       int e = 0;
-      if (R.valid)
-        for (int q = part; q < L; q += np)
-          e = max(e, (int)((__double_as_longlong(A.src[elem(A, R.base, q)]) >> 52) & 0x7FF));
-      atomicMax(&S.emax[r], e);
+      for (int q = tid / kV; q < L; q += blockDim.x / kV) {
+        long long b = 0;
+        if (R.valid) {
+          b = __double_as_longlong(A.src[elem_off(A, R.base, q)]);
+          if (R.neg && q >= A.Nth) b ^= (long long)0x8000000000000000ULL;
+          e = max(e, (int)((b >> 52) & 0x7FF));
+        }
+        store[(size_t)v * pitch + q] = b;
+      }
+      atomicMax(&C.vexp[v], e);
     } else {
-      const int lane = tid & 31;
-      for (int r = warp; r < kM; r += kThr / 32) {
-        const Row& R = S.row[r];
+      for (int v = warp; v < kV; v += blockDim.x / 32) {
+        const RowInfo& R = C.row[v];
         int e = 0;
-        if (R.valid)
-          for (int q = lane; q < L; q += 32) e = max(e, (int)((__double_as_longlong(A.src[R.base + q]) >> 52) & 0x7FF));
+        for (int q = lane; q < L; q += 32) {
+          long long b = 0;
+          if (R.valid) {
+            b = __double_as_longlong(A.src[R.base + q]);
+            e = max(e, (int)((b >> 52) & 0x7FF));
+          }
+          store[(size_t)v * pitch + q] = b;
+        }
         e = __reduce_max_sync(0xffffffffu, e);
-        if (lane == 0) atomicMax(&S.emax[r], e);
+        if (lane == 0) C.vexp[v] = e;
       }
     }
     __syncthreads();
-    if (tid < kM) {
-      // |u| <= 2 max|c| < 2^(e - 1023 + 2), so E = e - 1023 + 3 keeps |u| 2^-E below 1/2
-      S.row[tid].ex = S.emax[tid] ? S.emax[tid] - 1023 + 3 : 0;
-      S.emax[tid] = 0;
-    }
-    __syncthreads();
-    for (int op = kCF; op <= kSI && ok; ++op) {
-      if (op == kCI) {
-        __syncthreads();  // spectrum maxima complete
-        if (tid < kM) {
-          // |Y| < 2^(e - 126) for the largest FP32 exponent field e: E = e - 125 keeps |Y| 2^-E < 1/2
-          S.row[tid].ey = S.emax[tid] ? S.emax[tid] - 125 : 0;
-          S.nyq[tid] = 0ull;
-        }
+    // symmetry split, in place (the first stage converts to fixed point)
+    {
+      int n = L;
+      for (int l = 0; l < d.nl; ++l, n /= 2) {
+        level_fwd(k, n, l == 0);
         __syncthreads();
       }
-      if (op == kSI) __syncthreads();  // y_e complete before the SI epilogue reads it
-      for (int half = 0; half < A.op[op].nh && ok; ++half) {
-        ok = gemm(C, op, half);
-        if (ok) epilogue(C, op, half);
+      base_fwd(k, d.nb, d.nl == 0);
+      __syncthreads();
+    }
+    // block GEMM pairs
+    for (int gi = 0; gi < d.ngemm && ok; ++gi) {
+      const GemmDesc& g = d.g[gi];
+      prologue(k, g);
+      ok = run_gemm(k, g.Kc, g.concat ? 2 * g.Km : g.Km);
+      if (!ok) break;
+      if (tid == 0) bulk_load(opbuf, A.ops + g.inv_off, g.inv_bytes, su32(&C.op_bar));
+      mid_step(k, g);
+      ok = run_gemm(k, g.Km, g.concat ? 2 * g.Kc : g.Kc);
+      if (!ok) break;
+      if (tid == 0 && gi + 1 < d.ngemm) bulk_load(opbuf, A.ops + d.g[gi + 1].fwd_off, d.g[gi + 1].fwd_bytes, su32(&C.op_bar));
+      epilogue(k, g);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+    }
+    if (!ok) break;
+    // undo the split and write the results (FP64)
+    if (d.nl == 0) {
+      base_inv(k, d.nb, true);
+    } else {
+      base_inv(k, d.nb, false);
+      __syncthreads();
+      int sc = 1;
+      int n = d.nb * 2;
+      for (int l = d.nl - 1; l >= 1; --l, n *= 2, ++sc) {
+        level_inv(k, n, sc, false);
+        __syncthreads();
       }
+      level_inv(k, n, sc, true);
     }
-    if (!ok) atomicExch(&S.abort, 1);
     __syncthreads();
-    if (S.abort) {
-      if (tid == 0) atomicCAS(A.status, 0u, (unsigned)SPH_ETIMEOUT);
-      ok = false;
-    }
   }
+  if (!ok && tid == 0) atomicCAS(A.status, 0u, (unsigned)SPH_ETIMEOUT);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(S.tslot), "r"(512));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(C.tslot), "r"(d.tmem_cols));
 }
 
-// ---------------------------------------------------------------- host side
-
-// Balanced base-256 digits of v (|v| <= 1/2), most significant first: v ~ sum_a d_a 256^-(a+1).
-void digits(long double v, int d[kS]) {
-  for (int a = 0; a < kS; ++a) {
-    v *= 256.0L;
-    const long double r = rintl(v);
-    d[a] = (int)r;
-    v -= r;
-  }
-}
-
-uint16_t bf16_bits_exact(int d, int a) {
-  const float f = ldexpf((float)d, -8 * (a + 1));  // at most 8 significant bits: exact in BF16
-  uint32_t u;
-  std::memcpy(&u, &f, 4);
-  return (uint16_t)(u >> 16);
-}
-
-int pad_to(int n, int m) { return (n + m - 1) / m * m; }
-
-// Slices of the N x K operator F(n, k) 2^-E in the layout gemm() reads.
-template <class F>
-std::vector<uint16_t> build_op(int N, int K, int E, F f, OpTab* t) {
-  t->N = N;
-  t->K = K;
-  t->nh = 1;
-  t->NPh = pad_to(std::max(N, 16), 16);
-  if (t->NPh > kMaxNPh) {
-    t->nh = 2;
-    t->NPh = pad_to((N + 1) / 2, 16);
-  }
-  t->KP = pad_to(std::max(K, 1), kKC);
-  const int NP = t->NPh * t->nh;
-  std::vector<uint16_t> tab((size_t)(t->KP / kKC) * kS * NP * kKC, 0);
-  for (int n = 0; n < N; ++n)
-    for (int k = 0; k < K; ++k) {
-      int d[kS];
-      digits(ldexpl(f(n, k), -E), d);
-      const int kc = k / kKC;
-      for (int b = 0; b < kS; ++b)
-        tab[((size_t)kc * kS + b) * NP * kKC + kmaj_elem(n, k % kKC)] = bf16_bits_exact(d[b], b);
-    }
-  return tab;
+size_t smem_bytes(const PassDesc& d) {
+  const size_t op = (d.op_max + 1023) / 1024 * 1024;
+  const size_t store = (size_t)kV * (d.L + 1) * 8;
+  const size_t maps = ((size_t)d.nmap * 2 + 15) / 16 * 16;
+  return op + store + maps + sizeof(Ctl);
 }
 
 }  // namespace tcx
 
+// ---------------------------------------------------------------- host side
+
 struct TcPass {
-  int L = 0;
-  void* d_tab = nullptr;           // the four operators' slices
-  tcx::OpTab op[4];
-  int Ef = 0, Ei = 0;
-  float2* d_h = nullptr;
+  tcx::PassDesc d{};
+  unsigned char* d_ops = nullptr;
+  int16_t* d_maps = nullptr;
+  unsigned long long* d_mu = nullptr;
   int* d_list = nullptr;
   std::vector<long long> var_off;  // list entries of fields [0, v): prefix counts
   std::vector<int> copy_runs;      // theta pass: [field, first shell, shells] runs of identity shells
+  size_t smem = 0;
+  int ctas_per_sm = 1;
 };
 
-// Scratch set 0 serves sph_filter_apply and the calls built on it; sets 1..3 (allocated on first
-// use) serve the three streams of the host-buffer pipeline, whose chunk launches may overlap.
 struct TcPlan {
   TcPass pass[2];
-  float2* d_scratch = nullptr;       // set 0
-  uint4* d_akeep = nullptr;
-  float2* d_scratch_pipe = nullptr;  // sets 1..3
-  uint4* d_akeep_pipe = nullptr;
-  size_t scratch_set = 0, akeep_set = 0;  // elements per set
-  int akeep_chunks = 0;
   int nsm = 0;
 };
 
 namespace {
 
-sph_status build_pass(TcPass* P, int L) {
-  using namespace tcx;
-  const long double pi = acosl(-1.0L);
-  const int H = L / 2;
-  P->L = L;
-  // forward entries are at most 1 -> E = 1; inverse entries at most 2/L -> smallest E with 2/L <= 2^(E-1)
-  P->Ef = 1;
-  int Ei = 1;
-  while (ldexpl(1.0L, Ei - 2) >= 2.0L / (long double)L) --Ei;
-  P->Ei = Ei;
-  auto cs = [&](long long m, long long k) { return cosl(2.0L * pi * (long double)((m * k) % L) / (long double)L); };
-  auto sn = [&](long long m, long long k) { return sinl(2.0L * pi * (long double)((m * k) % L) / (long double)L); };
-  // the cos GEMMs leave out their Nyquist output (m = H, k = H), summed exactly in the kernel
-  std::vector<uint16_t> t0 = build_op(H, H + 1, P->Ef, [&](int m, int q) { return cs(m, q); }, &P->op[kCF]);
-  std::vector<uint16_t> t1 =
-      build_op(H - 1, H - 1, P->Ef, [&](int n, int k) { return sn(n + 1, k + 1); }, &P->op[kSF]);
-  std::vector<uint16_t> t2 = build_op(
-      H, H + 1, P->Ei,
-      [&](int k, int m) { return ((m == 0 || m == H) ? 1.0L : 2.0L) * cs(m, k) / (long double)L; }, &P->op[kCI]);
-  std::vector<uint16_t> t3 =
-      build_op(H - 1, H - 1, P->Ei, [&](int n, int k) { return 2.0L * sn(k + 1, n + 1) / (long double)L; }, &P->op[kSI]);
-  const size_t total = t0.size() + t1.size() + t2.size() + t3.size();
-  if (cudaMalloc(&P->d_tab, total * 2) != cudaSuccess) return SPH_ENOMEM;
-  uint16_t* d = static_cast<uint16_t*>(P->d_tab);
-  const std::vector<uint16_t>* ts[4] = {&t0, &t1, &t2, &t3};
-  size_t off = 0;
-  for (int o = 0; o < 4; ++o) {
-    if (cudaMemcpy(d + off, ts[o]->data(), ts[o]->size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) return SPH_ECUDA;
-    P->op[o].tab = d + off;
-    off += ts[o]->size();
-  }
+unsigned long long mu_fixed(long double mu) {
+  if (mu <= 0) return 0ULL;
+  if (mu >= 1) return 1ULL << 62;
+  return (unsigned long long)llroundl(ldexpl(mu, 62));
+}
+
+sph_status build_tc_pass(TcPass* P, int L, int device) {
+  std::vector<uint16_t> ops;
+  std::vector<int16_t> maps;
+  if (!tcx::build_pass_desc(L, &P->d, &ops, &maps)) return SPH_EUNSUPPORTED;
+  if (cudaMalloc((void**)&P->d_ops, ops.size() * 2) != cudaSuccess) return SPH_ENOMEM;
+  if (cudaMemcpy(P->d_ops, ops.data(), ops.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) return SPH_ECUDA;
+  if (cudaMalloc((void**)&P->d_maps, maps.size() * 2) != cudaSuccess) return SPH_ENOMEM;
+  if (cudaMemcpy(P->d_maps, maps.data(), maps.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) return SPH_ECUDA;
+  P->smem = tcx::smem_bytes(P->d);
+  const int optin = max_smem_optin(device);
+  if ((int)P->smem > optin) return SPH_EUNSUPPORTED;
+  P->ctas_per_sm = (P->d.tmem_cols <= 256 && P->d.threads <= 256 && 2 * (P->smem + 1024) <= (size_t)optin) ? 2 : 1;
+  // ask for enough shared memory that no SM holds more CTAs than its tensor memory serves at once
+  // (a further CTA would wait in tcgen05.alloc until one of them has finished all its tiles)
+  P->smem = std::max(P->smem, (size_t)optin / (P->ctas_per_sm + 1) + 1024);
+  P->smem = std::min(P->smem, (size_t)optin);
   return SPH_OK;
 }
 
@@ -692,30 +727,25 @@ sph_status build_pass(TcPass* P, int L) {
 
 sph_status tc_setup(sph_filter_plan_s* p) {
   const int Lth = 2 * p->Nth, Lph = p->Nph;
-  if (Lth < 8 || Lph < 8 || Lth > tcx::kMaxL || Lph > tcx::kMaxL) return SPH_EUNSUPPORTED;
   TcPlan* T = new (std::nothrow) TcPlan();
   if (!T) return SPH_ENOMEM;
   p->tc = T;
-  sph_status st = build_pass(&T->pass[0], Lth);
-  if (st == SPH_OK) st = build_pass(&T->pass[1], Lph);
+  sph_status st = build_tc_pass(&T->pass[0], Lth, p->device);
+  if (st == SPH_OK) st = build_tc_pass(&T->pass[1], Lph, p->device);
   if (st != SPH_OK) return st;
   const int Nr = p->Nr, Nth = p->Nth, Nph = p->Nph, ncls = p->ncls;
-  // high-pass multipliers 1 - f (Sec. II.C filter functions) and the active vectors of each pass
-  std::vector<float2> hth((size_t)ncls * Nr * (Nth + 1)), hph((size_t)ncls * Nr * Nth * (Nph / 2 + 1));
-  auto pair = [](long double v) {
-    const float hi = (float)v;
-    return make_float2(hi, (float)(v - (long double)hi));
-  };
+  // removed fractions mu = 1 - f (Sec. II.C filter functions) as 62-bit fixed-point fractions
+  std::vector<unsigned long long> mth((size_t)ncls * Nr * (Nth + 1)), mph((size_t)ncls * Nr * Nth * (Nph / 2 + 1));
   for (int c = 0; c < ncls; ++c)
     for (int i = 0; i < Nr; ++i) {
       const long double lm = p->h_lmax[(size_t)c * Nr + i];
       for (int l = 0; l <= Nth; ++l)
-        hth[((size_t)c * Nr + i) * (Nth + 1) + l] = pair(1.0L - filter_value(p->cls_kind[(size_t)c], l, lm));
+        mth[((size_t)c * Nr + i) * (Nth + 1) + l] = mu_fixed(1.0L - filter_value(p->cls_kind[(size_t)c], l, lm));
       for (int j = 0; j < Nth; ++j) {
         const long double mm = p->h_mmax[((size_t)c * Nr + i) * Nth + j];
         for (int m = 0; m <= Nph / 2; ++m)
-          hph[(((size_t)c * Nr + i) * Nth + j) * (Nph / 2 + 1) + m] =
-              pair(1.0L - filter_value(p->cls_kind[(size_t)c], m, mm));
+          mph[(((size_t)c * Nr + i) * Nth + j) * (Nph / 2 + 1) + m] =
+              mu_fixed(1.0L - filter_value(p->cls_kind[(size_t)c], m, mm));
       }
     }
   std::vector<int> lth, lph;
@@ -733,7 +763,6 @@ sph_status tc_setup(sph_filter_plan_s* p) {
     T->pass[0].var_off.push_back((long long)lth.size());
     T->pass[1].var_off.push_back((long long)lph.size());
   }
-  // identity theta shells, in runs of consecutive shells per field (copied by out-of-place calls)
   {
     std::vector<char> act((size_t)p->nvars * Nr, 0);
     for (int e : lth) act[(size_t)e] = 1;
@@ -755,25 +784,14 @@ sph_status tc_setup(sph_filter_plan_s* p) {
     return cudaMemcpy(*d, h.data(), h.size() * sizeof(h[0]), cudaMemcpyHostToDevice) == cudaSuccess ? SPH_OK
                                                                                                       : SPH_ECUDA;
   };
-  st = up(&T->pass[0].d_h, hth);
-  if (st == SPH_OK) st = up(&T->pass[1].d_h, hph);
+  st = up(&T->pass[0].d_mu, mth);
+  if (st == SPH_OK) st = up(&T->pass[1].d_mu, mph);
   if (st == SPH_OK) st = up(&T->pass[0].d_list, lth);
   if (st == SPH_OK) st = up(&T->pass[1].d_list, lph);
   if (st != SPH_OK) return st;
   if (cudaDeviceGetAttribute(&T->nsm, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) return SPH_ECUDA;
-  const int Hmax = std::max(Lth, Lph) / 2;
-  const size_t per_cta = (size_t)tcx::kM * (3 * Hmax + 1);
-  T->scratch_set = per_cta * T->nsm;
-  if (cudaMalloc((void**)&T->d_scratch, T->scratch_set * sizeof(float2)) != cudaSuccess) return SPH_ENOMEM;
-  // kept A stages for GEMMs whose outputs take two passes of the K loop
-  for (int q = 0; q < 2; ++q)
-    for (int o = 0; o < 4; ++o)
-      if (T->pass[q].op[o].nh > 1) T->akeep_chunks = std::max(T->akeep_chunks, T->pass[q].op[o].KP / tcx::kKC);
-  T->akeep_set = (size_t)T->akeep_chunks * (tcx::kStageA / 16) * T->nsm;
-  if (T->akeep_chunks > 0 && cudaMalloc((void**)&T->d_akeep, T->akeep_set * sizeof(uint4)) != cudaSuccess)
-    return SPH_ENOMEM;
-  if (cudaFuncSetAttribute(tcx::tc_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcx::kSmemBytes) !=
-      cudaSuccess)
+  const size_t smax = std::max(T->pass[0].smem, T->pass[1].smem);
+  if (cudaFuncSetAttribute(tcx::tc_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax) != cudaSuccess)
     return SPH_ECUDA;
   return SPH_OK;
 }
@@ -782,40 +800,27 @@ void tc_free(sph_filter_plan_s* p) {
   TcPlan* T = p->tc;
   if (!T) return;
   for (TcPass& P : T->pass) {
-    cudaFree(P.d_tab);
-    cudaFree(P.d_h);
+    cudaFree(P.d_ops);
+    cudaFree(P.d_maps);
+    cudaFree(P.d_mu);
     cudaFree(P.d_list);
   }
-  cudaFree(T->d_scratch);
-  cudaFree(T->d_akeep);
-  cudaFree(T->d_scratch_pipe);
-  cudaFree(T->d_akeep_pipe);
   delete T;
   p->tc = nullptr;
 }
 
-sph_status tc_reserve_pipeline(sph_filter_plan_s* p) {
-  TcPlan* T = p->tc;
-  if (T->d_scratch_pipe) return SPH_OK;
-  if (cudaMalloc((void**)&T->d_scratch_pipe, 3 * T->scratch_set * sizeof(float2)) != cudaSuccess) return SPH_ENOMEM;
-  if (T->akeep_set && cudaMalloc((void**)&T->d_akeep_pipe, 3 * T->akeep_set * sizeof(uint4)) != cudaSuccess) {
-    cudaFree(T->d_scratch_pipe);
-    T->d_scratch_pipe = nullptr;
-    return SPH_ENOMEM;
-  }
-  return SPH_OK;
-}
+// The form keeps no scratch outside the kernel's shared and tensor memory: nothing to reserve.
+sph_status tc_reserve_pipeline(sph_filter_plan_s*) { return SPH_OK; }
 
 namespace {
 cudaError_t launch_pass(sph_filter_plan_s* p, int q, const double* src, double* dst, int var_begin, int var_count,
-                        cudaStream_t s, int set) {
+                        cudaStream_t s, int* nlaunch) {
   TcPlan* T = p->tc;
   TcPass& P = T->pass[q];
   const long long e0 = P.var_off[(size_t)var_begin], e1 = P.var_off[(size_t)(var_begin + var_count)];
   if (e1 <= e0) return cudaSuccess;
   tcx::TcArgs a{};
   a.pass = q;
-  a.L = P.L;
   a.Nr = p->Nr;
   a.Nth = p->Nth;
   a.Nph = p->Nph;
@@ -823,25 +828,25 @@ cudaError_t launch_pass(sph_filter_plan_s* p, int q, const double* src, double* 
   a.dst = dst;
   a.list = P.d_list + e0;
   a.nvec = q == 0 ? (e1 - e0) * (p->Nph / 2) : (e1 - e0);
-  a.h = P.d_h;
+  a.mu = P.d_mu;
   a.var = p->d_var;
-  for (int o = 0; o < 4; ++o) a.op[o] = P.op[o];
-  a.Ef = P.Ef;
-  a.Ei = P.Ei;
-  a.scratch = set == 0 ? T->d_scratch : T->d_scratch_pipe + (size_t)(set - 1) * T->scratch_set;
-  a.akeep = set == 0 ? T->d_akeep : (T->d_akeep_pipe ? T->d_akeep_pipe + (size_t)(set - 1) * T->akeep_set : nullptr);
-  a.akeep_chunks = T->akeep_chunks;
+  a.ops = P.d_ops;
+  a.maps = P.d_maps;
+  a.d = P.d;
   a.status = p->d_status;
-  const long long ntiles = (a.nvec + tcx::kM - 1) / tcx::kM;
-  const int grid = (int)std::min<long long>(ntiles, T->nsm);
-  tcx::tc_pass_kernel<<<grid, tcx::kThr, tcx::kSmemBytes, s>>>(a);
+  const long long ntiles = (a.nvec + tcx::kV - 1) / tcx::kV;
+  const int grid = (int)std::min<long long>(ntiles, (long long)T->nsm * P.ctas_per_sm);
+  tcx::tc_pass_kernel<<<grid, P.d.threads, P.smem, s>>>(a);
+  ++*nlaunch;
   return cudaGetLastError();
 }
 }  // namespace
 
 cudaError_t tc_launch(sph_filter_plan_s* p, const double* in, double* out, int transpose, int var_begin,
-                      int var_count, cudaStream_t s, int set) {
-  if (set < 0 || set > 3 || (set > 0 && !p->tc->d_scratch_pipe)) return cudaErrorInvalidValue;
+                      int var_count, cudaStream_t s, int, int* nlaunch) {
+  int dummy = 0;
+  if (!nlaunch) nlaunch = &dummy;
+  *nlaunch = 0;
   const size_t shell = (size_t)p->Nth * p->Nph, field = shell * p->Nr;
   if (!transpose) {
     // theta pass in -> out (identity shells copied), then the phi pass in place (Sec. II.C order)
@@ -856,9 +861,9 @@ cudaError_t tc_launch(sph_filter_plan_s* p, const double* in, double* out, int t
         if (e != cudaSuccess) return e;
       }
     }
-    const cudaError_t e = launch_pass(p, 0, in, out, var_begin, var_count, s, set);
+    const cudaError_t e = launch_pass(p, 0, in, out, var_begin, var_count, s, nlaunch);
     if (e != cudaSuccess) return e;
-    return launch_pass(p, 1, out, out, var_begin, var_count, s, set);
+    return launch_pass(p, 1, out, out, var_begin, var_count, s, nlaunch);
   }
   // transpose: phi pass, then theta pass, both in place on out
   if (in != out) {
@@ -866,9 +871,9 @@ cudaError_t tc_launch(sph_filter_plan_s* p, const double* in, double* out, int t
                                           sizeof(double) * field * var_count, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return e;
   }
-  const cudaError_t e = launch_pass(p, 1, out, out, var_begin, var_count, s, set);
+  const cudaError_t e = launch_pass(p, 1, out, out, var_begin, var_count, s, nlaunch);
   if (e != cudaSuccess) return e;
-  return launch_pass(p, 0, out, out, var_begin, var_count, s, set);
+  return launch_pass(p, 0, out, out, var_begin, var_count, s, nlaunch);
 }
 
 }  // namespace sph

@@ -44,12 +44,20 @@ def test_batch_matches_single_plans(torch_cuda):
     torch.cuda.synchronize()
     for p, x, o in zip(plans, xs, outs):
         assert torch.equal(o, p.apply(x))
-    # oracle on the smallest grid and one shell of the others
+    # every grid against the oracle: all shells of the smallest, sampled shells of every field class
+    # of the others (each shell normalised by the largest reference value of its field's samples)
     g0 = grids[0]
     ref = oracle.filter(xs[0].cpu().numpy(), g0.parity, g0.kind, g0.L, g0.r, g0.dr_min, g0.floor)
     y0 = outs[0].cpu().numpy()
     err = max(np.abs(y0[v] - ref[v]).max() / np.abs(ref[v]).max() for v in range(g0.nvars))
     assert err <= 1e-13
+    for n in range(1, len(grids)):
+        g, x, y = grids[n], xs[n].cpu().numpy(), outs[n].cpu().numpy()
+        shells = [(v, i) for v in (0, 14, 18, 20, 24, 26) for i in sorted({0, g.Nr - 1})]
+        refs = oracle.filter_shells(x, shells, g.parity, g.kind, g.L, g.r, g.dr_min, g.floor)
+        fmax = {v: max(np.abs(refs[k]).max() for k, s in enumerate(shells) if s[0] == v) for v, _ in shells}
+        errs = [np.abs(y[v, i] - refs[k]).max() / fmax[v] for k, (v, i) in enumerate(shells)]
+        assert max(errs) <= 1e-13, (n, shells[int(np.argmax(errs))], max(errs))
 
 
 def test_graph_replay_three_substeps(torch_cuda):
