@@ -42,11 +42,11 @@ namespace sph {
 namespace tcx {
 
 constexpr long long kWaitLimit = 1LL << 24;  // bounded mbarrier polls (about a second at most)
-constexpr int kMaxChunks = 4;                // 8-value chunks per thread and row in the mid step
+constexpr int kMaxChunks = 3;                // 8-value chunks per thread and row in the mid step
 
 struct RowInfo {
   long long base;                  // offset of the vector's element 0 in the state (circle: meridian k)
-  const unsigned long long* mu;    // the vector's multipliers mu_m 2^62, m = 0 .. L/2
+  const uint2* mu;                 // the vector's multipliers mu_m as (mu 2^30, low bits 2^60), m = 0 .. L/2
   int neg;                         // theta circles of odd fields: the second meridian carries -1
   int valid;
 };
@@ -58,10 +58,15 @@ struct TcArgs {
   double* dst;                     // may equal src; only the pass's vectors are written
   const int* list;                 // theta: active shells v*Nr+i; phi: active rings (v*Nr+i)*Nth+j
   long long nvec;                  // theta: entries * Nph/2; phi: entries
-  const unsigned long long* mu;    // theta: [ncls][Nr][Nth+1]; phi: [ncls][Nr][Nth][Nph/2+1]
+  const uint2* mu;                 // theta: [ncls][Nr][Nth+1]; phi: [ncls][Nr][Nth][Nph/2+1]
   const VarInfo* var;
   const unsigned char* ops;        // operator blob (global), layout of PassDesc
-  const int16_t* maps;             // index maps (global)
+  // direct form (theta pass, tiles inside one shell): per (class, radius) block matrices
+  // U^T diag(mu) U; dop_off / dpb [(cls * Nr + i) * ngemm + g]: byte offset in dops, scale bits
+  int direct;
+  const unsigned char* dops;
+  const uint32_t* dop_off;
+  const int8_t* dpb;
   PassDesc d;
   unsigned* status;
 };
@@ -70,7 +75,7 @@ struct Ctl {
   RowInfo row[kV];
   int vexp[kV];                    // largest biased FP64 exponent of each vector
   int rowbl[kM];                   // bit length of the largest |value| of a GEMM row
-  int sh_in[kM], sh_mid[kM];       // per-row shifts of the two slicings
+  int sh_mid[kM];                  // per-row shift of the mid-step slicing
   unsigned long long op_bar, mma_bar;
   uint32_t tslot;
   int abort;
@@ -92,7 +97,8 @@ __device__ __forceinline__ uint32_t make_idesc(int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Bounded wait on an mbarrier phase; gives up early once another thread has set *abort.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* abort) {
   for (long long it = 0; it < kWaitLimit; ++it) {
     uint32_t ok;
     asm volatile(
@@ -101,6 +107,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (ok) return true;
+    if ((it & 1023) == 1023 && *abort) return false;
   }
   return false;
 }
@@ -151,28 +158,33 @@ __device__ __forceinline__ double from_fixed(long long v, int expo) {
   return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) | (r & 0xFFFFFFFFFFFFFULL)));
 }
 
-// Exact FP32 integer (|f| < 2^22) to int; a fractional f is rounded to nearest.
-__device__ __forceinline__ int f2i(float f) { return __float_as_int(__fadd_rn(f, 12582912.0f)) - 0x4B400000; }
-
-// The GEMM result from the five accumulators: sum_t acc_t 2^(80 - 8t - Pb), acc 4 holding diagonal 4
-// plus diagonal 5 / 256.
-__device__ __forceinline__ long long combine5(float a0, float a1, float a2, float a3, float a4, int Pb) {
-  const long long hi = (long long)(f2i(a0) * 256 + f2i(a1));
-  const long long lo = (long long)(f2i(a2) * 256 + f2i(a3));
-  return (hi << (72 - Pb)) + (lo << (56 - Pb)) + ((long long)f2i(a4) << (48 - Pb));
+// The GEMM result from the five accumulators, sum_t acc_t 2^(80 - 8t - Pb), acc 4 holding diagonal 4
+// plus diagonal 5 / 256. Each accumulator is an integer below 2^22 (acc 4 rounded to one): adding
+// 1.5 2^23 leaves it in the low mantissa bits; m[0..2] = 2^(72 - Pb), 2^(56 - Pb), 2^(48 - Pb).
+__device__ __forceinline__ long long combine5(float a0, float a1, float a2, float a3, float a4, const int m[3]) {
+  const unsigned b0 = (unsigned)__float_as_int(__fadd_rn(a0, 12582912.0f));
+  const unsigned b1 = (unsigned)__float_as_int(__fadd_rn(a1, 12582912.0f));
+  const unsigned b2 = (unsigned)__float_as_int(__fadd_rn(a2, 12582912.0f));
+  const unsigned b3 = (unsigned)__float_as_int(__fadd_rn(a3, 12582912.0f));
+  const unsigned b4 = (unsigned)__float_as_int(__fadd_rn(a4, 12582912.0f));
+  const unsigned kM257 = 257u * 0x4B400000u;  // (b - M) 256 + (b' - M) = 256 b + b' - 257 M (mod 2^32)
+  const int hi = (int)(b0 * 256u + b1 - kM257);
+  const int lo = (int)(b2 * 256u + b3 - kM257);
+  const int i4 = (int)(b4 - 0x4B400000u);
+  return (long long)hi * m[0] + (long long)lo * m[1] + (long long)i4 * m[2];
 }
 
-// d mu / 2^62 (floor), mu <= 2^62.
-__device__ __forceinline__ long long mul_mu(long long d, unsigned long long mu) {
-  const long long hi = __mul64hi(d, (long long)mu);
-  const unsigned long long lo = (unsigned long long)d * mu;
-  return (long long)(((unsigned long long)hi << 2) | (lo >> 62));
+// d mu for mu = mh 2^-30 + ml 2^-60 (mh <= 2^30, ml < 2^30), with 32-bit limbs of d; the dropped
+// low-by-low product is below 4 units of d.
+__device__ __forceinline__ long long mul_mu(long long d, uint2 mu) {
+  const int dh = (int)(d >> 32);
+  const unsigned dl = (unsigned)d;
+  const long long t1 = (long long)dh * (int)mu.x;                    // 2^2 weight
+  const unsigned long long t2 = (unsigned long long)dl * mu.x;       // 2^-30 weight
+  const long long t3 = (long long)dh * (int)mu.y;                    // 2^-28 weight
+  return (t1 << 2) + (long long)(t2 >> 30) + (t3 >> 28);
 }
 
-__device__ __forceinline__ long long shift_round(long long v, int s) {  // v 2^s, rounded
-  if (s >= 0) return v << s;
-  return (v + (1LL << (-s - 1))) >> (-s);
-}
 
 __device__ __forceinline__ int bitlen(unsigned long long v) { return v ? 64 - __clzll((long long)v) : 0; }
 
@@ -227,74 +239,88 @@ struct Kern {
   Ctl& C;
   unsigned char* opbuf;      // operator buffer (shared)
   long long* store;          // [kV][pitch] fixed-point store
-  const int16_t* maps;       // index maps (shared)
   int pitch;
   uint32_t tmem;
   int tid, warp, lane, lq, cp, WQ, r, h, v;   // thread role in the GEMM phases: row r = 32 lq + lane
   uint32_t op_phase, mma_phase;
 };
 
-// Issue the MMAs of one GEMM: D (columns N) = A (tensor memory, K) x B^T (shared, N x K), 21 digit
-// pairs, 5 accumulators; then commit to the MMA barrier. One thread.
+// One tcgen05.mma (kind::f16, A in tensor memory, B in shared memory): D = A B^T (+ D) or, with the
+// input scaling, D = A B^T + D 2^-8.
+__device__ __forceinline__ void mma_first(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc) {
+  asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, 0, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+               "r"(a), "l"(b), "r"(idesc));
+}
+__device__ __forceinline__ void mma_acc(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc) {
+  asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, 1, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+               "r"(a), "l"(b), "r"(idesc));
+}
+__device__ __forceinline__ void mma_acc_scaled(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc) {
+  asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, 1, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p, 8;\n\t}" ::"r"(d),
+               "r"(a), "l"(b), "r"(idesc));
+}
+
+// Issue the MMAs of one GEMM: D (columns N) = A (tensor memory, K = 16 NKS) x B^T (shared, N x K),
+// the 21 digit pairs a + b <= 5 into 5 accumulators (diagonals 5 and 4 first, into accumulator 4,
+// the first diagonal-4 product scaling the diagonal-5 sum by 2^-8), then commit to the MMA barrier.
+// One thread; every address is a compile-time offset from the bases.
+template <int NKS>
+__device__ __forceinline__ void issue_gemm_t(uint32_t tmem, uint32_t acc0, int KAh, int NA, uint64_t bd0,
+                                             uint32_t slice16, uint32_t idesc) {
+#pragma unroll
+  for (int t = 5; t >= 0; --t) {
+    const uint32_t dcol = acc0 + (uint32_t)((t >= 4 ? 4 : t) * NA);
+#pragma unroll
+    for (int s = 0; s < NKS; ++s)
+#pragma unroll
+      for (int a = 0; a <= t; ++a) {
+        const int b = t - a;
+        const uint32_t acol = tmem + (uint32_t)(a * KAh + s * 8);
+        const uint64_t bd = bd0 + (uint64_t)((uint32_t)b * slice16 + (uint32_t)s * 16u);
+        if (s == 0 && a == 0 && (t == 5 || t <= 3)) mma_first(dcol, acol, bd, idesc);
+        else if (s == 0 && a == 0 && t == 4) mma_acc_scaled(dcol, acol, bd, idesc);
+        else mma_acc(dcol, acol, bd, idesc);
+      }
+  }
+}
+
 __device__ void issue_gemm(Kern& k, int K, int N) {
   const PassDesc& d = k.A.d;
   const uint32_t idesc = make_idesc(N);
-  const uint32_t sliceB = (uint32_t)(N * K * 2);
-  const uint32_t b0 = su32(k.opbuf);
+  const uint32_t slice16 = (uint32_t)(N * K * 2) >> 4;
+  const uint64_t bd0 = make_desc(su32(k.opbuf), K);
   const uint32_t acc0 = k.tmem + (uint32_t)(3 * d.KA);
-  const int nks = K / 16;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll 1
-  for (int t = 5; t >= 0; --t) {
-    const int acc = t >= 4 ? 4 : t;
-    const uint32_t dcol = acc0 + (uint32_t)(acc * d.NA);
-#pragma unroll 1
-    for (int s = 0; s < nks; ++s)
-#pragma unroll 1
-      for (int a = 0; a <= t; ++a) {
-        const int b = t - a;
-        if (b >= kS || a >= kS) continue;
-        const bool first = s == 0 && a == 0 && (t == 5 || t <= 3);
-        const bool scaled = s == 0 && a == 0 && t == 4;
-        const uint32_t acol = k.tmem + (uint32_t)(a * (d.KA / 2) + s * 8);
-        const uint64_t bd = make_desc(b0 + (uint32_t)b * sliceB + (uint32_t)s * 256, K);
-        const uint32_t en = first ? 0u : 1u;
-        if (scaled)
-          asm volatile(
-              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-              "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p, 8;\n\t}" ::"r"(dcol),
-              "r"(acol), "l"(bd), "r"(idesc), "r"(en));
-        else
-          asm volatile(
-              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-              "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(dcol),
-              "r"(acol), "l"(bd), "r"(idesc), "r"(en));
-      }
+  switch (K / 16) {
+    case 1: issue_gemm_t<1>(k.tmem, acc0, d.KA / 2, d.NA, bd0, slice16, idesc); break;
+    case 2: issue_gemm_t<2>(k.tmem, acc0, d.KA / 2, d.NA, bd0, slice16, idesc); break;
+    case 3: issue_gemm_t<3>(k.tmem, acc0, d.KA / 2, d.NA, bd0, slice16, idesc); break;
+    default: issue_gemm_t<4>(k.tmem, acc0, d.KA / 2, d.NA, bd0, slice16, idesc); break;
   }
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(&k.C.mma_bar))
                : "memory");
 }
 
-// Runs one GEMM: waits for the operator, issues (thread 0), waits for completion (all threads).
-// Returns false if a wait ran out.
-__device__ bool run_gemm(Kern& k, int K, int N) {
-  // A operand written by every thread: make it visible to the tensor core
+// Runs one GEMM: a barrier (every thread's A operand and its reads of the previous GEMM's
+// accumulators are done), thread 0 waits for the operator, issues and waits for the completion,
+// and a second barrier releases the others (who sleep at it instead of polling). A wait that runs
+// out sets `abort`.
+__device__ void run_gemm(Kern& k, int K, int N) {
   tmem_wait_st();
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  bool ok = true;
   if (k.tid == 0) {
-    ok = mbar_wait(su32(&k.C.op_bar), k.op_phase & 1u);
-    if (ok) issue_gemm(k, K, N);
-    else atomicExch(&k.C.abort, 1);
+    if (!k.C.abort && mbar_wait(su32(&k.C.op_bar), k.op_phase & 1u, &k.C.abort)) {
+      issue_gemm(k, K, N);
+      if (!mbar_wait(su32(&k.C.mma_bar), k.mma_phase & 1u, &k.C.abort)) k.C.abort = 1;
+    } else {
+      k.C.abort = 1;
+    }
   }
   k.op_phase++;
-  __syncthreads();
-  if (k.C.abort) return false;
-  ok = mbar_wait(su32(&k.C.mma_bar), k.mma_phase & 1u);
   k.mma_phase++;
+  __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  return __syncthreads_and(ok ? 1 : 0) != 0;
 }
 
 // Slices 8 values of row r into the A region at K offset k0 (6 slices).
@@ -306,47 +332,31 @@ __device__ __forceinline__ void put_a(const Kern& k, const long long vals[8], in
   for (int a = 0; a < kS; ++a) tmem_st4(lane_base + (uint32_t)(a * (k.A.d.KA / 2) + k0 / 2), w[a]);
 }
 
-// Prologue: the GEMM's input coordinates of row r, brought to 46 bits, as the A operand.
+// Prologue: the GEMM's input coordinates of row r, shifted right by the block's bound (|c| < 2^(F +
+// growth) becomes |A| < 2^46), as the A operand.
 __device__ void prologue(Kern& k, const GemmDesc& g) {
-  const int16_t* kin = k.maps + g.kin_off + k.h * g.Kc;
-  const bool act = k.C.row[k.v].valid && (k.h == 0 || g.rows2);
-  const long long* srow = k.store + (size_t)k.v * k.pitch;
-  unsigned long long orv = 0;
+  const int cnt = k.C.row[k.v].valid ? g.cnt[k.h] : 0;
+  const long long* srow = k.store + (size_t)k.v * k.pitch + g.ka[k.h];
+  const int ks = g.ks[k.h];
   const int nch = g.Kc / 8;
-  if (act)
-    for (int c = k.cp; c < nch; c += k.WQ)
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int idx = kin[8 * c + i];
-        const long long x = idx >= 0 ? srow[idx] : 0;
-        orv |= (unsigned long long)(x ^ (x >> 63));
-      }
-  if (orv) atomicMax(&k.C.rowbl[k.r], bitlen(orv));
-  __syncthreads();
-  const int bl = k.C.rowbl[k.r];
-  const int sh = bl ? 46 - bl : 0;
   for (int c = k.cp; c < nch; c += k.WQ) {
     long long vals[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const int idx = act ? kin[8 * c + i] : -1;
-      vals[i] = idx >= 0 ? shift_round(srow[idx], sh) : 0;
+      const int kk = 8 * c + i;
+      vals[i] = kk < cnt ? (srow[ks * kk] >> g.rin) : 0;
     }
     put_a(k, vals, 8 * c);
-  }
-  __syncthreads();  // every thread has read rowbl
-  if (k.cp == 0) {
-    k.C.sh_in[k.r] = sh;
-    k.C.rowbl[k.r] = 0;
   }
 }
 
 // Mid step: forward GEMM result -> times mu_m -> rescaled per row -> the inverse GEMM's A operand.
 __device__ void mid_step(Kern& k, const GemmDesc& g) {
-  const int16_t* mode = k.maps + g.mode_off + k.h * g.Km;
-  const bool act = k.C.row[k.v].valid && (k.h == 0 || g.rows2);
-  const unsigned long long* mu = k.C.row[k.v].mu;
+  const int cnt = k.C.row[k.v].valid ? g.cnt[k.h] : 0;
+  const uint2* mu = k.C.row[k.v].mu + g.ma[k.h];
+  const int ms = g.ms[k.h];
   const int coff = g.concat ? k.h * g.Km : 0;
+  const int mlt[3] = {1 << (72 - g.Pb), 1 << (56 - g.Pb), 1 << (48 - g.Pb)};
   const uint32_t lane_base = k.tmem + ((uint32_t)(32 * k.lq) << 16);
   const uint32_t accb = lane_base + (uint32_t)(3 * k.A.d.KA);
   const int nch = g.Km / 8;
@@ -362,11 +372,11 @@ __device__ void mid_step(Kern& k, const GemmDesc& g) {
       tmem_wait_ld();
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        const int m = act ? mode[8 * c + i] : -1;
+        const int j = 8 * c + i;
         long long yy = 0;
-        if (m >= 0) {
-          const long long dd = combine5(f[0][i], f[1][i], f[2][i], f[3][i], f[4][i], g.Pb);
-          yy = mul_mu(dd, __ldg(mu + m));
+        if (j < cnt) {
+          const long long dd = combine5(f[0][i], f[1][i], f[2][i], f[3][i], f[4][i], mlt);
+          yy = mul_mu(dd, __ldg(mu + ms * j));
         }
         y[ci][i] = yy;
         orv |= (unsigned long long)(yy ^ (yy >> 63));
@@ -375,116 +385,150 @@ __device__ void mid_step(Kern& k, const GemmDesc& g) {
   }
   if (orv) atomicMax(&k.C.rowbl[k.r], bitlen(orv));
   __syncthreads();
+  // |Y| brought to 46 bits, but never scaled up by more than the prologue's right shift, so that
+  // the epilogue's shift back to the store's unit is a left shift
   const int bl = k.C.rowbl[k.r];
-  const int sm = bl ? 46 - bl : 0;
+  const int sm = min(g.rin, bl ? 46 - bl : g.rin);
 #pragma unroll
   for (int ci = 0; ci < kMaxChunks; ++ci) {
     const int c = k.cp + ci * k.WQ;
     if (c < nch) {
       long long vals[8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) vals[i] = shift_round(y[ci][i], sm);
+      for (int i = 0; i < 8; ++i) vals[i] = sm >= 0 ? (y[ci][i] << sm) : (y[ci][i] >> (-sm));
       put_a(k, vals, 8 * c);
     }
   }
-  __syncthreads();
-  if (k.cp == 0) {
-    k.C.sh_mid[k.r] = sm;
-    k.C.rowbl[k.r] = 0;
-  }
+  if (k.cp == 0) k.C.sh_mid[k.r] = sm;
 }
 
-// Epilogue: the inverse GEMM's result W (units 2^-(sh_in + sh_mid) of the store) subtracted from the
+// Epilogue: the inverse GEMM's result W (units 2^(rin - sh_mid) of the store) subtracted from the
 // stored coordinates.
 __device__ void epilogue(Kern& k, const GemmDesc& g) {
-  const int16_t* kin = k.maps + g.kin_off + k.h * g.Kc;
-  const bool act = k.C.row[k.v].valid && (k.h == 0 || g.rows2);
+  const int cnt = k.C.row[k.v].valid ? g.cnt[k.h] : 0;
+  const int ks = g.ks[k.h];
   const int coff = g.concat ? k.h * g.Kc : 0;
   const uint32_t lane_base = k.tmem + ((uint32_t)(32 * k.lq) << 16);
   const uint32_t accb = lane_base + (uint32_t)(3 * k.A.d.KA);
-  const int tot = -(k.C.sh_in[k.r] + k.C.sh_mid[k.r]);
-  long long* srow = k.store + (size_t)k.v * k.pitch;
+  const int mlt[3] = {1 << (72 - g.Pb), 1 << (56 - g.Pb), 1 << (48 - g.Pb)};
+  const int up = g.rin - k.C.sh_mid[k.r];  // >= 0
+  if (k.cp == 0) k.C.rowbl[k.r] = 0;         // every thread read it before the inverse GEMM's barrier
+  long long* srow = k.store + (size_t)k.v * k.pitch + g.ka[k.h];
   const int nch = g.Kc / 8;
   for (int c = k.cp; c < nch; c += k.WQ) {
     float f[5][8];
 #pragma unroll
     for (int t = 0; t < 5; ++t) tmem_ld8(accb + (uint32_t)(t * k.A.d.NA + coff + 8 * c), f[t]);
     tmem_wait_ld();
-    if (!act) continue;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const int idx = kin[8 * c + i];
-      if (idx < 0) continue;
-      const long long w = combine5(f[0][i], f[1][i], f[2][i], f[3][i], f[4][i], g.Pb);
-      srow[idx] -= shift_round(w, tot);
+      const int kk = 8 * c + i;
+      if (kk >= cnt) continue;
+      const long long w = combine5(f[0][i], f[1][i], f[2][i], f[3][i], f[4][i], mlt);
+      srow[ks * kk] -= w << up;
     }
+  }
+}
+
+// Epilogue of the direct form: the GEMM's result W = K A (units 2^rin of the store) subtracted from
+// the stored coordinates.
+__device__ void epilogue_direct(Kern& k, const GemmDesc& g, int Pb) {
+  const int cnt = k.C.row[k.v].valid ? g.cnt[k.h] : 0;
+  const int ks = g.ks[k.h];
+  const int coff = g.concat ? k.h * g.Kc : 0;
+  const uint32_t lane_base = k.tmem + ((uint32_t)(32 * k.lq) << 16);
+  const uint32_t accb = lane_base + (uint32_t)(3 * k.A.d.KA);
+  const int mlt[3] = {1 << (72 - Pb), 1 << (56 - Pb), 1 << (48 - Pb)};
+  long long* srow = k.store + (size_t)k.v * k.pitch + g.ka[k.h];
+  const int nch = g.Kc / 8;
+  for (int c = k.cp; c < nch; c += k.WQ) {
+    float f[5][8];
+#pragma unroll
+    for (int t = 0; t < 5; ++t) tmem_ld8(accb + (uint32_t)(t * k.A.d.NA + coff + 8 * c), f[t]);
+    tmem_wait_ld();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int kk = 8 * c + i;
+      if (kk >= cnt) continue;
+      const long long w = combine5(f[0][i], f[1][i], f[2][i], f[3][i], f[4][i], mlt);
+      srow[ks * kk] -= w << g.rin;
+    }
+  }
+}
+
+// Runs f(v, p) for every vector v of the tile and p < count, without divisions: theta circles take
+// the vector from the thread (consecutive threads, consecutive circles: coalesced meridian rows),
+// rings one warp per vector (consecutive lanes, consecutive positions).
+template <class Fn>
+__device__ __forceinline__ void for_tasks(const Kern& k, int count, Fn f) {
+  if (k.A.pass == 0) {
+    const int v = k.tid & (kV - 1);
+    for (int p = k.tid >> 6; p < count; p += (int)(blockDim.x >> 6)) f(v, p);
+  } else {
+    for (int v = k.warp; v < kV; v += (int)(blockDim.x >> 5))
+      for (int p = k.lane; p < count; p += 32) f(v, p);
   }
 }
 
 // In-place level stage (forward) on the first n entries of every vector's store.
 __device__ void level_fwd(Kern& k, int n, bool convert) {
   const int q = n / 4;
-  const int ntask = kV * q;
-  for (int t = k.tid; t < ntask; t += blockDim.x) {
-    int v, p;
-    if (k.A.pass == 0) { v = t % kV; p = t / kV; }
-    else { p = t % q; v = t / q; }
+  for_tasks(k, q, [&](int v, int p) {
     long long* s = k.store + (size_t)v * k.pitch;
     long long vp = s[p], vq = s[p + n / 2], vr = s[n / 2 - 1 - p], vs = s[n - 1 - p];
     if (convert) {
+      // the outermost level reads the raw FP64 values; on a theta circle positions p + n/2 and
+      // n - 1 - p lie on the second meridian, which carries the field's parity sign
       const int base = 53 - k.A.d.F + k.C.vexp[v];
+      const bool neg = k.A.pass == 0 && k.C.row[v].neg;
       vp = to_fixed(vp, base);
       vq = to_fixed(vq, base);
       vr = to_fixed(vr, base);
       vs = to_fixed(vs, base);
+      if (neg) {
+        vq = -vq;
+        vs = -vs;
+      }
     }
     const long long e0 = vp + vq, z0 = vp - vq, e1 = vr + vs, z1 = vr - vs;
     s[p] = e0;
     s[n / 2 - 1 - p] = e1;
     s[n / 2 + p] = z0 - z1;
     s[n - 1 - p] = z0 + z1;
-  }
+  });
 }
 
 __device__ void base_fwd(Kern& k, int nb, bool convert) {
-  const int hb = nb / 2;
-  const int ntask = kV * hb;
-  for (int t = k.tid; t < ntask; t += blockDim.x) {
-    int v, p;
-    if (k.A.pass == 0) { v = t % kV; p = t / kV; }
-    else { p = t % hb; v = t / hb; }
+  for_tasks(k, nb / 2, [&](int v, int p) {
     long long* s = k.store + (size_t)v * k.pitch;
     long long a = s[p], b = s[nb - 1 - p];
     if (convert) {
+      // no levels: nb = L; on a theta circle position nb - 1 - p is on the second meridian
       const int base = 53 - k.A.d.F + k.C.vexp[v];
       a = to_fixed(a, base);
       b = to_fixed(b, base);
+      if (k.A.pass == 0 && k.C.row[v].neg) b = -b;
     }
     s[p] = a + b;
     s[nb - 1 - p] = a - b;
-  }
+  });
 }
 
-// Writes value x (scaled by 2^expo) of position q of vector v to the destination state.
+// Writes value x (scaled by 2^expo) of position q of vector v to the destination state (the
+// parity sign of a circle's second meridian applied to the integer).
 __device__ __forceinline__ void put_out(const Kern& k, int v, int q, long long x, int expo) {
   const RowInfo& R = k.C.row[v];
-  double y = from_fixed(x, expo);
-  if (k.A.pass == 0 && R.neg && q >= k.A.Nth) y = -y;
-  k.A.dst[elem_off(k.A, R.base, q)] = y;
+  if (k.A.pass == 0 && R.neg && q >= k.A.Nth) x = -x;
+  k.A.dst[elem_off(k.A, R.base, q)] = from_fixed(x, expo);
 }
 
 // Inverse base stage: values become 2 v; `out` writes them to the destination (no levels).
 __device__ void base_inv(Kern& k, int nb, bool out) {
-  const int hb = nb / 2;
-  const int ntask = kV * hb;
-  for (int t = k.tid; t < ntask; t += blockDim.x) {
-    int v, p;
-    if (k.A.pass == 0) { v = t % kV; p = t / kV; }
-    else { p = t % hb; v = t / hb; }
+  for_tasks(k, nb / 2, [&](int v, int p) {
     long long* s = k.store + (size_t)v * k.pitch;
     const long long a = s[p], b = s[nb - 1 - p];
     if (out) {
-      if (!k.C.row[v].valid) continue;
+      if (!k.C.row[v].valid) return;
       const int expo = (k.C.vexp[v] - 1022) - k.A.d.F - 1;
       put_out(k, v, p, a + b, expo);
       put_out(k, v, nb - 1 - p, a - b, expo);
@@ -492,24 +536,19 @@ __device__ void base_inv(Kern& k, int nb, bool out) {
       s[p] = a + b;
       s[nb - 1 - p] = a - b;
     }
-  }
+  });
 }
 
 // Inverse level stage for the level of length n, with the T-even part scaled by 2^sc (sc >= 1);
 // results scaled by 2^(sc + 1). `out` writes them to the destination (outermost level).
 __device__ void level_inv(Kern& k, int n, int sc, bool out) {
-  const int q = n / 4;
-  const int ntask = kV * q;
-  for (int t = k.tid; t < ntask; t += blockDim.x) {
-    int v, p;
-    if (k.A.pass == 0) { v = t % kV; p = t / kV; }
-    else { p = t % q; v = t / q; }
+  for_tasks(k, n / 4, [&](int v, int p) {
     long long* s = k.store + (size_t)v * k.pitch;
     const long long E0 = s[p], E1 = s[n / 2 - 1 - p], a = s[n / 2 + p], o = s[n - 1 - p];
     const long long zp = (o + a) << (sc - 1), zq = (o - a) << (sc - 1);
     const long long y0 = E0 + zp, y1 = E0 - zp, y2 = E1 + zq, y3 = E1 - zq;
     if (out) {
-      if (!k.C.row[v].valid) continue;
+      if (!k.C.row[v].valid) return;
       const int expo = (k.C.vexp[v] - 1022) - k.A.d.F - (sc + 1);
       put_out(k, v, p, y0, expo);
       put_out(k, v, p + n / 2, y1, expo);
@@ -521,7 +560,7 @@ __device__ void level_inv(Kern& k, int n, int sc, bool out) {
       s[n / 2 - 1 - p] = y2;
       s[n - 1 - p] = y3;
     }
-  }
+  });
 }
 
 __global__ void __launch_bounds__(512, 1) tc_pass_kernel(const __grid_constant__ TcArgs A) {
@@ -531,8 +570,7 @@ __global__ void __launch_bounds__(512, 1) tc_pass_kernel(const __grid_constant__
   const int pitch = L + 1;
   unsigned char* opbuf = smem;
   long long* store = reinterpret_cast<long long*>(smem + ((d.op_max + 1023) / 1024) * 1024);
-  int16_t* maps = reinterpret_cast<int16_t*>(store + (size_t)kV * pitch);
-  Ctl& C = *reinterpret_cast<Ctl*>(reinterpret_cast<unsigned char*>(maps) + ((d.nmap * 2 + 15) / 16) * 16);
+  Ctl& C = *reinterpret_cast<Ctl*>(store + (size_t)kV * pitch);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&C.tslot)),
@@ -545,12 +583,11 @@ __global__ void __launch_bounds__(512, 1) tc_pass_kernel(const __grid_constant__
     asm volatile("fence.mbarrier_init.release.cluster;");
     C.abort = 0;
   }
-  for (int i = tid; i < d.nmap; i += blockDim.x) maps[i] = A.maps[i];
   for (int i = tid; i < kM; i += blockDim.x) C.rowbl[i] = 0;
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  Kern k{A, C, opbuf, store, maps, pitch, C.tslot, tid, warp, lane, warp & 3, warp >> 2, (int)(blockDim.x / 128),
+  Kern k{A, C, opbuf, store, pitch, C.tslot, tid, warp, lane, warp & 3, warp >> 2, (int)(blockDim.x / 128),
          0, 0, 0, 0u, 0u};
   k.r = 32 * k.lq + lane;
   k.h = k.r >> 6;
@@ -558,8 +595,19 @@ __global__ void __launch_bounds__(512, 1) tc_pass_kernel(const __grid_constant__
   const long long ntiles = (A.nvec + kV - 1) / kV;
   bool ok = true;
   for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-    // the first operator of the tile (the buffer is free: the previous tile's GEMMs completed)
-    if (tid == 0) bulk_load(opbuf, A.ops + d.g[0].fwd_off, d.g[0].fwd_bytes, su32(&C.op_bar));
+    // the first operator of the tile (the buffer is free: the previous tile's GEMMs completed); the
+    // direct form's operators are those of the tile's (class, radius): every vector of a tile lies
+    // in one shell
+    int dci = 0;
+    if (A.direct) {
+      const int shell = A.list[(tile * kV) / (A.Nph / 2)];
+      const int vv = shell / A.Nr, i = shell - vv * A.Nr;
+      dci = (A.var[vv].cls * A.Nr + i) * d.ngemm;
+    }
+    if (tid == 0) {
+      if (A.direct) bulk_load(opbuf, A.dops + A.dop_off[dci], d.g[0].Kc * (d.g[0].concat ? 2 : 1) * d.g[0].Kc * 2 * kS, su32(&C.op_bar));
+      else bulk_load(opbuf, A.ops + d.g[0].fwd_off, d.g[0].fwd_bytes, su32(&C.op_bar));
+    }
     if (tid < kV) {
       RowInfo R{};
       const long long vg = tile * kV + tid;
@@ -588,35 +636,29 @@ __global__ void __launch_bounds__(512, 1) tc_pass_kernel(const __grid_constant__
       C.vexp[tid] = 0;
     }
     __syncthreads();
-    // load: raw FP64 values (parity sign applied) and each vector's largest exponent
-    if (A.pass == 0) {
-      const int v = tid % kV;
+    // load: raw FP64 values by asynchronous 8-byte copies (all of a thread's copies in flight at
+    // once), then each vector's largest exponent
+    const int L2 = L;
+    for_tasks(k, L2, [&](int v, int q) {
       const RowInfo& R = C.row[v];
+      if (!R.valid) return;
+      const double* g = A.src + elem_off(A, R.base, q);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(su32(store + (size_t)v * pitch + q)), "l"(g)
+                   : "memory");
+    });
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+    if (A.pass == 0) {
       int e = 0;
-      for (int q = tid / kV; q < L; q += blockDim.x / kV) {
-        long long b = 0;
-        if (R.valid) {
-          b = __double_as_longlong(A.src[elem_off(A, R.base, q)]);
-          if (R.neg && q >= A.Nth) b ^= (long long)0x8000000000000000ULL;
-          e = max(e, (int)((b >> 52) & 0x7FF));
-        }
-        store[(size_t)v * pitch + q] = b;
-      }
-      atomicMax(&C.vexp[v], e);
+      for_tasks(k, L2, [&](int v, int q) {
+        e = max(e, (int)((store[(size_t)v * pitch + q] >> 52) & 0x7FF));
+      });
+      atomicMax(&C.vexp[tid & (kV - 1)], e);
     } else {
       for (int v = warp; v < kV; v += blockDim.x / 32) {
-        const RowInfo& R = C.row[v];
         int e = 0;
-        for (int q = lane; q < L; q += 32) {
-          long long b = 0;
-          if (R.valid) {
-            b = __double_as_longlong(A.src[R.base + q]);
-            e = max(e, (int)((b >> 52) & 0x7FF));
-          }
-          store[(size_t)v * pitch + q] = b;
-        }
+        for (int q = lane; q < L; q += 32) e = max(e, (int)((store[(size_t)v * pitch + q] >> 52) & 0x7FF));
         e = __reduce_max_sync(0xffffffffu, e);
-        if (lane == 0) C.vexp[v] = e;
+        if (lane == 0) C.vexp[v] = C.row[v].valid ? e : 0;
       }
     }
     __syncthreads();
@@ -630,21 +672,32 @@ __global__ void __launch_bounds__(512, 1) tc_pass_kernel(const __grid_constant__
       base_fwd(k, d.nb, d.nl == 0);
       __syncthreads();
     }
-    // block GEMM pairs
-    for (int gi = 0; gi < d.ngemm && ok; ++gi) {
+    // block GEMMs: the direct form, one per block
+    for (int gi = 0; gi < d.ngemm && A.direct; ++gi) {
+      const GemmDesc& g = d.g[gi];
+      const int N = g.concat ? 2 * g.Kc : g.Kc;
+      prologue(k, g);
+      run_gemm(k, g.Kc, N);
+      if (tid == 0 && gi + 1 < d.ngemm) {
+        const GemmDesc& g2 = d.g[gi + 1];
+        bulk_load(opbuf, A.dops + A.dop_off[dci + gi + 1], g2.Kc * (g2.concat ? 2 : 1) * g2.Kc * 2 * kS, su32(&C.op_bar));
+      }
+      epilogue_direct(k, g, A.dpb[dci + gi]);
+    }
+    // block GEMM pairs of the factored form
+    for (int gi = 0; gi < d.ngemm && !A.direct; ++gi) {
       const GemmDesc& g = d.g[gi];
       prologue(k, g);
-      ok = run_gemm(k, g.Kc, g.concat ? 2 * g.Km : g.Km);
-      if (!ok) break;
+      run_gemm(k, g.Kc, g.concat ? 2 * g.Km : g.Km);
       if (tid == 0) bulk_load(opbuf, A.ops + g.inv_off, g.inv_bytes, su32(&C.op_bar));
       mid_step(k, g);
-      ok = run_gemm(k, g.Km, g.concat ? 2 * g.Kc : g.Kc);
-      if (!ok) break;
+      run_gemm(k, g.Km, g.concat ? 2 * g.Kc : g.Kc);
       if (tid == 0 && gi + 1 < d.ngemm) bulk_load(opbuf, A.ops + d.g[gi + 1].fwd_off, d.g[gi + 1].fwd_bytes, su32(&C.op_bar));
       epilogue(k, g);
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncthreads();
     }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    ok = C.abort == 0;
     if (!ok) break;
     // undo the split and write the results (FP64)
     if (d.nl == 0) {
@@ -671,8 +724,7 @@ __global__ void __launch_bounds__(512, 1) tc_pass_kernel(const __grid_constant__
 size_t smem_bytes(const PassDesc& d) {
   const size_t op = (d.op_max + 1023) / 1024 * 1024;
   const size_t store = (size_t)kV * (d.L + 1) * 8;
-  const size_t maps = ((size_t)d.nmap * 2 + 15) / 16 * 16;
-  return op + store + maps + sizeof(Ctl);
+  return op + store + sizeof(Ctl);
 }
 
 }  // namespace tcx
@@ -681,9 +733,14 @@ size_t smem_bytes(const PassDesc& d) {
 
 struct TcPass {
   tcx::PassDesc d{};
+  std::vector<tcx::GemmBasis> basis;
   unsigned char* d_ops = nullptr;
-  int16_t* d_maps = nullptr;
-  unsigned long long* d_mu = nullptr;
+  // direct form (theta pass when every tile lies inside one shell)
+  bool direct = false;
+  unsigned char* d_dops = nullptr;
+  uint32_t* d_dop_off = nullptr;
+  int8_t* d_dpb = nullptr;
+  uint2* d_mu = nullptr;
   int* d_list = nullptr;
   std::vector<long long> var_off;  // list entries of fields [0, v): prefix counts
   std::vector<int> copy_runs;      // theta pass: [field, first shell, shells] runs of identity shells
@@ -698,20 +755,20 @@ struct TcPlan {
 
 namespace {
 
-unsigned long long mu_fixed(long double mu) {
-  if (mu <= 0) return 0ULL;
-  if (mu >= 1) return 1ULL << 62;
-  return (unsigned long long)llroundl(ldexpl(mu, 62));
+// mu = x 2^-30 + y 2^-60 with integers x <= 2^30, y < 2^30 (mu in [0, 1], rounded at 2^-60).
+uint2 mu_fixed(long double mu) {
+  if (mu <= 0) return make_uint2(0u, 0u);
+  if (mu >= 1) return make_uint2(1u << 30, 0u);
+  const unsigned long long t = (unsigned long long)llroundl(ldexpl(mu, 60));
+  return make_uint2((unsigned)(t >> 30), (unsigned)(t & ((1ULL << 30) - 1)));
 }
 
 sph_status build_tc_pass(TcPass* P, int L, int device) {
   std::vector<uint16_t> ops;
   std::vector<int16_t> maps;
-  if (!tcx::build_pass_desc(L, &P->d, &ops, &maps)) return SPH_EUNSUPPORTED;
+  if (!tcx::build_pass_desc(L, &P->d, &ops, &maps, &P->basis)) return SPH_EUNSUPPORTED;
   if (cudaMalloc((void**)&P->d_ops, ops.size() * 2) != cudaSuccess) return SPH_ENOMEM;
   if (cudaMemcpy(P->d_ops, ops.data(), ops.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) return SPH_ECUDA;
-  if (cudaMalloc((void**)&P->d_maps, maps.size() * 2) != cudaSuccess) return SPH_ENOMEM;
-  if (cudaMemcpy(P->d_maps, maps.data(), maps.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) return SPH_ECUDA;
   P->smem = tcx::smem_bytes(P->d);
   const int optin = max_smem_optin(device);
   if ((int)P->smem > optin) return SPH_EUNSUPPORTED;
@@ -735,7 +792,7 @@ sph_status tc_setup(sph_filter_plan_s* p) {
   if (st != SPH_OK) return st;
   const int Nr = p->Nr, Nth = p->Nth, Nph = p->Nph, ncls = p->ncls;
   // removed fractions mu = 1 - f (Sec. II.C filter functions) as 62-bit fixed-point fractions
-  std::vector<unsigned long long> mth((size_t)ncls * Nr * (Nth + 1)), mph((size_t)ncls * Nr * Nth * (Nph / 2 + 1));
+  std::vector<uint2> mth((size_t)ncls * Nr * (Nth + 1)), mph((size_t)ncls * Nr * Nth * (Nph / 2 + 1));
   for (int c = 0; c < ncls; ++c)
     for (int i = 0; i < Nr; ++i) {
       const long double lm = p->h_lmax[(size_t)c * Nr + i];
@@ -778,6 +835,38 @@ sph_status tc_setup(sph_filter_plan_s* p) {
         i = j;
       }
   }
+  // direct theta operators, per active (class, radius): possible when a tile of 64 doubled circles
+  // never spans two shells
+  std::vector<unsigned char> dops;
+  std::vector<uint32_t> dop_off;
+  std::vector<int8_t> dpb;
+  TcPass& P0 = T->pass[0];
+  P0.direct = (Nph / 2) % tcx::kV == 0;
+  if (P0.direct) {
+    const int ng = P0.d.ngemm;
+    dop_off.assign((size_t)ncls * Nr * ng, 0u);
+    dpb.assign((size_t)ncls * Nr * ng, (int8_t)48);
+    std::vector<char> need((size_t)ncls * Nr, 0);
+    for (int e : lth) {
+      const int v = e / Nr, i = e % Nr;
+      need[(size_t)p->var_cls[(size_t)v] * Nr + i] = 1;
+    }
+    std::vector<uint16_t> blob;
+    std::vector<long double> mu((size_t)Nth + 1);
+    for (int c = 0; c < ncls; ++c)
+      for (int i = 0; i < Nr; ++i) {
+        if (!need[(size_t)c * Nr + i]) continue;
+        const long double lm = p->h_lmax[(size_t)c * Nr + i];
+        for (int l = 0; l <= Nth; ++l) mu[(size_t)l] = 1.0L - filter_value(p->cls_kind[(size_t)c], l, lm);
+        for (int g = 0; g < ng; ++g) {
+          int pb = 48;
+          dop_off[((size_t)c * Nr + i) * ng + g] = tcx::append_direct_op(P0.d, g, P0.basis[(size_t)g], mu.data(), &blob, &pb);
+          dpb[((size_t)c * Nr + i) * ng + g] = (int8_t)pb;
+        }
+      }
+    dops.resize(blob.size() * 2);
+    std::memcpy(dops.data(), blob.data(), dops.size());
+  }
   auto up = [](auto** d, const auto& h) -> sph_status {
     if (h.empty()) return SPH_OK;
     if (cudaMalloc((void**)d, h.size() * sizeof(h[0])) != cudaSuccess) return SPH_ENOMEM;
@@ -788,6 +877,9 @@ sph_status tc_setup(sph_filter_plan_s* p) {
   if (st == SPH_OK) st = up(&T->pass[1].d_mu, mph);
   if (st == SPH_OK) st = up(&T->pass[0].d_list, lth);
   if (st == SPH_OK) st = up(&T->pass[1].d_list, lph);
+  if (st == SPH_OK) st = up(&P0.d_dops, dops);
+  if (st == SPH_OK) st = up(&P0.d_dop_off, dop_off);
+  if (st == SPH_OK) st = up(&P0.d_dpb, dpb);
   if (st != SPH_OK) return st;
   if (cudaDeviceGetAttribute(&T->nsm, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) return SPH_ECUDA;
   const size_t smax = std::max(T->pass[0].smem, T->pass[1].smem);
@@ -801,9 +893,11 @@ void tc_free(sph_filter_plan_s* p) {
   if (!T) return;
   for (TcPass& P : T->pass) {
     cudaFree(P.d_ops);
-    cudaFree(P.d_maps);
     cudaFree(P.d_mu);
     cudaFree(P.d_list);
+    cudaFree(P.d_dops);
+    cudaFree(P.d_dop_off);
+    cudaFree(P.d_dpb);
   }
   delete T;
   p->tc = nullptr;
@@ -831,7 +925,10 @@ cudaError_t launch_pass(sph_filter_plan_s* p, int q, const double* src, double* 
   a.mu = P.d_mu;
   a.var = p->d_var;
   a.ops = P.d_ops;
-  a.maps = P.d_maps;
+  a.direct = P.direct ? 1 : 0;
+  a.dops = P.d_dops;
+  a.dop_off = P.d_dop_off;
+  a.dpb = P.d_dpb;
   a.d = P.d;
   a.status = p->d_status;
   const long long ntiles = (a.nvec + tcx::kV - 1) / tcx::kV;

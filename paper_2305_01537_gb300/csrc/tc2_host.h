@@ -27,11 +27,15 @@ struct GemmDesc {
   int concat;       // halves side by side in the output columns
   int rows2;        // rows 64 .. 127 carry data
   int Pb;           // operator fixed-point bits: entry = digits * 2^-Pb (45 .. 48)
+  int rin;          // right shift that brings the block's coordinates (|c| < 2^(F + growth)) to 46 bits
   uint32_t fwd_off; // byte offset of the forward operator [kS][Nf][Kc] in the pass's operator blob
   uint32_t inv_off; // byte offset of the inverse operator [kS][Ni][Km]
   uint32_t fwd_bytes, inv_bytes;
   int kin_off;      // int16 map kin[2][Kc]: store index of coordinate k of half h (-1: padding)
   int mode_off;     // int16 map mode[2][Km]: Fourier mode m of output/input j of half h (-1: padding)
+  // the same maps in affine form (checked at plan creation): for k < cnt[h], store index
+  // ka[h] + ks[h] k and mode ma[h] + ms[h] k; cnt[h] = 0 for a half without data
+  int cnt[2], ka[2], ks[2], ma[2], ms[2];
 };
 
 struct PassDesc {
@@ -48,9 +52,25 @@ struct PassDesc {
   int nmap;         // int16 map entries
 };
 
+// The orthonormal mode basis of a GEMM's blocks: U[h][j][k] is basis vector j (Fourier mode
+// modes[h][j]) over the block's coordinates k, for row half h (a level's halves share U[0]; a base
+// GEMM without a second half leaves h = 1 empty).
+struct GemmBasis {
+  std::vector<int> modes[2];
+  std::vector<std::vector<long double>> U[2];
+};
+
 // Builds the pass description, the operator blob (BF16 digit slices in the kernel's shared-memory
-// layout) and the int16 index maps for vectors of length L. Returns false if L is not supported.
-bool build_pass_desc(int L, PassDesc* d, std::vector<uint16_t>* ops, std::vector<int16_t>* maps);
+// layout) and the int16 index maps for vectors of length L, and (if basis is not null) the bases.
+// Returns false if L is not supported.
+bool build_pass_desc(int L, PassDesc* d, std::vector<uint16_t>* ops, std::vector<int16_t>* maps,
+                     std::vector<GemmBasis>* basis = nullptr);
+
+// The direct operator of GEMM g for the multipliers mu[m] (m = 0 .. L/2): the block matrix
+// K = U^T diag(mu) U (rows: output coordinates, (concat ? 2 : 1) Kc of them; columns: input
+// coordinates, Kc), appended to ops as digit slices at scale 2^Pb. Returns its byte offset.
+uint32_t append_direct_op(const PassDesc& d, int g, const GemmBasis& b, const long double* mu,
+                          std::vector<uint16_t>* ops, int* Pb);
 
 // Offset (elements) of (row, k) in a ROWS x K operand stored K-major without swizzle: 8-row x
 // 8-element core matrices of 128 contiguous bytes; the next core matrix along K is 128 bytes on,

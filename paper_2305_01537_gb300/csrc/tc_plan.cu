@@ -112,11 +112,13 @@ int op_bits(const std::vector<std::vector<long double>>& u) {
 
 }  // namespace
 
-bool build_pass_desc(int L, PassDesc* d, std::vector<uint16_t>* ops, std::vector<int16_t>* maps) {
+bool build_pass_desc(int L, PassDesc* d, std::vector<uint16_t>* ops, std::vector<int16_t>* maps,
+                     std::vector<GemmBasis>* basis) {
   if (L < 2 || L % 2 != 0 || L > kMaxL) return false;
   *d = PassDesc{};
   ops->clear();
   maps->clear();
+  if (basis) basis->clear();
   int nl = 0, nb = 0;
   plan_levels(L, &nl, &nb);
   d->L = L;
@@ -207,6 +209,7 @@ bool build_pass_desc(int L, PassDesc* d, std::vector<uint16_t>* ops, std::vector
     g.concat = 0;
     g.rows2 = 1;
     g.Pb = op_bits(a.u);
+    g.rin = d->F + (l + 2) - 46;  // level-l coordinates are sums of 2^(l + 2) stored values
     g.fwd_off = append_op(ops, g.Km, g.Kc, g.Pb, [&](int j, int k) {
       return (j < q && k < q) ? a.u[(size_t)j][(size_t)k] : 0.0L;
     });
@@ -217,6 +220,14 @@ bool build_pass_desc(int L, PassDesc* d, std::vector<uint16_t>* ops, std::vector
     g.inv_bytes = (uint32_t)(kS * g.Kc * g.Km * 2);
     g.kin_off = add_map(a.idx, b.idx, g.Kc);
     g.mode_off = add_map(a.modes, b.modes, g.Km);
+    if (basis) {
+      GemmBasis gb;
+      gb.modes[0] = a.modes;
+      gb.U[0] = a.u;
+      gb.modes[1] = b.modes;
+      gb.U[1] = b.u;
+      basis->push_back(gb);
+    }
   }
   // base: the even and odd halves, side by side in one GEMM if that fits the same tensor memory
   {
@@ -245,6 +256,7 @@ bool build_pass_desc(int L, PassDesc* d, std::vector<uint16_t>* ops, std::vector
       g.concat = 1;
       g.rows2 = 1;
       g.Pb = Pb;
+      g.rin = d->F + (nl + 1) - 46;  // base coordinates are sums of 2^(nl + 1) stored values
       g.fwd_off = append_op(ops, 2 * Kb, Kb, Pb, [&](int n, int k) {
         const Block& B = n < Kb ? e : o;
         const int j = n % Kb;
@@ -259,6 +271,14 @@ bool build_pass_desc(int L, PassDesc* d, std::vector<uint16_t>* ops, std::vector
       g.inv_bytes = g.fwd_bytes;
       g.kin_off = add_map(e.idx, o.idx, Kb);
       g.mode_off = add_map(e.modes, o.modes, Kb);
+      if (basis) {
+        GemmBasis gb;
+        gb.modes[0] = e.modes;
+        gb.U[0] = e.u;
+        gb.modes[1] = o.modes;
+        gb.U[1] = o.u;
+        basis->push_back(gb);
+      }
     } else {
       for (int half = 0; half < 2; ++half) {
         const Block& B = half == 0 ? e : o;
@@ -267,6 +287,7 @@ bool build_pass_desc(int L, PassDesc* d, std::vector<uint16_t>* ops, std::vector
         g.concat = 0;
         g.rows2 = 0;
         g.Pb = op_bits(B.u);
+        g.rin = d->F + (nl + 1) - 46;
         g.fwd_off = append_op(ops, Kb, Kb, g.Pb, [&](int j, int k) {
           return (j < hcnt && k < hcnt) ? B.u[(size_t)j][(size_t)k] : 0.0L;
         });
@@ -277,7 +298,32 @@ bool build_pass_desc(int L, PassDesc* d, std::vector<uint16_t>* ops, std::vector
         g.inv_bytes = g.fwd_bytes;
         g.kin_off = add_map(B.idx, none, Kb);
         g.mode_off = add_map(B.modes, none, Kb);
+        if (basis) {
+          GemmBasis gb;
+          gb.modes[0] = B.modes;
+          gb.U[0] = B.u;
+          basis->push_back(gb);
+        }
       }
+    }
+  }
+  // affine forms of the index maps (the kernel computes indices instead of reading the maps)
+  for (int i = 0; i < d->ngemm; ++i) {
+    GemmDesc& g = d->g[i];
+    for (int h = 0; h < 2; ++h) {
+      const int16_t* kin = maps->data() + g.kin_off + h * g.Kc;
+      const int16_t* mode = maps->data() + g.mode_off + h * g.Km;
+      int n = 0;
+      while (n < g.Kc && kin[n] >= 0) ++n;
+      g.cnt[h] = n;
+      g.ka[h] = n > 0 ? kin[0] : 0;
+      g.ks[h] = n > 1 ? kin[1] - kin[0] : 1;
+      g.ma[h] = n > 0 ? mode[0] : 0;
+      g.ms[h] = n > 1 ? mode[1] - mode[0] : 1;
+      for (int k = 0; k < g.Kc; ++k)
+        if (k < n ? kin[k] != g.ka[h] + g.ks[h] * k : kin[k] >= 0) return false;
+      for (int k = 0; k < g.Km; ++k)
+        if (k < n ? mode[k] != g.ma[h] + g.ms[h] * k : mode[k] >= 0) return false;
     }
   }
   d->KA = 16;
@@ -295,9 +341,35 @@ bool build_pass_desc(int L, PassDesc* d, std::vector<uint16_t>* ops, std::vector
   if (cols > 512) return false;
   d->tmem_cols = cols;
   d->threads = d->KA >= 64 ? 512 : 256;
+  // the mid step holds at most 3 chunks of 8 modes per thread (threads / 128 threads share a row)
+  if (d->KA / 8 > 3 * (d->threads / 128)) return false;
   d->nmap = (int)maps->size();
   if (d->nmap > kMaxMap) return false;
   return true;
+}
+
+uint32_t append_direct_op(const PassDesc& d, int gi, const GemmBasis& b, const long double* mu,
+                          std::vector<uint16_t>* ops, int* Pb) {
+  const GemmDesc& g = d.g[gi];
+  const int halves = g.concat ? 2 : 1;
+  const int rows = halves * g.Kc;
+  std::vector<std::vector<long double>> K((size_t)rows, std::vector<long double>((size_t)g.Kc, 0.0L));
+  long double mx = 0;
+  for (int h = 0; h < halves; ++h) {
+    // a level's second half uses the first half's operator (the two are equal)
+    const std::vector<std::vector<long double>>& U = (g.concat && h == 1) ? b.U[1] : b.U[0];
+    const std::vector<int>& modes = (g.concat && h == 1) ? b.modes[1] : b.modes[0];
+    const int n = (int)U.size();
+    for (int p = 0; p < n; ++p)
+      for (int q = 0; q < n; ++q) {
+        long double s = 0;
+        for (int j = 0; j < n; ++j) s += mu[modes[(size_t)j]] * U[(size_t)j][(size_t)p] * U[(size_t)j][(size_t)q];
+        K[(size_t)(h * g.Kc + p)][(size_t)q] = s;
+        mx = std::max(mx, fabsl(s));
+      }
+  }
+  *Pb = mx > 0 ? std::min(48, (int)floorl(45.999L - log2l(mx))) : 48;
+  return append_op(ops, rows, g.Kc, *Pb, [&](int n, int k) { return K[(size_t)n][(size_t)k]; });
 }
 
 }  // namespace tcx
