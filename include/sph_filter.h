@@ -22,9 +22,10 @@
  *    sph_filter_plan_sync_status().
  *  - There is no CPU fallback: without a usable CUDA device every call fails with SPH_ECUDA.
  *  - The plan is immutable after creation; concurrent calls on different streams with the same
- *    plan are allowed. (The tensor-core form keeps per-CTA scratch in the plan: the library orders
- *    its launches of one plan one after the other across streams, except inside a CUDA-graph
- *    capture, whose launches are ordered by the graph.)
+ *    plan are allowed. (The tensor-core form's single launch per application keeps its work
+ *    counters in one of four sets of the plan, taken in turn; a launch waits for the previous user
+ *    of its set, except inside a CUDA-graph capture, whose launches are ordered by the graph: do
+ *    not run a captured graph of a tensor-core plan concurrently with other calls of that plan.)
  *  - A plan with shells whose theta pass is the identity (see sph_filter_plan_launches) runs part
  *    of an FP64 call on a stream it owns: the call forks that stream from `stream` with an event
  *    and joins it back with another before returning, so work enqueued on `stream` afterwards
@@ -146,10 +147,10 @@ sph_status sph_filter_apply_adjoint_tanh_f32(sph_filter_plan plan, const float* 
 /* End-to-end variant for host-resident states: copies host_in to the device, filters, copies
  * the result to host_out, all on `stream`, and returns after enqueueing. host_in/host_out should
  * be page-locked for the copies to overlap. The device staging buffers are allocated by the plan
- * on first use and kept until the plan is destroyed (for the tensor-core form also three more sets
- * of its per-CTA scratch, one per pipeline stream); calls of this function on one plan share them,
- * so order such calls (one stream, or a synchronisation between them). Synchronise the stream
- * before reading host_out. Errors as sph_filter_apply, plus SPH_ENOMEM. */
+ * on first use and kept until the plan is destroyed (for the tensor-core form also the work lists
+ * of the field chunks the call filters one at a time); calls of this function on one plan share
+ * them, so order such calls (one stream, or a synchronisation between them). Synchronise the
+ * stream before reading host_out. Errors as sph_filter_apply, plus SPH_ENOMEM. */
 sph_status sph_filter_apply_host(sph_filter_plan plan, const double* host_in, double* host_out,
                                  sph_stream_t stream);
 

@@ -32,6 +32,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -46,28 +48,46 @@ constexpr int kMaxChunks = 3;                // 8-value chunks per thread and ro
 
 struct RowInfo {
   long long base;                  // offset of the vector's element 0 in the state (circle: meridian k)
+  const double* src;               // state the vector is read from
   const uint2* mu;                 // the vector's multipliers mu_m as (mu 2^30, low bits 2^60), m = 0 .. L/2
+  int shell;                       // v * Nr + i
   int neg;                         // theta circles of odd fields: the second meridian carries -1
   int valid;
 };
 
-struct TcArgs {
-  int pass;                        // 0: theta (doubled circles), 1: phi (rings)
-  int Nr, Nth, Nph;
-  const double* src;
-  double* dst;                     // may equal src; only the pass's vectors are written
+// Per pass (0: theta, doubled circles; 1: phi, rings).
+struct PassArgs {
   const int* list;                 // theta: active shells v*Nr+i; phi: active rings (v*Nr+i)*Nth+j
-  long long nvec;                  // theta: entries * Nph/2; phi: entries
   const uint2* mu;                 // theta: [ncls][Nr][Nth+1]; phi: [ncls][Nr][Nth][Nph/2+1]
+  const unsigned char* ops;        // operator blob (global), layout of the pass's PassDesc
+};
+
+// Work items (int4): {0, first circle, circles, 0} a theta tile; {1, first ring of the list, rings,
+// depends} a phi tile (depends: some ring's shell has a theta pass, whose circles must be done
+// first); {2, shell, first ring, rings} a copy of rings without any pass (out-of-place calls).
+enum { kItemTheta = 0, kItemPhi = 1, kItemCopy = 2 };
+
+struct TcArgs {
+  int Nr, Nth, Nph;
+  int var_begin, var_end;          // fields [var_begin, var_end) are filtered
+  const double* in;
+  double* out;                     // may equal in
+  int fused;                       // 1: phi tiles of shells with a theta pass read `out` after waiting for
+                                   // their circles; 0: every tile reads `in` (one pass per launch)
   const VarInfo* var;
-  const unsigned char* ops;        // operator blob (global), layout of PassDesc
+  PassDesc pd[2];
+  PassArgs pa[2];
   // direct form (theta pass, tiles inside one shell): per (class, radius) block matrices
   // U^T diag(mu) U; dop_off / dpb [(cls * Nr + i) * ngemm + g]: byte offset in dops, scale bits
   int direct;
   const unsigned char* dops;
   const uint32_t* dop_off;
   const int8_t* dpb;
-  PassDesc d;
+  const int4* items;
+  int nitems;
+  const unsigned char* shell_th;   // [nvars * Nr]: the shell has a theta pass
+  int* counters;                   // [0] next item, [1] CTAs finished, [2 + shell] theta circles done
+  int nshells;
   unsigned* status;
 };
 
@@ -79,6 +99,8 @@ struct Ctl {
   unsigned long long op_bar, mma_bar;
   uint32_t tslot;
   int abort;
+  int item[2];
+  int last;
 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -97,8 +119,8 @@ __device__ __forceinline__ uint32_t make_idesc(int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
 }
 
-// Bounded wait on an mbarrier phase; gives up early once another thread has set *abort.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* abort) {
+// Bounded wait on an mbarrier phase (about a second at most).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   for (long long it = 0; it < kWaitLimit; ++it) {
     uint32_t ok;
     asm volatile(
@@ -107,7 +129,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const v
         : "r"(bar), "r"(parity)
         : "memory");
     if (ok) return true;
-    if ((it & 1023) == 1023 && *abort) return false;
   }
   return false;
 }
@@ -228,14 +249,16 @@ __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.
 
 // Offset of element q of a vector: theta circles run down meridian k, then back up meridian
 // k + Nphi/2 (Sec. II.C double covering); rings are contiguous.
-__device__ __forceinline__ long long elem_off(const TcArgs& A, long long base, int q) {
-  if (A.pass == 0)
+__device__ __forceinline__ long long elem_off(const TcArgs& A, int pass, long long base, int q) {
+  if (pass == 0)
     return q < A.Nth ? base + (long long)q * A.Nph : base + (long long)(2 * A.Nth - 1 - q) * A.Nph + A.Nph / 2;
   return base + q;
 }
 
 struct Kern {
   const TcArgs& A;
+  const PassDesc* d;         // the current tile's pass
+  int pass;
   Ctl& C;
   unsigned char* opbuf;      // operator buffer (shared)
   long long* store;          // [kV][pitch] fixed-point store
@@ -285,7 +308,7 @@ __device__ __forceinline__ void issue_gemm_t(uint32_t tmem, uint32_t acc0, int K
 }
 
 __device__ void issue_gemm(Kern& k, int K, int N) {
-  const PassDesc& d = k.A.d;
+  const PassDesc& d = *k.d;
   const uint32_t idesc = make_idesc(N);
   const uint32_t slice16 = (uint32_t)(N * K * 2) >> 4;
   const uint64_t bd0 = make_desc(su32(k.opbuf), K);
@@ -310,9 +333,11 @@ __device__ void run_gemm(Kern& k, int K, int N) {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (k.tid == 0) {
-    if (!k.C.abort && mbar_wait(su32(&k.C.op_bar), k.op_phase & 1u, &k.C.abort)) {
+    // the operator copy and the MMAs were issued by this CTA: wait for them even after an abort
+    // elsewhere, so that nothing is in flight when the CTA leaves
+    if (mbar_wait(su32(&k.C.op_bar), k.op_phase & 1u)) {
       issue_gemm(k, K, N);
-      if (!mbar_wait(su32(&k.C.mma_bar), k.mma_phase & 1u, &k.C.abort)) k.C.abort = 1;
+      if (!mbar_wait(su32(&k.C.mma_bar), k.mma_phase & 1u)) k.C.abort = 1;
     } else {
       k.C.abort = 1;
     }
@@ -329,7 +354,7 @@ __device__ __forceinline__ void put_a(const Kern& k, const long long vals[8], in
   slice8(vals, w);
   const uint32_t lane_base = k.tmem + ((uint32_t)(32 * k.lq) << 16);
 #pragma unroll
-  for (int a = 0; a < kS; ++a) tmem_st4(lane_base + (uint32_t)(a * (k.A.d.KA / 2) + k0 / 2), w[a]);
+  for (int a = 0; a < kS; ++a) tmem_st4(lane_base + (uint32_t)(a * (k.d->KA / 2) + k0 / 2), w[a]);
 }
 
 // Prologue: the GEMM's input coordinates of row r, shifted right by the block's bound (|c| < 2^(F +
@@ -358,7 +383,7 @@ __device__ void mid_step(Kern& k, const GemmDesc& g) {
   const int coff = g.concat ? k.h * g.Km : 0;
   const int mlt[3] = {1 << (72 - g.Pb), 1 << (56 - g.Pb), 1 << (48 - g.Pb)};
   const uint32_t lane_base = k.tmem + ((uint32_t)(32 * k.lq) << 16);
-  const uint32_t accb = lane_base + (uint32_t)(3 * k.A.d.KA);
+  const uint32_t accb = lane_base + (uint32_t)(3 * k.d->KA);
   const int nch = g.Km / 8;
   long long y[kMaxChunks][8];
   unsigned long long orv = 0;
@@ -368,7 +393,7 @@ __device__ void mid_step(Kern& k, const GemmDesc& g) {
     if (c < nch) {
       float f[5][8];
 #pragma unroll
-      for (int t = 0; t < 5; ++t) tmem_ld8(accb + (uint32_t)(t * k.A.d.NA + coff + 8 * c), f[t]);
+      for (int t = 0; t < 5; ++t) tmem_ld8(accb + (uint32_t)(t * k.d->NA + coff + 8 * c), f[t]);
       tmem_wait_ld();
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
@@ -409,7 +434,7 @@ __device__ void epilogue(Kern& k, const GemmDesc& g) {
   const int ks = g.ks[k.h];
   const int coff = g.concat ? k.h * g.Kc : 0;
   const uint32_t lane_base = k.tmem + ((uint32_t)(32 * k.lq) << 16);
-  const uint32_t accb = lane_base + (uint32_t)(3 * k.A.d.KA);
+  const uint32_t accb = lane_base + (uint32_t)(3 * k.d->KA);
   const int mlt[3] = {1 << (72 - g.Pb), 1 << (56 - g.Pb), 1 << (48 - g.Pb)};
   const int up = g.rin - k.C.sh_mid[k.r];  // >= 0
   if (k.cp == 0) k.C.rowbl[k.r] = 0;         // every thread read it before the inverse GEMM's barrier
@@ -418,7 +443,7 @@ __device__ void epilogue(Kern& k, const GemmDesc& g) {
   for (int c = k.cp; c < nch; c += k.WQ) {
     float f[5][8];
 #pragma unroll
-    for (int t = 0; t < 5; ++t) tmem_ld8(accb + (uint32_t)(t * k.A.d.NA + coff + 8 * c), f[t]);
+    for (int t = 0; t < 5; ++t) tmem_ld8(accb + (uint32_t)(t * k.d->NA + coff + 8 * c), f[t]);
     tmem_wait_ld();
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -437,14 +462,14 @@ __device__ void epilogue_direct(Kern& k, const GemmDesc& g, int Pb) {
   const int ks = g.ks[k.h];
   const int coff = g.concat ? k.h * g.Kc : 0;
   const uint32_t lane_base = k.tmem + ((uint32_t)(32 * k.lq) << 16);
-  const uint32_t accb = lane_base + (uint32_t)(3 * k.A.d.KA);
+  const uint32_t accb = lane_base + (uint32_t)(3 * k.d->KA);
   const int mlt[3] = {1 << (72 - Pb), 1 << (56 - Pb), 1 << (48 - Pb)};
   long long* srow = k.store + (size_t)k.v * k.pitch + g.ka[k.h];
   const int nch = g.Kc / 8;
   for (int c = k.cp; c < nch; c += k.WQ) {
     float f[5][8];
 #pragma unroll
-    for (int t = 0; t < 5; ++t) tmem_ld8(accb + (uint32_t)(t * k.A.d.NA + coff + 8 * c), f[t]);
+    for (int t = 0; t < 5; ++t) tmem_ld8(accb + (uint32_t)(t * k.d->NA + coff + 8 * c), f[t]);
     tmem_wait_ld();
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -461,7 +486,7 @@ __device__ void epilogue_direct(Kern& k, const GemmDesc& g, int Pb) {
 // rings one warp per vector (consecutive lanes, consecutive positions).
 template <class Fn>
 __device__ __forceinline__ void for_tasks(const Kern& k, int count, Fn f) {
-  if (k.A.pass == 0) {
+  if (k.pass == 0) {
     const int v = k.tid & (kV - 1);
     for (int p = k.tid >> 6; p < count; p += (int)(blockDim.x >> 6)) f(v, p);
   } else {
@@ -479,8 +504,8 @@ __device__ void level_fwd(Kern& k, int n, bool convert) {
     if (convert) {
       // the outermost level reads the raw FP64 values; on a theta circle positions p + n/2 and
       // n - 1 - p lie on the second meridian, which carries the field's parity sign
-      const int base = 53 - k.A.d.F + k.C.vexp[v];
-      const bool neg = k.A.pass == 0 && k.C.row[v].neg;
+      const int base = 53 - k.d->F + k.C.vexp[v];
+      const bool neg = k.pass == 0 && k.C.row[v].neg;
       vp = to_fixed(vp, base);
       vq = to_fixed(vq, base);
       vr = to_fixed(vr, base);
@@ -504,10 +529,10 @@ __device__ void base_fwd(Kern& k, int nb, bool convert) {
     long long a = s[p], b = s[nb - 1 - p];
     if (convert) {
       // no levels: nb = L; on a theta circle position nb - 1 - p is on the second meridian
-      const int base = 53 - k.A.d.F + k.C.vexp[v];
+      const int base = 53 - k.d->F + k.C.vexp[v];
       a = to_fixed(a, base);
       b = to_fixed(b, base);
-      if (k.A.pass == 0 && k.C.row[v].neg) b = -b;
+      if (k.pass == 0 && k.C.row[v].neg) b = -b;
     }
     s[p] = a + b;
     s[nb - 1 - p] = a - b;
@@ -518,8 +543,8 @@ __device__ void base_fwd(Kern& k, int nb, bool convert) {
 // parity sign of a circle's second meridian applied to the integer).
 __device__ __forceinline__ void put_out(const Kern& k, int v, int q, long long x, int expo) {
   const RowInfo& R = k.C.row[v];
-  if (k.A.pass == 0 && R.neg && q >= k.A.Nth) x = -x;
-  k.A.dst[elem_off(k.A, R.base, q)] = from_fixed(x, expo);
+  if (k.pass == 0 && R.neg && q >= k.A.Nth) x = -x;
+  k.A.out[elem_off(k.A, k.pass, R.base, q)] = from_fixed(x, expo);
 }
 
 // Inverse base stage: values become 2 v; `out` writes them to the destination (no levels).
@@ -529,7 +554,7 @@ __device__ void base_inv(Kern& k, int nb, bool out) {
     const long long a = s[p], b = s[nb - 1 - p];
     if (out) {
       if (!k.C.row[v].valid) return;
-      const int expo = (k.C.vexp[v] - 1022) - k.A.d.F - 1;
+      const int expo = (k.C.vexp[v] - 1022) - k.d->F - 1;
       put_out(k, v, p, a + b, expo);
       put_out(k, v, nb - 1 - p, a - b, expo);
     } else {
@@ -549,7 +574,7 @@ __device__ void level_inv(Kern& k, int n, int sc, bool out) {
     const long long y0 = E0 + zp, y1 = E0 - zp, y2 = E1 + zq, y3 = E1 - zq;
     if (out) {
       if (!k.C.row[v].valid) return;
-      const int expo = (k.C.vexp[v] - 1022) - k.A.d.F - (sc + 1);
+      const int expo = (k.C.vexp[v] - 1022) - k.d->F - (sc + 1);
       put_out(k, v, p, y0, expo);
       put_out(k, v, p + n / 2, y1, expo);
       put_out(k, v, n / 2 - 1 - p, y2, expo);
@@ -563,18 +588,47 @@ __device__ void level_inv(Kern& k, int n, int sc, bool out) {
   });
 }
 
+// Bounded wait (on the GPU, about a second) for a shell's theta circles; false if it ran out.
+__device__ __forceinline__ bool wait_circles(const int* ctr, int need) {
+  for (long long it = 0; it < (1LL << 22); ++it) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+    if (v >= need) return true;
+    __nanosleep(256);
+  }
+  return false;
+}
+
+// Copies rings [j0, j0 + nj) of one shell from in to out (rings no pass changes).
+__device__ void copy_rings(const TcArgs& A, int shell, int j0, int nj) {
+  const size_t off = ((size_t)shell * A.Nth + j0) * A.Nph;
+  const size_t n16 = (size_t)nj * A.Nph / 2;  // 16-byte pieces (Nphi is even)
+  const double2* s = reinterpret_cast<const double2*>(A.in + off);
+  double2* d = reinterpret_cast<double2*>(A.out + off);
+  size_t i = threadIdx.x;
+  for (; i + 3 * blockDim.x < n16; i += 4 * blockDim.x) {
+    const double2 a = __ldcs(s + i), b = __ldcs(s + i + blockDim.x), c = __ldcs(s + i + 2 * blockDim.x),
+                  e = __ldcs(s + i + 3 * blockDim.x);
+    __stcs(d + i, a);
+    __stcs(d + i + blockDim.x, b);
+    __stcs(d + i + 2 * blockDim.x, c);
+    __stcs(d + i + 3 * blockDim.x, e);
+  }
+  for (; i < n16; i += blockDim.x) __stcs(d + i, __ldcs(s + i));
+}
+
 __global__ void __launch_bounds__(512, 1) tc_pass_kernel(const __grid_constant__ TcArgs A) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  const PassDesc& d = A.d;
-  const int L = d.L;
-  const int pitch = L + 1;
+  const int Lmax = max(A.pd[0].L, A.pd[1].L);
+  const uint32_t opmax = max(A.pd[0].op_max, A.pd[1].op_max);
+  const int tmem_cols = max(A.pd[0].tmem_cols, A.pd[1].tmem_cols);
   unsigned char* opbuf = smem;
-  long long* store = reinterpret_cast<long long*>(smem + ((d.op_max + 1023) / 1024) * 1024);
-  Ctl& C = *reinterpret_cast<Ctl*>(store + (size_t)kV * pitch);
+  long long* store = reinterpret_cast<long long*>(smem + ((opmax + 1023) / 1024) * 1024);
+  Ctl& C = *reinterpret_cast<Ctl*>(store + (size_t)kV * (Lmax + 1));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&C.tslot)),
-                 "r"(d.tmem_cols));
+                 "r"(tmem_cols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
@@ -587,78 +641,112 @@ __global__ void __launch_bounds__(512, 1) tc_pass_kernel(const __grid_constant__
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  Kern k{A, C, opbuf, store, pitch, C.tslot, tid, warp, lane, warp & 3, warp >> 2, (int)(blockDim.x / 128),
+  Kern k{A, &A.pd[0], 0, C, opbuf, store, 0, C.tslot, tid, warp, lane, warp & 3, warp >> 2, (int)(blockDim.x / 128),
          0, 0, 0, 0u, 0u};
   k.r = 32 * k.lq + lane;
   k.h = k.r >> 6;
   k.v = k.r & (kV - 1);
-  const long long ntiles = (A.nvec + kV - 1) / kV;
-  bool ok = true;
-  for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-    // the first operator of the tile (the buffer is free: the previous tile's GEMMs completed); the
-    // direct form's operators are those of the tile's (class, radius): every vector of a tile lies
-    // in one shell
+  const int half = A.Nph / 2;
+  for (int n = 0;; ++n) {
+    // two slots: a slot is rewritten two iterations later, after a barrier every thread passed
+    // having read it
+    if (tid == 0) C.item[n & 1] = atomicAdd(&A.counters[0], 1);
+    __syncthreads();
+    const int it = C.item[n & 1];
+    if (it >= A.nitems || C.abort) break;
+    const int4 w = A.items[it];
+    if (w.x == kItemCopy) {
+      const int v = w.y / A.Nr;
+      if (A.in != A.out && v >= A.var_begin && v < A.var_end) copy_rings(A, w.y, w.z, w.w);
+      continue;  // the barrier at the top of the loop orders the next item
+    }
+    const int pass = w.x;
+    const PassDesc& d = A.pd[pass];
+    const PassArgs& P = A.pa[pass];
+    k.d = &d;
+    k.pass = pass;
+    const int L = d.L;
+    const int pitch = L + 1;
+    k.pitch = pitch;
+    // the direct form's operators are those of the tile's (class, radius): every circle of a
+    // theta tile lies in one shell
     int dci = 0;
-    if (A.direct) {
-      const int shell = A.list[(tile * kV) / (A.Nph / 2)];
+    const bool direct = pass == 0 && A.direct;
+    if (direct) {
+      const int shell = P.list[w.y / half];
       const int vv = shell / A.Nr, i = shell - vv * A.Nr;
       dci = (A.var[vv].cls * A.Nr + i) * d.ngemm;
     }
-    if (tid == 0) {
-      if (A.direct) bulk_load(opbuf, A.dops + A.dop_off[dci], d.g[0].Kc * (d.g[0].concat ? 2 : 1) * d.g[0].Kc * 2 * kS, su32(&C.op_bar));
-      else bulk_load(opbuf, A.ops + d.g[0].fwd_off, d.g[0].fwd_bytes, su32(&C.op_bar));
-    }
     if (tid < kV) {
       RowInfo R{};
-      const long long vg = tile * kV + tid;
-      R.valid = vg < A.nvec;
-      if (R.valid) {
-        if (A.pass == 0) {
-          const int half = A.Nph / 2;
-          const int shell = A.list[vg / half];
-          const int kk = (int)(vg % half);
-          const int vv = shell / A.Nr, i = shell - vv * A.Nr;
-          const VarInfo vi = A.var[vv];
-          R.base = (long long)shell * A.Nth * A.Nph + kk;
-          R.mu = A.mu + ((size_t)vi.cls * A.Nr + i) * (A.Nth + 1);
-          R.neg = vi.parity;
+      R.valid = 0;
+      if (tid < w.z) {
+        const long long vg = (long long)w.y + tid;
+        int shell, vv, i;
+        if (pass == 0) {
+          shell = P.list[vg / half];
+          vv = shell / A.Nr;
+          i = shell - vv * A.Nr;
+          R.base = (long long)shell * A.Nth * A.Nph + (int)(vg % half);
+          R.mu = P.mu + ((size_t)A.var[vv].cls * A.Nr + i) * (A.Nth + 1);
+          R.neg = A.var[vv].parity;
+          R.src = A.in;
         } else {
-          const int ring = A.list[vg];
-          const int j = ring % A.Nth, vi_ = ring / A.Nth;
-          const int vv = vi_ / A.Nr, i = vi_ - vv * A.Nr;
-          const VarInfo vi = A.var[vv];
+          const int ring = P.list[vg];
+          const int j = ring % A.Nth;
+          shell = ring / A.Nth;
+          vv = shell / A.Nr;
+          i = shell - vv * A.Nr;
           R.base = (long long)ring * A.Nph;
-          R.mu = A.mu + (((size_t)vi.cls * A.Nr + i) * A.Nth + j) * (A.Nph / 2 + 1);
+          R.mu = P.mu + (((size_t)A.var[vv].cls * A.Nr + i) * A.Nth + j) * (A.Nph / 2 + 1);
           R.neg = 0;
+          // in the fused application a shell with a theta pass is read back from out once all its
+          // circles are done
+          const bool after_theta = A.fused && A.shell_th[shell];
+          R.src = after_theta ? A.out : A.in;
+          if (after_theta && vv >= A.var_begin && vv < A.var_end &&
+              !wait_circles(A.counters + 2 + shell, half))
+            C.abort = 1;
         }
+        R.shell = shell;
+        R.valid = vv >= A.var_begin && vv < A.var_end;
       }
       C.row[tid] = R;
       C.vexp[tid] = 0;
     }
-    __syncthreads();
-    // load: raw FP64 values by asynchronous 8-byte copies (all of a thread's copies in flight at
-    // once), then each vector's largest exponent
-    const int L2 = L;
-    for_tasks(k, L2, [&](int v, int q) {
+    const int any = __syncthreads_or(tid < kV && C.row[tid].valid);
+    if (C.abort) break;
+    if (!any) continue;  // every vector belongs to fields outside the call's range
+    // the first operator (the buffer is free: the previous tile's GEMMs completed)
+    if (tid == 0) {
+      if (direct) bulk_load(opbuf, A.dops + A.dop_off[dci], d.g[0].Kc * (d.g[0].concat ? 2 : 1) * d.g[0].Kc * 2 * kS, su32(&C.op_bar));
+      else bulk_load(opbuf, P.ops + d.g[0].fwd_off, d.g[0].fwd_bytes, su32(&C.op_bar));
+    }
+    // load: raw FP64 values by asynchronous 8-byte copies (all of a thread's copies in flight at once),
+    // then each vector's exponent. A ring read back after its shell's theta tiles cannot be stale in
+    // this SM's L1: the only earlier reads of those lines in this launch are by the theta tile that
+    // wrote them (and this SM's own writes keep its L1 current)
+    for_tasks(k, L, [&](int v, int q) {
       const RowInfo& R = C.row[v];
       if (!R.valid) return;
-      const double* g = A.src + elem_off(A, R.base, q);
+      const double* g = R.src + elem_off(A, pass, R.base, q);
       asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(su32(store + (size_t)v * pitch + q)), "l"(g)
                    : "memory");
     });
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-    if (A.pass == 0) {
+    if (pass == 0) {
       int e = 0;
-      for_tasks(k, L2, [&](int v, int q) {
-        e = max(e, (int)((store[(size_t)v * pitch + q] >> 52) & 0x7FF));
+      for_tasks(k, L, [&](int v, int q) {
+        if (C.row[v].valid) e = max(e, (int)((store[(size_t)v * pitch + q] >> 52) & 0x7FF));
       });
       atomicMax(&C.vexp[tid & (kV - 1)], e);
     } else {
       for (int v = warp; v < kV; v += blockDim.x / 32) {
         int e = 0;
-        for (int q = lane; q < L; q += 32) e = max(e, (int)((store[(size_t)v * pitch + q] >> 52) & 0x7FF));
+        if (C.row[v].valid)
+          for (int q = lane; q < L; q += 32) e = max(e, (int)((store[(size_t)v * pitch + q] >> 52) & 0x7FF));
         e = __reduce_max_sync(0xffffffffu, e);
-        if (lane == 0) C.vexp[v] = C.row[v].valid ? e : 0;
+        if (lane == 0) C.vexp[v] = e;
       }
     }
     __syncthreads();
@@ -673,7 +761,7 @@ __global__ void __launch_bounds__(512, 1) tc_pass_kernel(const __grid_constant__
       __syncthreads();
     }
     // block GEMMs: the direct form, one per block
-    for (int gi = 0; gi < d.ngemm && A.direct; ++gi) {
+    for (int gi = 0; gi < d.ngemm && direct; ++gi) {
       const GemmDesc& g = d.g[gi];
       const int N = g.concat ? 2 * g.Kc : g.Kc;
       prologue(k, g);
@@ -685,20 +773,19 @@ __global__ void __launch_bounds__(512, 1) tc_pass_kernel(const __grid_constant__
       epilogue_direct(k, g, A.dpb[dci + gi]);
     }
     // block GEMM pairs of the factored form
-    for (int gi = 0; gi < d.ngemm && !A.direct; ++gi) {
+    for (int gi = 0; gi < d.ngemm && !direct; ++gi) {
       const GemmDesc& g = d.g[gi];
       prologue(k, g);
       run_gemm(k, g.Kc, g.concat ? 2 * g.Km : g.Km);
-      if (tid == 0) bulk_load(opbuf, A.ops + g.inv_off, g.inv_bytes, su32(&C.op_bar));
+      if (tid == 0) bulk_load(opbuf, P.ops + g.inv_off, g.inv_bytes, su32(&C.op_bar));
       mid_step(k, g);
       run_gemm(k, g.Km, g.concat ? 2 * g.Kc : g.Kc);
-      if (tid == 0 && gi + 1 < d.ngemm) bulk_load(opbuf, A.ops + d.g[gi + 1].fwd_off, d.g[gi + 1].fwd_bytes, su32(&C.op_bar));
+      if (tid == 0 && gi + 1 < d.ngemm) bulk_load(opbuf, P.ops + d.g[gi + 1].fwd_off, d.g[gi + 1].fwd_bytes, su32(&C.op_bar));
       epilogue(k, g);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    ok = C.abort == 0;
-    if (!ok) break;
+    if (C.abort) break;
     // undo the split and write the results (FP64)
     if (d.nl == 0) {
       base_inv(k, d.nb, true);
@@ -713,12 +800,31 @@ __global__ void __launch_bounds__(512, 1) tc_pass_kernel(const __grid_constant__
       }
       level_inv(k, n, sc, true);
     }
-    __syncthreads();
+    // a theta tile's circles are done: publish them (every thread's writes first)
+    if (pass == 0) {
+      __threadfence();
+      __syncthreads();
+      if (tid < kV && C.row[tid].valid) atomicAdd(A.counters + 2 + C.row[tid].shell, 1);
+    }
   }
-  if (!ok && tid == 0) atomicCAS(A.status, 0u, (unsigned)SPH_ETIMEOUT);
+  if (C.abort && tid == 0) atomicCAS(A.status, 0u, (unsigned)SPH_ETIMEOUT);
+  // the last CTA to finish resets the counters for the next application
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    C.last = atomicAdd(A.counters + 1, 1) == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (C.last) {
+    for (int i = tid; i < A.nshells; i += blockDim.x) A.counters[2 + i] = 0;
+    if (tid == 0) A.counters[0] = 0;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) A.counters[1] = 0;
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(C.tslot), "r"(d.tmem_cols));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(C.tslot), "r"(tmem_cols));
 }
 
 size_t smem_bytes(const PassDesc& d) {
@@ -733,6 +839,7 @@ size_t smem_bytes(const PassDesc& d) {
 
 struct TcPass {
   tcx::PassDesc d{};
+  std::vector<int> h_list;         // the pass's list (host copy)
   std::vector<tcx::GemmBasis> basis;
   unsigned char* d_ops = nullptr;
   // direct form (theta pass when every tile lies inside one shell)
@@ -748,9 +855,31 @@ struct TcPass {
   int ctas_per_sm = 1;
 };
 
+// Work lists and the per-application counters. Each call takes the next of kSets counter sets; a call
+// on a stream waits for the previous user of its set (an event), so calls on different streams can
+// overlap. The kernel's last CTA resets its set, so no call needs a memset.
+constexpr int kSets = 4;
 struct TcPlan {
   TcPass pass[2];
   int nsm = 0;
+  int threads = 0, ctas_per_sm = 1;
+  size_t smem = 0;
+  int4* d_items = nullptr;          // [fused application | theta tiles | phi tiles], all fields
+  int n_fused = 0, n_theta = 0, n_phi = 0;
+  std::vector<int4> h_items;        // the same on the host (filtered for calls on a field range)
+  // lists of the items that touch a field range [first, first + count), made on first use
+  struct RangeItems {
+    int4* d = nullptr;
+    int n_fused = 0, n_theta = 0, n_phi = 0;
+  };
+  std::map<std::pair<int, int>, RangeItems> ranges;
+  unsigned char* d_shell_th = nullptr;
+  int* d_counters = nullptr;        // kSets x (2 + nshells)
+  int nshells = 0;
+  cudaEvent_t set_ev[kSets] = {};
+  bool set_used[kSets] = {};
+  unsigned next_set = 0;
+  std::mutex mu;
 };
 
 namespace {
@@ -873,6 +1002,8 @@ sph_status tc_setup(sph_filter_plan_s* p) {
     return cudaMemcpy(*d, h.data(), h.size() * sizeof(h[0]), cudaMemcpyHostToDevice) == cudaSuccess ? SPH_OK
                                                                                                       : SPH_ECUDA;
   };
+  T->pass[0].h_list = lth;
+  T->pass[1].h_list = lph;
   st = up(&T->pass[0].d_mu, mth);
   if (st == SPH_OK) st = up(&T->pass[1].d_mu, mph);
   if (st == SPH_OK) st = up(&T->pass[0].d_list, lth);
@@ -882,8 +1013,80 @@ sph_status tc_setup(sph_filter_plan_s* p) {
   if (st == SPH_OK) st = up(&P0.d_dpb, dpb);
   if (st != SPH_OK) return st;
   if (cudaDeviceGetAttribute(&T->nsm, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) return SPH_ECUDA;
-  const size_t smax = std::max(T->pass[0].smem, T->pass[1].smem);
-  if (cudaFuncSetAttribute(tcx::tc_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax) != cudaSuccess)
+  // work lists. Fused application: theta tiles first, then phi tiles and copies that need no theta
+  // result, then phi tiles of shells with a theta pass (every theta tile has been taken by then, so
+  // their waits are short and cannot block a running tile).
+  const int half = Nph / 2;
+  const int nshells = p->nvars * Nr;
+  std::vector<unsigned char> shell_th((size_t)nshells, 0);
+  for (int e : lth) shell_th[(size_t)e] = 1;
+  std::vector<int4> th_items, ph_indep, ph_dep, copies;
+  const long long ncirc = (long long)lth.size() * half;
+  for (long long s = 0; s < ncirc; s += tcx::kV)
+    th_items.push_back(make_int4(tcx::kItemTheta, (int)s, (int)std::min<long long>(tcx::kV, ncirc - s), 0));
+  for (size_t s = 0; s < lph.size(); s += tcx::kV) {
+    const int cnt = (int)std::min<size_t>(tcx::kV, lph.size() - s);
+    int dep = 0;
+    for (int r = 0; r < cnt; ++r) dep |= shell_th[(size_t)(lph[s + (size_t)r] / Nth)];
+    (dep ? ph_dep : ph_indep).push_back(make_int4(tcx::kItemPhi, (int)s, cnt, dep));
+  }
+  // rings of shells without a theta pass that the phi pass leaves alone: runs of consecutive rings
+  {
+    std::vector<char> ring_act((size_t)nshells * Nth, 0);
+    for (int e : lph) ring_act[(size_t)e] = 1;
+    for (int sh = 0; sh < nshells; ++sh) {
+      if (shell_th[(size_t)sh]) continue;
+      for (int j = 0; j < Nth;) {
+        if (ring_act[(size_t)sh * Nth + j]) {
+          ++j;
+          continue;
+        }
+        int j1 = j;
+        while (j1 < Nth && !ring_act[(size_t)sh * Nth + j1]) ++j1;
+        copies.push_back(make_int4(tcx::kItemCopy, sh, j, j1 - j));
+        j = j1;
+      }
+    }
+  }
+  std::vector<int4> items;
+  items.insert(items.end(), th_items.begin(), th_items.end());
+  // interleave the independent phi tiles with the copies (compute next to memory-bound work)
+  {
+    size_t a = 0, b = 0;
+    while (a < ph_indep.size() || b < copies.size()) {
+      if (a < ph_indep.size()) items.push_back(ph_indep[a++]);
+      if (b < copies.size()) items.push_back(copies[b++]);
+    }
+  }
+  items.insert(items.end(), ph_dep.begin(), ph_dep.end());
+  T->n_fused = (int)items.size();
+  items.insert(items.end(), th_items.begin(), th_items.end());
+  T->n_theta = (int)th_items.size();
+  items.insert(items.end(), ph_indep.begin(), ph_indep.end());
+  items.insert(items.end(), ph_dep.begin(), ph_dep.end());
+  T->n_phi = (int)(ph_indep.size() + ph_dep.size());
+  T->nshells = nshells;
+  T->h_items = items;
+  st = up(&T->d_items, items);
+  if (st == SPH_OK) st = up(&T->d_shell_th, shell_th);
+  if (st != SPH_OK) return st;
+  if (cudaMalloc((void**)&T->d_counters, sizeof(int) * kSets * (2 + (size_t)nshells)) != cudaSuccess) return SPH_ENOMEM;
+  if (cudaMemset(T->d_counters, 0, sizeof(int) * kSets * (2 + (size_t)nshells)) != cudaSuccess) return SPH_ECUDA;
+  for (cudaEvent_t& e : T->set_ev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return SPH_ECUDA;
+  // one kernel serves both passes: the larger of the two shapes
+  T->threads = std::max(T->pass[0].d.threads, T->pass[1].d.threads);
+  const size_t op = std::max(T->pass[0].d.op_max, T->pass[1].d.op_max);
+  const int Lmax = std::max(T->pass[0].d.L, T->pass[1].d.L);
+  const int tmem = std::max(T->pass[0].d.tmem_cols, T->pass[1].d.tmem_cols);
+  T->smem = (op + 1023) / 1024 * 1024 + (size_t)tcx::kV * (Lmax + 1) * 8 + sizeof(tcx::Ctl);
+  const int optin = max_smem_optin(p->device);
+  if ((int)T->smem > optin) return SPH_EUNSUPPORTED;
+  T->ctas_per_sm = (tmem <= 256 && T->threads <= 256 && 2 * (T->smem + 1024) <= (size_t)optin) ? 2 : 1;
+  // enough shared memory that no SM holds more CTAs than its tensor memory serves at once (a further
+  // CTA would wait in tcgen05.alloc)
+  T->smem = std::min(std::max(T->smem, (size_t)optin / (T->ctas_per_sm + 1) + 1024), (size_t)optin);
+  if (cudaFuncSetAttribute(tcx::tc_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T->smem) != cudaSuccess)
     return SPH_ECUDA;
   return SPH_OK;
 }
@@ -899,6 +1102,12 @@ void tc_free(sph_filter_plan_s* p) {
     cudaFree(P.d_dop_off);
     cudaFree(P.d_dpb);
   }
+  cudaFree(T->d_items);
+  for (auto& kv : T->ranges) cudaFree(kv.second.d);
+  cudaFree(T->d_shell_th);
+  cudaFree(T->d_counters);
+  for (cudaEvent_t e : T->set_ev)
+    if (e) cudaEventDestroy(e);
   delete T;
   p->tc = nullptr;
 }
@@ -907,35 +1116,78 @@ void tc_free(sph_filter_plan_s* p) {
 sph_status tc_reserve_pipeline(sph_filter_plan_s*) { return SPH_OK; }
 
 namespace {
-cudaError_t launch_pass(sph_filter_plan_s* p, int q, const double* src, double* dst, int var_begin, int var_count,
-                        cudaStream_t s, int* nlaunch) {
+// One launch over the work items [first, first + count): the fused application (fused = 1) or one
+// pass (fused = 0), fields [var_begin, var_begin + var_count).
+cudaError_t launch_items(sph_filter_plan_s* p, const int4* items, int count, int fused, const double* in, double* out,
+                         int var_begin, int var_count, cudaStream_t s, int* nlaunch) {
   TcPlan* T = p->tc;
-  TcPass& P = T->pass[q];
-  const long long e0 = P.var_off[(size_t)var_begin], e1 = P.var_off[(size_t)(var_begin + var_count)];
-  if (e1 <= e0) return cudaSuccess;
+  if (count <= 0) return cudaSuccess;
   tcx::TcArgs a{};
-  a.pass = q;
   a.Nr = p->Nr;
   a.Nth = p->Nth;
   a.Nph = p->Nph;
-  a.src = src;
-  a.dst = dst;
-  a.list = P.d_list + e0;
-  a.nvec = q == 0 ? (e1 - e0) * (p->Nph / 2) : (e1 - e0);
-  a.mu = P.d_mu;
+  a.var_begin = var_begin;
+  a.var_end = var_begin + var_count;
+  a.in = in;
+  a.out = out;
+  a.fused = fused;
   a.var = p->d_var;
-  a.ops = P.d_ops;
-  a.direct = P.direct ? 1 : 0;
-  a.dops = P.d_dops;
-  a.dop_off = P.d_dop_off;
-  a.dpb = P.d_dpb;
-  a.d = P.d;
+  for (int q = 0; q < 2; ++q) {
+    a.pd[q] = T->pass[q].d;
+    a.pa[q].list = T->pass[q].d_list;
+    a.pa[q].mu = T->pass[q].d_mu;
+    a.pa[q].ops = T->pass[q].d_ops;
+  }
+  a.direct = T->pass[0].direct ? 1 : 0;
+  a.dops = T->pass[0].d_dops;
+  a.dop_off = T->pass[0].d_dop_off;
+  a.dpb = T->pass[0].d_dpb;
+  a.items = items;
+  a.nitems = count;
+  a.shell_th = T->d_shell_th;
+  a.nshells = T->nshells;
   a.status = p->d_status;
-  const long long ntiles = (a.nvec + tcx::kV - 1) / tcx::kV;
-  const int grid = (int)std::min<long long>(ntiles, (long long)T->nsm * P.ctas_per_sm);
-  tcx::tc_pass_kernel<<<grid, P.d.threads, P.smem, s>>>(a);
+  // a counter set, after its previous user (except inside a graph capture, which orders its own work)
+  std::lock_guard<std::mutex> lock(T->mu);
+  const int set = (int)(T->next_set++ % kSets);
+  a.counters = T->d_counters + (size_t)set * (2 + T->nshells);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(s, &cap);
+  if (e != cudaSuccess) return e;
+  const bool chain = cap == cudaStreamCaptureStatusNone;
+  if (chain && T->set_used[set]) {
+    e = cudaStreamWaitEvent(s, T->set_ev[set], 0);
+    if (e != cudaSuccess) return e;
+  }
+  const int grid = std::min(count, T->nsm * T->ctas_per_sm);
+  tcx::tc_pass_kernel<<<grid, T->threads, T->smem, s>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   ++*nlaunch;
-  return cudaGetLastError();
+  if (chain) {
+    e = cudaEventRecord(T->set_ev[set], s);
+    T->set_used[set] = e == cudaSuccess;
+  }
+  return e;
+}
+}  // namespace
+
+// The field of an item (of its first vector for a tile; tiles of consecutive vectors may cover two).
+namespace {
+void item_fields(const sph_filter_plan_s* p, const int4& w, int* f0, int* f1) {
+  const TcPlan* T = p->tc;
+  if (w.x == tcx::kItemCopy) {
+    *f0 = *f1 = w.y / p->Nr;
+    return;
+  }
+  const TcPass& P = T->pass[w.x];
+  const int half = p->Nph / 2;
+  auto field = [&](long long vg) {
+    if (w.x == tcx::kItemTheta) return P.h_list[(size_t)(vg / half)] / p->Nr;
+    return P.h_list[(size_t)vg] / p->Nth / p->Nr;
+  };
+  *f0 = field(w.y);
+  *f1 = field((long long)w.y + w.z - 1);
 }
 }  // namespace
 
@@ -944,33 +1196,57 @@ cudaError_t tc_launch(sph_filter_plan_s* p, const double* in, double* out, int t
   int dummy = 0;
   if (!nlaunch) nlaunch = &dummy;
   *nlaunch = 0;
-  const size_t shell = (size_t)p->Nth * p->Nph, field = shell * p->Nr;
-  if (!transpose) {
-    // theta pass in -> out (identity shells copied), then the phi pass in place (Sec. II.C order)
-    if (in != out) {
-      const std::vector<int>& runs = p->tc->pass[0].copy_runs;
-      for (size_t n = 0; n + 2 < runs.size(); n += 3) {
-        const int v = runs[n], i0 = runs[n + 1], cnt = runs[n + 2];
-        if (v < var_begin || v >= var_begin + var_count) continue;
-        const size_t off = field * v + shell * i0;
-        const cudaError_t e =
-            cudaMemcpyAsync(out + off, in + off, sizeof(double) * shell * cnt, cudaMemcpyDeviceToDevice, s);
+  TcPlan* T = p->tc;
+  const int4* items = T->d_items;
+  int n_fused = T->n_fused, n_theta = T->n_theta, n_phi = T->n_phi;
+  if (var_begin != 0 || var_count != p->nvars) {
+    // a field range (e.g. one chunk of the host-buffer pipeline): the items that touch it
+    std::lock_guard<std::mutex> lock(T->mu);
+    auto it = T->ranges.find({var_begin, var_count});
+    if (it == T->ranges.end()) {
+      TcPlan::RangeItems R;
+      std::vector<int4> sel;
+      const int ve = var_begin + var_count;
+      const int bounds[4] = {0, T->n_fused, T->n_fused + T->n_theta, T->n_fused + T->n_theta + T->n_phi};
+      int counts[3] = {0, 0, 0};
+      for (int part = 0; part < 3; ++part)
+        for (int i = bounds[part]; i < bounds[part + 1]; ++i) {
+          int f0, f1;
+          item_fields(p, T->h_items[(size_t)i], &f0, &f1);
+          if (f1 < var_begin || f0 >= ve) continue;
+          sel.push_back(T->h_items[(size_t)i]);
+          ++counts[part];
+        }
+      if (!sel.empty()) {
+        if (cudaMalloc((void**)&R.d, sel.size() * sizeof(int4)) != cudaSuccess) return cudaErrorMemoryAllocation;
+        const cudaError_t e = cudaMemcpy(R.d, sel.data(), sel.size() * sizeof(int4), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return e;
       }
+      R.n_fused = counts[0];
+      R.n_theta = counts[1];
+      R.n_phi = counts[2];
+      it = T->ranges.emplace(std::make_pair(var_begin, var_count), R).first;
     }
-    const cudaError_t e = launch_pass(p, 0, in, out, var_begin, var_count, s, nlaunch);
-    if (e != cudaSuccess) return e;
-    return launch_pass(p, 1, out, out, var_begin, var_count, s, nlaunch);
+    items = it->second.d;
+    n_fused = it->second.n_fused;
+    n_theta = it->second.n_theta;
+    n_phi = it->second.n_phi;
+  }
+  if (!transpose) {
+    // one launch: theta tiles in -> out, phi tiles of shells with a theta pass out -> out after them,
+    // the others in -> out, and copies of the rings no pass changes (Sec. II.C order)
+    return launch_items(p, items, n_fused, 1, in, out, var_begin, var_count, s, nlaunch);
   }
   // transpose: phi pass, then theta pass, both in place on out
+  const size_t field = (size_t)p->Nth * p->Nph * p->Nr;
   if (in != out) {
     const cudaError_t e = cudaMemcpyAsync(out + field * var_begin, in + field * var_begin,
                                           sizeof(double) * field * var_count, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return e;
   }
-  const cudaError_t e = launch_pass(p, 1, out, out, var_begin, var_count, s, nlaunch);
+  const cudaError_t e = launch_items(p, items + n_fused + n_theta, n_phi, 0, out, out, var_begin, var_count, s, nlaunch);
   if (e != cudaSuccess) return e;
-  return launch_pass(p, 0, out, out, var_begin, var_count, s, nlaunch);
+  return launch_items(p, items + n_fused, n_theta, 0, out, out, var_begin, var_count, s, nlaunch);
 }
 
 }  // namespace sph
