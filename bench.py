@@ -104,31 +104,58 @@ def algorithmic_flops(grid) -> float:
     return flops
 
 
-def tc_slice_products(L: int) -> float:
-    """Flops of the tensor-core form's four GEMMs for one vector of length L (unpadded sizes): with
-    H = L/2, cos forward H x (H+1), sin forward (H-1) x (H-1), and the same two inverse, each run
-    for the 21 slice pairs a + b <= 5 of six-slice operands, 2 flops per multiply-add."""
-    H = L // 2
-    return 21 * 2.0 * (2 * H * (H + 1) + 2 * (H - 1) ** 2)
+def tc_blocks(L: int):
+    """The split-precision form's GEMM shapes for vectors of length L, as the plan builds them: levels
+    while L/2^l is divisible by 4 with a quarter of at least 16 and a half of at least 32 (each level's
+    two halves fill the 128 rows of one GEMM, K = N = the quarter padded to 16), then the base of length
+    nb split into two halves of nb/2 (side by side in one GEMM with N = 2K when that needs no more than
+    256 tensor-memory columns or the separate form's, else two GEMMs). Returns [(K, N, gemms)]."""
+    pad = lambda n: (n + 15) // 16 * 16
+    shapes, n = [], L
+    while n % 4 == 0 and n // 4 >= 16 and n // 2 >= 32:
+        shapes.append((pad(n // 4), pad(n // 4), 1))
+        n //= 2
+    kb = pad(n // 2)
+    KA = max([kb] + [k for k, _, _ in shapes])
+    NA = max([kb] + [nn for _, nn, _ in shapes])
+
+    def cols(ka, na):
+        c = 32
+        while c < 3 * ka + 5 * na:
+            c *= 2
+        return c
+    c_with = cols(KA, max(NA, 2 * kb))
+    if c_with <= max(cols(KA, NA), 256) and c_with <= 512:
+        shapes.append((kb, 2 * kb, 1))
+    else:
+        shapes.append((kb, kb, 2))
+    return shapes
+
+
+def tc_tile_flops(L: int, factored: bool) -> float:
+    """Tensor-core flops of one tile of 64 vectors: every GEMM runs 128 rows (two per vector) for the
+    21 digit pairs a + b <= 5, 2 flops per multiply-add; the factored form runs each block twice
+    (forward to the modes and back)."""
+    f = sum(g * 128.0 * K * N * 21 * 2 for K, N, g in tc_blocks(L))
+    return 2 * f if factored else f
 
 
 def tc_tensor_flops(grid) -> float:
-    """Tensor-core flops of one application of the split-precision form: every active theta shell
-    contributes Nphi/2 doubled circles of length 2 Ntheta, every active ring one vector of length
-    Nphi (the same activity rule as the FFT form)."""
-    flops = 0.0
+    """Tensor-core flops of one application of the split-precision form: theta tiles of 64 doubled
+    circles of the active shells (direct form, one GEMM per block, when Nphi/2 is a multiple of 64,
+    else factored), phi tiles of 64 active rings (factored), with the activity rule of the FFT form."""
     th = (np.arange(grid.Ntheta) + 0.5) * math.pi / grid.Ntheta
-    f_th, f_ph = tc_slice_products(2 * grid.Ntheta), tc_slice_products(grid.Nphi)
+    circles, rings = 0, 0
     for v in range(grid.nvars):
         for i in range(grid.Nr):
             lm = max(grid.floor, 2 * grid.r[i] / grid.dr_min * grid.L[v])
             gauss = grid.kind[v] == W.GAUSS
             if gauss or lm < grid.Ntheta:
-                flops += grid.Nphi // 2 * f_th
+                circles += grid.Nphi // 2
             mm = np.maximum(grid.floor, 2 * grid.r[i] / grid.dr_min * np.sin(th) * grid.L[v])
-            nact = grid.Ntheta if gauss else int((mm < grid.Nphi / 2).sum())
-            flops += nact * f_ph
-    return flops
+            rings += grid.Ntheta if gauss else int((mm < grid.Nphi / 2).sum())
+    direct = (grid.Nphi // 2) % 64 == 0
+    return (-(-circles // 64)) * tc_tile_flops(2 * grid.Ntheta, not direct) + (-(-rings // 64)) * tc_tile_flops(grid.Nphi, True)
 
 
 class ClockSampler:
@@ -317,17 +344,19 @@ def _timed(fn, steps, warmup, stream):
 
 def run_batch(args):
     """Six uneven grids (28 fields each) filtered three times per step (one filter per RK3 substep),
-    replayed as one CUDA graph per step; every plan autotuned first."""
+    replayed as one CUDA graph per step. Tensor-core plans run all six grids in one persistent launch
+    per application; the plain forms' plans are autotuned and run one launch set per grid."""
     import torch
-    from paper_2305_01537_gb300 import Batch, Plan, SPH_PREC_F64, SPH_PREC_F32X2
-    prec = SPH_PREC_F32X2 if args.precision == "f32x2" else SPH_PREC_F64
+    from paper_2305_01537_gb300 import Batch, Plan, SPH_PREC_F64, SPH_PREC_F32X2, SPH_PREC_SPLIT_TC
+    prec = {"f64": SPH_PREC_F64, "f32x2": SPH_PREC_F32X2, "tc": SPH_PREC_SPLIT_TC}[args.precision]
     wl = W.batched_six_grids()
     xs, outs, plans = [], [], []
     for n, g in enumerate(wl.grids):
         xs.append(torch.from_numpy(wl.state(n)).cuda())
         outs.append(torch.empty_like(xs[-1]))
         plans.append(Plan.from_grid(g, precision=prec))
-        plans[-1].autotune(xs[-1], outs[-1])
+        if prec != SPH_PREC_SPLIT_TC:
+            plans[-1].autotune(xs[-1], outs[-1])
     b = Batch(plans)
     stream = torch.cuda.current_stream()
     captured0 = sum(p.launch_count for p in plans)
@@ -344,12 +373,16 @@ def run_batch(args):
     print(json.dumps({
         "metric": "filtered Gpoints/s (theta+phi double FFT filter, FP64 I/O)", "value": value, "unit": "Gpoints/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAME[args.precision],
+        "data": "synthetic",
         "config": {"workload": wl.name, "grids": [[g.Nr, g.Ntheta, g.Nphi, g.nvars] for g in wl.grids],
                    "applications_per_step": 3, "precision": args.precision,
-                   "launch": "one CUDA graph per step (per-grid kernels on parallel branches)"},
+                   "launch": ("one CUDA graph per step: one persistent launch per application over all six grids"
+                              if prec == SPH_PREC_SPLIT_TC else
+                              "one CUDA graph per step (per-grid kernels on parallel branches)")},
         "hbm": {"achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"], "frac": gbs / peaks["hbm_gbs"], "peak_source": src},
-        "gpu_launches": args.steps * per_graph, "clocks": clk.summary()}), flush=True)
+        "gpu_launches": args.steps * per_graph, "launches_per_application": per_graph / 3,
+        "clocks": clk.summary()}), flush=True)
     return 0
 
 
@@ -660,7 +693,7 @@ def main():
 
         def label_for(p, pl):
             if p == "tc":
-                return "tc kernels of one application (theta and phi passes, copies of identity shells)"
+                return "tc_pass_kernel: one persistent launch per application (theta tiles, phi tiles, copies)"
             name = {"f64": "F64", "f32x2": "DF"}[p]
             if pl.launches < 3:
                 return f"shell_kernel<{name}>"

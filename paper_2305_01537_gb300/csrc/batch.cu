@@ -14,6 +14,7 @@ struct sph_filter_batch_s {
   cudaStream_t cap = nullptr;         // capture stream
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  sph::TcBatch* tcb = nullptr;        // every plan in the tensor-core form: one launch for all grids
 };
 
 namespace {
@@ -28,6 +29,7 @@ void drop_graph(sph_filter_batch_s* b) {
 void free_batch(sph_filter_batch_s* b) {
   if (!b) return;
   drop_graph(b);
+  sph::tc_batch_free(b->tcb);
   for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
   for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
@@ -35,8 +37,17 @@ void free_batch(sph_filter_batch_s* b) {
   delete b;
 }
 
-// Fork from `s` to the per-grid streams, filter every grid, join back into `s`.
+// Filter every grid: one persistent launch over all grids for tensor-core plans; otherwise fork from
+// `s` to the per-grid streams, launch each plan and join back into `s`.
 sph_status enqueue(sph_filter_batch_s* b, const double* const* in, double* const* out, cudaStream_t s) {
+  if (b->tcb) {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != b->device) cudaSetDevice(b->device);
+    const cudaError_t e = sph::tc_batch_launch(b->tcb, in, out, s);
+    if (cur != b->device) cudaSetDevice(cur);
+    return e == cudaSuccess ? SPH_OK : SPH_ECUDA;
+  }
   if (cudaEventRecord(b->fork, s) != cudaSuccess) return SPH_ECUDA;
   for (size_t g = 0; g < b->plans.size(); ++g) {
     if (cudaStreamWaitEvent(b->streams[g], b->fork, 0) != cudaSuccess) return SPH_ECUDA;
@@ -109,6 +120,12 @@ sph_status sph_filter_batch_create(sph_filter_batch* out, int nplans, const sph_
     if (s) b->streams.push_back(s);
     if (e) b->joins.push_back(e);
     b->plans.push_back(plans[g]);
+  }
+  bool all_tc = true;
+  for (int g = 0; g < nplans; ++g) all_tc &= plans[g]->tc != nullptr;
+  if (ok && all_tc) {
+    const sph_status st = sph::tc_batch_setup(&b->tcb, b->plans.data(), nplans);
+    if (st != SPH_OK && st != SPH_EUNSUPPORTED) ok = false;  // unsupported: per-grid launches instead
   }
   if (cur >= 0) cudaSetDevice(cur);
   if (!ok) {

@@ -259,6 +259,13 @@ sph_status tc_reserve_pipeline(sph_filter_plan_s* p);
 cudaError_t tc_launch(sph_filter_plan_s* p, const double* in, double* out, int transpose, int var_begin,
                       int var_count, cudaStream_t s, int set, int* nlaunch = nullptr);
 
+// Several tensor-core plans filtered by one persistent launch per application (tc.cu): a merged work
+// list over the grids and one set of counters (launches of one batch must not overlap).
+struct TcBatch;
+sph_status tc_batch_setup(TcBatch** out, sph_filter_plan_s* const* plans, int nplans);
+void tc_batch_free(TcBatch* b);
+cudaError_t tc_batch_launch(TcBatch* b, const double* const* in, double* const* out, cudaStream_t s);
+
 // Enqueue one filter application of a plan (validates pointers; see sph_filter_apply).
 sph_status launch_plan(sph_filter_plan_s* p, const void* in, const void* aux, void* out, int map_in, int map_out,
                        int transpose, int is_f32, cudaStream_t stream);

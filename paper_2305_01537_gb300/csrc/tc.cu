@@ -83,12 +83,37 @@ struct TcArgs {
   const unsigned char* dops;
   const uint32_t* dop_off;
   const int8_t* dpb;
-  const int4* items;
-  int nitems;
   const unsigned char* shell_th;   // [nvars * Nr]: the shell has a theta pass
-  int* counters;                   // [0] next item, [1] CTAs finished, [2 + shell] theta circles done
+  int* circles;                    // [nvars * Nr]: theta circles done in this application
   int nshells;
   unsigned* status;
+};
+
+// Sizes the kernel is launched for (the largest over its passes and grids).
+struct KShape {
+  int Lmax;
+  uint32_t opmax;
+  int tmem_cols;
+};
+
+// One plan's application.
+struct PlanArgs {
+  TcArgs a;
+  KShape shape;
+  const int4* items;
+  int nitems;
+  int* work;                       // [0] next item, [1] CTAs finished
+};
+
+// Several plans' applications in one launch: item.x = type | grid << 4.
+constexpr int kMaxGrids = 8;
+struct BatchArgs {
+  TcArgs g[kMaxGrids];
+  int ngrids;
+  KShape shape;
+  const int4* items;
+  int nitems;
+  int* work;
 };
 
 struct Ctl {
@@ -256,7 +281,7 @@ __device__ __forceinline__ long long elem_off(const TcArgs& A, int pass, long lo
 }
 
 struct Kern {
-  const TcArgs& A;
+  const TcArgs* A;           // the current item's grid
   const PassDesc* d;         // the current tile's pass
   int pass;
   Ctl& C;
@@ -543,8 +568,8 @@ __device__ void base_fwd(Kern& k, int nb, bool convert) {
 // parity sign of a circle's second meridian applied to the integer).
 __device__ __forceinline__ void put_out(const Kern& k, int v, int q, long long x, int expo) {
   const RowInfo& R = k.C.row[v];
-  if (k.pass == 0 && R.neg && q >= k.A.Nth) x = -x;
-  k.A.out[elem_off(k.A, k.pass, R.base, q)] = from_fixed(x, expo);
+  if (k.pass == 0 && R.neg && q >= k.A->Nth) x = -x;
+  k.A->out[elem_off(*k.A, k.pass, R.base, q)] = from_fixed(x, expo);
 }
 
 // Inverse base stage: values become 2 v; `out` writes them to the destination (no levels).
@@ -617,11 +642,15 @@ __device__ void copy_rings(const TcArgs& A, int shell, int j0, int nj) {
   for (; i < n16; i += blockDim.x) __stcs(d + i, __ldcs(s + i));
 }
 
-__global__ void __launch_bounds__(512, 1) tc_pass_kernel(const __grid_constant__ TcArgs A) {
+// The persistent loop over work items, shared by the one-plan and the several-plan kernels: grids[g]
+// holds the arguments of grid g (item.x >> 4 when MULTI, else 0).
+template <bool MULTI>
+__device__ __forceinline__ void run_items(const TcArgs* grids, int ngrids, const KShape& shape, const int4* items,
+                                          int nitems, int* work) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  const int Lmax = max(A.pd[0].L, A.pd[1].L);
-  const uint32_t opmax = max(A.pd[0].op_max, A.pd[1].op_max);
-  const int tmem_cols = max(A.pd[0].tmem_cols, A.pd[1].tmem_cols);
+  const int Lmax = shape.Lmax;
+  const uint32_t opmax = shape.opmax;
+  const int tmem_cols = shape.tmem_cols;
   unsigned char* opbuf = smem;
   long long* store = reinterpret_cast<long long*>(smem + ((opmax + 1023) / 1024) * 1024);
   Ctl& C = *reinterpret_cast<Ctl*>(store + (size_t)kV * (Lmax + 1));
@@ -641,20 +670,23 @@ __global__ void __launch_bounds__(512, 1) tc_pass_kernel(const __grid_constant__
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  Kern k{A, &A.pd[0], 0, C, opbuf, store, 0, C.tslot, tid, warp, lane, warp & 3, warp >> 2, (int)(blockDim.x / 128),
+  Kern k{grids, &grids[0].pd[0], 0, C, opbuf, store, 0, C.tslot, tid, warp, lane, warp & 3, warp >> 2, (int)(blockDim.x / 128),
          0, 0, 0, 0u, 0u};
   k.r = 32 * k.lq + lane;
   k.h = k.r >> 6;
   k.v = k.r & (kV - 1);
-  const int half = A.Nph / 2;
   for (int n = 0;; ++n) {
     // two slots: a slot is rewritten two iterations later, after a barrier every thread passed
     // having read it
-    if (tid == 0) C.item[n & 1] = atomicAdd(&A.counters[0], 1);
+    if (tid == 0) C.item[n & 1] = atomicAdd(&work[0], 1);
     __syncthreads();
     const int it = C.item[n & 1];
-    if (it >= A.nitems || C.abort) break;
-    const int4 w = A.items[it];
+    if (it >= nitems || C.abort) break;
+    int4 w = items[it];
+    const TcArgs& A = grids[MULTI ? (w.x >> 4) : 0];
+    w.x &= 15;
+    k.A = &A;
+    const int half = A.Nph / 2;
     if (w.x == kItemCopy) {
       const int v = w.y / A.Nr;
       if (A.in != A.out && v >= A.var_begin && v < A.var_end) copy_rings(A, w.y, w.z, w.w);
@@ -705,7 +737,7 @@ __global__ void __launch_bounds__(512, 1) tc_pass_kernel(const __grid_constant__
           const bool after_theta = A.fused && A.shell_th[shell];
           R.src = after_theta ? A.out : A.in;
           if (after_theta && vv >= A.var_begin && vv < A.var_end &&
-              !wait_circles(A.counters + 2 + shell, half))
+              !wait_circles(A.circles + shell, half))
             C.abort = 1;
         }
         R.shell = shell;
@@ -804,27 +836,37 @@ __global__ void __launch_bounds__(512, 1) tc_pass_kernel(const __grid_constant__
     if (pass == 0) {
       __threadfence();
       __syncthreads();
-      if (tid < kV && C.row[tid].valid) atomicAdd(A.counters + 2 + C.row[tid].shell, 1);
+      if (tid < kV && C.row[tid].valid) atomicAdd(A.circles + C.row[tid].shell, 1);
     }
   }
-  if (C.abort && tid == 0) atomicCAS(A.status, 0u, (unsigned)SPH_ETIMEOUT);
+  if (C.abort && tid == 0)
+    for (int g = 0; g < ngrids; ++g) atomicCAS(grids[g].status, 0u, (unsigned)SPH_ETIMEOUT);
   // the last CTA to finish resets the counters for the next application
   __syncthreads();
   if (tid == 0) {
     __threadfence();
-    C.last = atomicAdd(A.counters + 1, 1) == (int)gridDim.x - 1;
+    C.last = atomicAdd(work + 1, 1) == (int)gridDim.x - 1;
   }
   __syncthreads();
   if (C.last) {
-    for (int i = tid; i < A.nshells; i += blockDim.x) A.counters[2 + i] = 0;
-    if (tid == 0) A.counters[0] = 0;
+    for (int g = 0; g < ngrids; ++g)
+      for (int i = tid; i < grids[g].nshells; i += blockDim.x) grids[g].circles[i] = 0;
+    if (tid == 0) work[0] = 0;
     __threadfence();
     __syncthreads();
-    if (tid == 0) A.counters[1] = 0;
+    if (tid == 0) work[1] = 0;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(C.tslot), "r"(tmem_cols));
+}
+
+__global__ void __launch_bounds__(512, 1) tc_pass_kernel(const __grid_constant__ PlanArgs P) {
+  run_items<false>(&P.a, 1, P.shape, P.items, P.nitems, P.work);
+}
+
+__global__ void __launch_bounds__(512, 1) tc_batch_kernel(const __grid_constant__ BatchArgs B) {
+  run_items<true>(B.g, B.ngrids, B.shape, B.items, B.nitems, B.work);
 }
 
 size_t smem_bytes(const PassDesc& d) {
@@ -864,6 +906,7 @@ struct TcPlan {
   int nsm = 0;
   int threads = 0, ctas_per_sm = 1;
   size_t smem = 0;
+  tcx::KShape shape{};
   int4* d_items = nullptr;          // [fused application | theta tiles | phi tiles], all fields
   int n_fused = 0, n_theta = 0, n_phi = 0;
   std::vector<int4> h_items;        // the same on the host (filtered for calls on a field range)
@@ -1079,6 +1122,7 @@ sph_status tc_setup(sph_filter_plan_s* p) {
   const size_t op = std::max(T->pass[0].d.op_max, T->pass[1].d.op_max);
   const int Lmax = std::max(T->pass[0].d.L, T->pass[1].d.L);
   const int tmem = std::max(T->pass[0].d.tmem_cols, T->pass[1].d.tmem_cols);
+  T->shape = tcx::KShape{Lmax, (uint32_t)op, tmem};
   T->smem = (op + 1023) / 1024 * 1024 + (size_t)tcx::kV * (Lmax + 1) * 8 + sizeof(tcx::Ctl);
   const int optin = max_smem_optin(p->device);
   if ((int)T->smem > optin) return SPH_EUNSUPPORTED;
@@ -1116,12 +1160,9 @@ void tc_free(sph_filter_plan_s* p) {
 sph_status tc_reserve_pipeline(sph_filter_plan_s*) { return SPH_OK; }
 
 namespace {
-// One launch over the work items [first, first + count): the fused application (fused = 1) or one
-// pass (fused = 0), fields [var_begin, var_begin + var_count).
-cudaError_t launch_items(sph_filter_plan_s* p, const int4* items, int count, int fused, const double* in, double* out,
-                         int var_begin, int var_count, cudaStream_t s, int* nlaunch) {
+// The kernel arguments of one plan's application (the work and circle counters are set by the caller).
+tcx::TcArgs plan_args(sph_filter_plan_s* p, int fused, const double* in, double* out, int var_begin, int var_count) {
   TcPlan* T = p->tc;
-  if (count <= 0) return cudaSuccess;
   tcx::TcArgs a{};
   a.Nr = p->Nr;
   a.Nth = p->Nth;
@@ -1142,15 +1183,29 @@ cudaError_t launch_items(sph_filter_plan_s* p, const int4* items, int count, int
   a.dops = T->pass[0].d_dops;
   a.dop_off = T->pass[0].d_dop_off;
   a.dpb = T->pass[0].d_dpb;
-  a.items = items;
-  a.nitems = count;
   a.shell_th = T->d_shell_th;
   a.nshells = T->nshells;
   a.status = p->d_status;
+  return a;
+}
+
+// One launch over the work items [first, first + count): the fused application (fused = 1) or one
+// pass (fused = 0), fields [var_begin, var_begin + var_count).
+cudaError_t launch_items(sph_filter_plan_s* p, const int4* items, int count, int fused, const double* in, double* out,
+                         int var_begin, int var_count, cudaStream_t s, int* nlaunch) {
+  TcPlan* T = p->tc;
+  if (count <= 0) return cudaSuccess;
+  tcx::TcArgs a = plan_args(p, fused, in, out, var_begin, var_count);
+  tcx::PlanArgs pa{};
+  pa.items = items;
+  pa.nitems = count;
+  pa.shape = T->shape;
   // a counter set, after its previous user (except inside a graph capture, which orders its own work)
   std::lock_guard<std::mutex> lock(T->mu);
   const int set = (int)(T->next_set++ % kSets);
-  a.counters = T->d_counters + (size_t)set * (2 + T->nshells);
+  pa.work = T->d_counters + (size_t)set * (2 + T->nshells);
+  a.circles = pa.work + 2;
+  pa.a = a;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   cudaError_t e = cudaStreamIsCapturing(s, &cap);
   if (e != cudaSuccess) return e;
@@ -1160,7 +1215,7 @@ cudaError_t launch_items(sph_filter_plan_s* p, const int4* items, int count, int
     if (e != cudaSuccess) return e;
   }
   const int grid = std::min(count, T->nsm * T->ctas_per_sm);
-  tcx::tc_pass_kernel<<<grid, T->threads, T->smem, s>>>(a);
+  tcx::tc_pass_kernel<<<grid, T->threads, T->smem, s>>>(pa);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   ++*nlaunch;
@@ -1247,6 +1302,110 @@ cudaError_t tc_launch(sph_filter_plan_s* p, const double* in, double* out, int t
   const cudaError_t e = launch_items(p, items + n_fused + n_theta, n_phi, 0, out, out, var_begin, var_count, s, nlaunch);
   if (e != cudaSuccess) return e;
   return launch_items(p, items + n_fused, n_theta, 0, out, out, var_begin, var_count, s, nlaunch);
+}
+
+// ---------------------------------------------------------------- several plans in one launch
+
+struct TcBatch {
+  std::vector<sph_filter_plan_s*> plans;
+  int4* d_items = nullptr;
+  int nitems = 0;
+  int* d_counters = nullptr;        // [0, 2) work, then each grid's circles
+  std::vector<size_t> circ_off;
+  tcx::KShape shape{};
+  int threads = 0, ctas_per_sm = 1;
+  size_t smem = 0;
+};
+
+sph_status tc_batch_setup(TcBatch** out, sph_filter_plan_s* const* plans, int nplans) {
+  *out = nullptr;
+  if (nplans < 1 || nplans > tcx::kMaxGrids) return SPH_EUNSUPPORTED;
+  TcBatch* B = new (std::nothrow) TcBatch();
+  if (!B) return SPH_ENOMEM;
+  // items of every grid, each phase of the fused order merged over the grids, costliest tiles first
+  struct It {
+    int4 w;
+    long long cost;
+  };
+  std::vector<It> ph[3];
+  size_t circ = 2;
+  int ctas = 2;
+  for (int g = 0; g < nplans; ++g) {
+    sph_filter_plan_s* p = plans[g];
+    TcPlan* T = p->tc;
+    B->plans.push_back(p);
+    B->circ_off.push_back(circ);
+    circ += (size_t)T->nshells;
+    // the fused list: theta tiles, then phi tiles and copies without theta results, then the rest
+    for (int i = 0; i < T->n_fused; ++i) {
+      int4 w = T->h_items[(size_t)i];
+      const int phase = w.x == tcx::kItemTheta ? 0 : (w.x == tcx::kItemPhi && w.w) ? 2 : 1;
+      const long long cost = w.x == tcx::kItemCopy ? (long long)w.w * p->Nph / 8
+                                                   : (long long)w.z * (w.x == tcx::kItemTheta ? 2 * p->Nth : p->Nph);
+      w.x |= g << 4;
+      ph[phase].push_back(It{w, cost});
+    }
+    B->shape.Lmax = std::max(B->shape.Lmax, T->shape.Lmax);
+    B->shape.opmax = std::max(B->shape.opmax, T->shape.opmax);
+    B->shape.tmem_cols = std::max(B->shape.tmem_cols, T->shape.tmem_cols);
+    B->threads = std::max(B->threads, T->threads);
+    ctas = std::min(ctas, T->ctas_per_sm);
+  }
+  std::vector<int4> items;
+  for (auto& v : ph) {
+    std::stable_sort(v.begin(), v.end(), [](const It& a, const It& b) { return a.cost > b.cost; });
+    for (const It& x : v) items.push_back(x.w);
+  }
+  B->nitems = (int)items.size();
+  const int device = plans[0]->device;
+  const int optin = max_smem_optin(device);
+  B->smem = ((size_t)B->shape.opmax + 1023) / 1024 * 1024 + (size_t)tcx::kV * (B->shape.Lmax + 1) * 8 + sizeof(tcx::Ctl);
+  if ((int)B->smem > optin) {
+    delete B;
+    return SPH_EUNSUPPORTED;
+  }
+  B->ctas_per_sm = (ctas == 2 && B->shape.tmem_cols <= 256 && B->threads <= 256 && 2 * (B->smem + 1024) <= (size_t)optin) ? 2 : 1;
+  B->smem = std::min(std::max(B->smem, (size_t)optin / (B->ctas_per_sm + 1) + 1024), (size_t)optin);
+  bool ok = cudaMalloc((void**)&B->d_items, items.size() * sizeof(int4)) == cudaSuccess &&
+            cudaMemcpy(B->d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMalloc((void**)&B->d_counters, circ * sizeof(int)) == cudaSuccess &&
+            cudaMemset(B->d_counters, 0, circ * sizeof(int)) == cudaSuccess &&
+            cudaFuncSetAttribute(tcx::tc_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->smem) ==
+                cudaSuccess;
+  if (!ok) {
+    tc_batch_free(B);
+    return SPH_ECUDA;
+  }
+  *out = B;
+  return SPH_OK;
+}
+
+void tc_batch_free(TcBatch* B) {
+  if (!B) return;
+  cudaFree(B->d_items);
+  cudaFree(B->d_counters);
+  delete B;
+}
+
+cudaError_t tc_batch_launch(TcBatch* B, const double* const* in, double* const* out, cudaStream_t s) {
+  tcx::BatchArgs ba{};
+  ba.ngrids = (int)B->plans.size();
+  for (int g = 0; g < ba.ngrids; ++g) {
+    sph_filter_plan_s* p = B->plans[(size_t)g];
+    ba.g[g] = plan_args(p, 1, in[g], out[g], 0, p->nvars);
+    ba.g[g].circles = B->d_counters + B->circ_off[(size_t)g];
+  }
+  ba.shape = B->shape;
+  ba.items = B->d_items;
+  ba.nitems = B->nitems;
+  ba.work = B->d_counters;
+  const int nsm = B->plans[0]->tc->nsm;
+  const int grid = std::min(B->nitems, nsm * B->ctas_per_sm);
+  if (grid <= 0) return cudaSuccess;
+  tcx::tc_batch_kernel<<<grid, B->threads, B->smem, s>>>(ba);
+  const cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) B->plans[0]->launched += 1;
+  return e;
 }
 
 }  // namespace sph

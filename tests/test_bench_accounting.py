@@ -37,14 +37,20 @@ def test_flop_counts_follow_the_oracle_cutoffs(Nr, Nth, Nph):
     shells, rings = active_counts(g)
     fft = shells * Nth * Nph * (5 * math.log2(2 * Nth) + 1) + rings * Nph * (5 * math.log2(Nph) + 1)
     assert bench.algorithmic_flops(g) == pytest.approx(fft, rel=1e-12)
-    tc = shells * (Nph // 2) * bench.tc_slice_products(2 * Nth) + rings * bench.tc_slice_products(Nph)
+    circles, direct = shells * (Nph // 2), (Nph // 2) % 64 == 0
+    tc = -(-circles // 64) * bench.tc_tile_flops(2 * Nth, not direct) + -(-rings // 64) * bench.tc_tile_flops(Nph, True)
     assert bench.tc_tensor_flops(g) == pytest.approx(tc, rel=1e-12)
 
 
-def test_tc_slice_products_counts_the_four_gemms():
-    """Length L = 8 (H = 4): cos forward 4 x 5, sin forward 3 x 3, the same two inverse; 21 slice
-    pairs, 2 flops per multiply-add."""
-    assert bench.tc_slice_products(8) == 21 * 2 * (4 * 5 + 3 * 3 + 4 * 5 + 3 * 3)
+def test_tc_block_shapes():
+    """The GEMM shapes of the symmetry-block form: levels while a quarter of the vector is at least 16
+    (two halves per GEMM, K = N = the padded quarter), then the base halves side by side."""
+    assert bench.tc_blocks(256) == [(64, 64, 1), (32, 32, 1), (16, 16, 1), (16, 32, 1)]
+    assert bench.tc_blocks(128) == [(32, 32, 1), (16, 16, 1), (16, 32, 1)]
+    assert bench.tc_blocks(16) == [(16, 32, 1)]
+    assert bench.tc_blocks(74) == [(48, 48, 2)]  # 37-point halves: two GEMMs (side by side needs 1024 columns)
+    # a 128-point tile, factored: 2 x (128 rows x (32x32 + 16x16 + 16x32)) x 21 pairs x 2 flops
+    assert bench.tc_tile_flops(128, True) == 2 * 128 * (32 * 32 + 16 * 16 + 16 * 32) * 21 * 2
 
 
 def test_traffic_record_names_known_families():
