@@ -566,6 +566,98 @@ def host_copy_ceiling(x_host, stream_a, stream_b, reps=3):
             "both_ways_ms": t_both, "both_ways_gbs_each": nbytes / t_both / 1e6}
 
 
+def measure_workload(wl_name, precisions, steps, warmup, sample_stride):
+    """One single-grid workload at several precisions (same state, out of place): Gpoints/s, ms per
+    application, kernel launches, and the largest per-field error against the oracle on the shells of
+    every `sample_stride`-th radius (the oracle's own output on those shells)."""
+    import torch
+    import oracle
+    from paper_2305_01537_gb300 import Plan, SPH_PREC_F64, SPH_PREC_F32X2, SPH_PREC_SPLIT_TC
+    code = {"f64": SPH_PREC_F64, "f32x2": SPH_PREC_F32X2, "tc": SPH_PREC_SPLIT_TC}
+    wl = single_grid_workload(wl_name)
+    g = wl.grids[0]
+    xh = wl.state()
+    idx = np.arange(0, g.Nr, sample_stride)
+    t0 = time.perf_counter()
+    ref = oracle.filter(np.ascontiguousarray(xh[:, idx]), g.parity, g.kind, g.L, g.r[idx], g.dr_min, g.floor, eps=g.eps)
+    oracle_s = time.perf_counter() - t0
+    x = torch.from_numpy(xh).cuda()
+    del xh
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for p in precisions:
+        plan = Plan.from_grid(g, precision=code[p])
+        ms, kms, launched = time_plan(plan, x, y, steps, warmup, stream)
+        assert plan.sync_status() == 0
+        out[p] = {"value": g.points * steps / (ms * 1e-3) / 1e9, "unit": "Gpoints/s", "ms_per_step": ms / steps,
+                  "dtype": DTYPE_NAME[p], "gpu_launches_per_application": launched / steps,
+                  "max_err_vs_oracle": sample_error(y, idx, ref),
+                  "hbm_frac": 16.0 * g.points / (statistics.mean(kms) * 1e-3) / 1e9 / measured_peaks()[0]["hbm_gbs"]}
+        del plan
+    del x, y
+    torch.cuda.empty_cache()
+    return {"workload": wl.name, "Nr": g.Nr, "Ntheta": g.Ntheta, "Nphi": g.Nphi, "nvars": g.nvars,
+            "points": g.points, "steps": steps, "warmup": warmup,
+            "err_sample": f"every {sample_stride}th radius of all {g.nvars} fields ({len(idx) * g.nvars} shells; "
+                          f"oracle {oracle_s:.1f} s)",
+            "by_precision": out}
+
+
+def measure_batch(steps, warmup):
+    """The six uneven grids, three applications per step as one CUDA graph per step, tensor-core plans
+    (one persistent launch per application over all grids)."""
+    import torch
+    from paper_2305_01537_gb300 import Batch, Plan, SPH_PREC_SPLIT_TC
+    wl = W.batched_six_grids()
+    xs, outs, plans = [], [], []
+    for n, g in enumerate(wl.grids):
+        xs.append(torch.from_numpy(wl.state(n)).cuda())
+        outs.append(torch.empty_like(xs[-1]))
+        plans.append(Plan.from_grid(g, precision=SPH_PREC_SPLIT_TC))
+    b = Batch(plans)
+    stream = torch.cuda.current_stream()
+    c0 = sum(p.launch_count for p in plans)
+    b.capture(xs, outs, 3, stream)
+    per_graph = sum(p.launch_count for p in plans) - c0
+    ms = _timed(lambda: b.launch(stream), steps, warmup, stream)
+    ok = all(p.sync_status() == 0 for p in plans)
+    points = wl.points * 3
+    res = {"workload": wl.name, "grids": [[g.Nr, g.Ntheta, g.Nphi, g.nvars] for g in wl.grids], "precision": "tc",
+           "value": points * steps / (ms * 1e-3) / 1e9, "unit": "Gpoints/s", "ms_per_step": ms / steps,
+           "applications_per_step": 3, "gpu_launches_per_application": per_graph / 3, "status_ok": ok,
+           "steps": steps, "warmup": warmup,
+           "launch": "one CUDA graph per step; one persistent launch per application over all six grids"}
+    del b, plans, xs, outs
+    torch.cuda.empty_cache()
+    return res
+
+
+def measure_chain(precision, steps, warmup):
+    """loss = sum w (F o tanh o ... o F x)^2 over 8 filters on the 8-field 128x64x128 state; one step is
+    the forward chain and its gradient (8 + 8 fused launches)."""
+    import torch
+    from paper_2305_01537_gb300 import Plan, SPH_PREC_F64, SPH_PREC_F32X2
+    from paper_2305_01537_gb300.autograd import chain_loss
+    wl = W.chain_8field()
+    g = wl.grids[0]
+    x = torch.from_numpy(wl.state() * 0.1).cuda()
+    w = torch.from_numpy(W.chain_weights(g)).cuda()
+    plan = Plan.from_grid(g, precision=SPH_PREC_F32X2 if precision == "f32x2" else SPH_PREC_F64)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        xd = x.detach().requires_grad_(True)
+        chain_loss(xd, plan, w, 8).backward()
+
+    n0 = plan.launch_count
+    ms = _timed(step, steps, warmup, stream)
+    per_step = (plan.launch_count - n0) / (steps + warmup)
+    return {"workload": wl.name, "precision": precision, "value": g.points * 16 * steps / (ms * 1e-3) / 1e9,
+            "unit": "Gpoints/s (8 forward + 8 adjoint filter applications per step)", "ms_per_step": ms / steps,
+            "gpu_launches_per_step": per_step, "status_ok": plan.sync_status() == 0, "steps": steps}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -575,6 +667,8 @@ def main():
     ap.add_argument("--precision", default="f64", choices=list(PRECISIONS),
                     help="arithmetic of the headline line (FP64 by default); the others are timed as variants")
     ap.add_argument("--no-variants", action="store_true", help="time the headline precision only")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the other configurations (256x128x256 state, six-grid batch, differentiable chain)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="state28_128x64x128",
                     choices=["state28_128x64x128", "state28_256x128x256", "batch6_uneven", "chain8_128x64x128",
@@ -750,6 +844,18 @@ def main():
                     "gpu_launches": v_launched,
                     "clocks": clk.summary((wall1, wall_end)),
                 }
+        if world == 1 and not args.no_extra and args.workload == "state28_128x64x128":
+            # the other configurations, in the same run (fewer steps: each application is longer)
+            var_runs.clear()
+            x = y = y_primary = None
+            torch.cuda.empty_cache()
+            k = max(3, min(args.steps, 10))
+            line["configs"] = {
+                "state28_256x128x256": measure_workload("state28_256x128x256", ["tc", "f32x2", "f64"], k,
+                                                        args.warmup, 64),
+                "batch6_uneven": measure_batch(k, args.warmup),
+                "chain8_128x64x128": {p: measure_chain(p, k, args.warmup) for p in ("f64", "f32x2")},
+            }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
