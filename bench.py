@@ -59,7 +59,7 @@ KERNEL_FAMILIES = {
     # CUDA sources whose device code each kernel family compiles from
     "plain": ["shell_kernel.cuh", "shell_inst.cu", "shell_dispatch.cu", "filter_plain.cu", "df32.h",
               "capi.cu"],  # capi.cu: which kernels an application launches (the split)
-    "tc": ["tc.cu", "df32.h"],
+    "tc": ["tc.cu", "tc_plan.cu", "tc2_host.h"],
 }
 
 
