@@ -181,6 +181,12 @@ class ClockSampler:
             self._t.start()
         except (OSError, FileNotFoundError):
             self._proc = None
+            return self
+        # nvidia-smi needs a moment before its first sample: wait for it (at most 3 s), so that a
+        # short run still has samples to report
+        t_end = time.time() + 3.0
+        while not self.rows and time.time() < t_end and self._proc.poll() is None:
+            time.sleep(0.02)
         return self
 
     def _read(self):

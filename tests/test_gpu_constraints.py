@@ -86,3 +86,22 @@ def test_full_size_sampled(torch_cuda):
         ref = reference(xs, flags[i:i + 1])
         assert np.abs(y[H, i:i + 1] - ref[H]).max() <= 1e-13
         assert np.abs(y[A, i:i + 1] - ref[A]).max() <= 1e-13 * np.abs(ref[A]).max()
+
+
+def test_values_outside_the_pair_range(torch_cuda):
+    """Points with a value the compensated FP32 pairs cannot hold to full relative precision (tiny
+    metric perturbations, huge curvature) take the FP64 path; the others the pairs. Both agree with
+    the oracle point by point."""
+    from paper_2305_01537_gb300 import enforce_constraints
+    torch = torch_cuda
+    x, flags = make_state(4, 8, 16, seed=123)
+    x[H[1], 0, :2] = 1e-30        # below the pairs' range
+    x[A[3], 1, :3] = 3e13         # above it
+    x[A[0], 2, 0, 0] = 0.0        # zero stays on the pair path
+    ref = reference(x, None)
+    xd = torch.from_numpy(x).cuda()
+    enforce_constraints(xd, H, A, ALPHA, None, 0.3)
+    y = xd.cpu().numpy()
+    scale_a = np.abs(ref[A]).max(axis=(1, 2, 3), keepdims=True)
+    assert np.abs(y[H] - ref[H]).max() <= 1e-13
+    assert (np.abs(y[A] - ref[A]) / scale_a).max() <= 1e-13
