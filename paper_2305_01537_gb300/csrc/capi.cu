@@ -212,13 +212,24 @@ sph_status setup_v2(sph_filter_plan_s* p) {
         }
       }
     }
+  // twiddles stage by stage, in the order of the kernels' radix sequence: the stage that follows
+  // Ns points already combined, with radix R, holds exp(-2 pi i t kk / (Ns R)) at entry
+  // kk (R - 1) + t - 1 (kk < Ns, 1 <= t < R); the tables add up to N - 1 entries
   for (int t = 0; t < 2; ++t) {
     const int N = t == 0 ? 2 * Nth : Nph;
     const size_t o = t == 0 ? o_tth : o_tph;
-    for (int n = 0; n < N; ++n) {
-      const long double ang = 2.0L * pi * (long double)n / (long double)N;
-      W.real(o + 16 * (size_t)n, cosl(ang));
-      W.real(o + 16 * (size_t)n + 8, -sinl(ang));
+    const Factors f = kernel_radices(a, N, p->precision);
+    size_t e = 0;
+    int Ns = 1;
+    for (int s = 0; s < f.nst; ++s) {
+      const int R = f.radix[s];
+      for (int kk = 0; kk < Ns; ++kk)
+        for (int q = 1; q < R; ++q, ++e) {
+          const long double ang = 2.0L * pi * (long double)(q * kk) / (long double)(Ns * R);
+          W.real(o + 16 * e, cosl(ang));
+          W.real(o + 16 * e + 8, -sinl(ang));
+        }
+      Ns *= R;
     }
   }
   W.real(o_con, sqrtl(0.5L));

@@ -175,6 +175,7 @@ cudaError_t launch_copy_shells(const double* in, double* out, const int* list, i
 
 size_t shell_smem_bytes(const ShellArgs2& a, int precision);
 int fixed_length(const ShellArgs2& a);
+Factors kernel_radices(const ShellArgs2& a, int N, int precision);
 cudaError_t launch_shell(const ShellArgs2& a, int precision, int threads, size_t smem, const LaunchIO& io,
                          cudaStream_t s);
 cudaError_t set_shell_smem_attr(int device);

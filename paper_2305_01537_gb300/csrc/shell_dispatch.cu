@@ -10,6 +10,24 @@ int fixed_length(const ShellArgs2& a) {
   return 0;
 }
 
+// The radix sequence the compiled kernels run for a transform of length N (2 Ntheta or Nphi): the
+// compiled sequence of run_pass for the fixed lengths, else the plan's factorisation. The twiddle
+// tables are laid out stage by stage in this order.
+Factors kernel_radices(const ShellArgs2& a, int N, int precision) {
+  Factors f = N == 2 * a.Nth ? a.f_th : a.f_ph;
+  const int L = fixed_length(a);
+  if (L != 0) {
+    static const int r32[] = {8, 4}, r64[] = {8, 8}, r96[] = {8, 4, 3}, r128d[] = {8, 4, 4}, r128[] = {8, 8, 2},
+                     r192[] = {8, 8, 3}, r256[] = {8, 8, 4};
+    const int* r = L == 32 ? r32 : L == 64 ? r64 : L == 96 ? r96 : L == 192 ? r192 : L == 256 ? r256
+                 : (precision == SPH_PREC_F32X2 ? r128d : r128);
+    f.n = L;
+    f.nst = L == 32 || L == 64 ? 2 : 3;
+    for (int s = 0; s < f.nst; ++s) f.radix[s] = r[s];
+  }
+  return f;
+}
+
 size_t shell_smem_bytes(const ShellArgs2& a, int precision) {
   return precision == SPH_PREC_F32X2 ? shellk::smem_impl<shellk::DF>(a) : shellk::smem_impl<shellk::F64>(a);
 }

@@ -3,7 +3,8 @@
 //
 // One CTA filters one (field, shell) pair; two CTAs share an SM where shared memory allows, so that
 // one CTA's copies and barriers overlap the other's arithmetic. The shell (Ntheta x Nphi values) is
-// staged once in shared memory (cp.async, 16-byte pieces). The sequences of a pass are transformed
+// staged once in shared memory: by bulk copies of its rows (TMA engine, one mbarrier) in the FP64
+// form, by 16-byte cp.async in the compensated-FP32 form. The sequences of a pass are transformed
 // in batches; the FFT stages ping-pong between the shell's own memory (each sequence's slots,
 // below) and a scratch buffer with a linear layout: a thread reads a butterfly's inputs from one,
 // writes its outputs to the other, and needs one barrier per stage.
@@ -46,6 +47,58 @@ namespace sph {
 namespace shellk {
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// ------------------------------------------------------------------ bulk copies (TMA engine)
+
+constexpr long long kBarWaitLimit = 1LL << 24;  // bounded mbarrier polls (about a second at most)
+
+__device__ __forceinline__ void bar_init(uint32_t bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// One try of the phase with the given parity (acquire: the copies that completed it are visible).
+__device__ __forceinline__ bool bar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
+  for (long long it = 0; it < kBarWaitLimit; ++it)
+    if (bar_try(bar, parity)) return true;
+  return false;
+}
+// The phase's single arrival, with the bytes its copies will deliver.
+__device__ __forceinline__ void bar_expect(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned) from global to this
+// CTA's shared memory, completing on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+// Thread 0 waits (bounded) for the shell's bulk copies; every thread then observes the completed
+// phase. A wait that runs out latches SPH_ETIMEOUT and waits once more for the copies in flight;
+// false (the same in every thread) if they never completed.
+__device__ __forceinline__ bool wait_copies(unsigned* status, uint32_t bar, int* flag) {
+  if (threadIdx.x == 0) {
+    int bad = 0;
+    if (!bar_wait(bar, 0)) {
+      atomicCAS(status, 0u, (unsigned)SPH_ETIMEOUT);
+      bad = bar_wait(bar, 0) ? 0 : 1;
+    }
+    *flag = bad;
+  }
+  __syncthreads();
+  if (*flag) return false;
+  bar_try(bar, 0);
+  return true;
+}
 
 // ------------------------------------------------------------------ arithmetic policies
 
@@ -523,7 +576,9 @@ struct PhiSplitAcc {
 enum { kFirst = 1, kLast = 2, kMul = 4 };
 
 // One radix-R Stockham stage over all B sequences: from the shell slots to the scratch (FROM_SLOTS)
-// or back. kFirst reads the logical sequence out of the shell layout, kLast writes it back there,
+// or back. tw is the stage's own twiddle table: entry kk (R - 1) + t - 1 holds exp(-2 pi i t kk /
+// (Ns R)), so the R - 1 twiddles of a butterfly are adjacent and the threads of a quarter warp (kk
+// consecutive) read entries R - 1 apart: different banks for R = 2, 4, 8. kFirst reads the logical sequence out of the shell layout, kLast writes it back there,
 // kMul multiplies each input by the spectral multiplier (sequences flagged `general` were
 // multiplied before, by general_multiply).
 template <class P, class Acc, int R, int DIR, int MODE, bool FROM_SLOTS>
@@ -532,7 +587,6 @@ __device__ __forceinline__ void stage(const Acc& A, int N, int B, int Ns, uint32
   using X = Cx<P>;
   const int NR = N / R;
   const int total = B * NR;
-  const int tws = N / (Ns * R);
 #pragma unroll 1
   for (int w = threadIdx.x; w < total; w += blockDim.x) {
     const int bl = w / NR, j = w - bl * NR;
@@ -550,7 +604,7 @@ __device__ __forceinline__ void stage(const Acc& A, int N, int B, int Ns, uint32
     if (Ns > 1) {
 #pragma unroll
       for (int t = 1; t < R; ++t) {
-        C wt = P::ld16(tw + 16u * (uint32_t)(t * kk * tws));
+        C wt = P::ld16(tw + 16u * (uint32_t)(kk * (R - 1) + t - 1));
         if (DIR > 0) wt = X::conj(wt);
         v[t] = P::cmul(v[t], wt);
       }
@@ -640,22 +694,26 @@ __device__ void pass_rt(const Acc& A, int N, int B, const Factors& f, uint32_t t
                         bool has_general) {
   // stage g (0-based over forward and inverse) reads the slots when g is even
   int Ns = 1;
+  uint32_t ts = tw;  // the stage's twiddle table (Ns (R - 1) entries)
   for (int s = 0; s < f.nst; ++s) {
     const int R = f.radix[s];
-    if (s == 0) stage_r<P, Acc, -1, kFirst>(R, A, N, B, Ns, tw, k, true);
-    else stage_r<P, Acc, -1, 0>(R, A, N, B, Ns, tw, k, (s & 1) == 0);
+    if (s == 0) stage_r<P, Acc, -1, kFirst>(R, A, N, B, Ns, ts, k, true);
+    else stage_r<P, Acc, -1, 0>(R, A, N, B, Ns, ts, k, (s & 1) == 0);
+    ts += 16u * (uint32_t)(Ns * (R - 1));
     Ns *= R;
   }
   if (has_general) general_multiply<P, Acc>(A, B, (f.nst & 1) == 0);
   Ns = 1;
+  ts = tw;
   for (int s = 0; s < f.nst; ++s) {
     const int R = f.radix[s];
     const bool first = s == 0, last = s == f.nst - 1;
     const bool from_slots = ((f.nst + s) & 1) == 0;
-    if (first && last) stage_r<P, Acc, 1, kMul | kLast>(R, A, N, B, Ns, tw, k, from_slots);
-    else if (first) stage_r<P, Acc, 1, kMul>(R, A, N, B, Ns, tw, k, from_slots);
-    else if (last) stage_r<P, Acc, 1, kLast>(R, A, N, B, Ns, tw, k, from_slots);
-    else stage_r<P, Acc, 1, 0>(R, A, N, B, Ns, tw, k, from_slots);
+    if (first && last) stage_r<P, Acc, 1, kMul | kLast>(R, A, N, B, Ns, ts, k, from_slots);
+    else if (first) stage_r<P, Acc, 1, kMul>(R, A, N, B, Ns, ts, k, from_slots);
+    else if (last) stage_r<P, Acc, 1, kLast>(R, A, N, B, Ns, ts, k, from_slots);
+    else stage_r<P, Acc, 1, 0>(R, A, N, B, Ns, ts, k, from_slots);
+    ts += 16u * (uint32_t)(Ns * (R - 1));
     Ns *= R;
   }
 }
@@ -666,7 +724,7 @@ __device__ __forceinline__ void run_stages(const Acc& A, int N, int B, int Ns, u
   constexpr bool last = sizeof...(Rs) == 0;
   constexpr int MODE = MODE0 | ((DIR > 0 && last) ? kLast : 0);
   stage<P, Acc, R0, DIR, MODE, FROM_SLOTS>(A, N, B, Ns, tw, k);
-  if constexpr (!last) run_stages<P, Acc, DIR, 0, !FROM_SLOTS, Rs...>(A, N, B, Ns * R0, tw, k);
+  if constexpr (!last) run_stages<P, Acc, DIR, 0, !FROM_SLOTS, Rs...>(A, N, B, Ns * R0, tw + 16u * (uint32_t)(Ns * (R0 - 1)), k);
 }
 
 template <class P, class Acc, int... Rs>
@@ -747,6 +805,8 @@ struct Layout {
   unsigned char* circ;     // hybrid fields: detector flags of the theta circles [Nphi/2],
   unsigned char* ring;     //   of the phi rings [Ntheta],
   unsigned char* thsel;    //   and the table choice of each theta sequence [(Nphi/2 + 1)/2]
+  uint32_t bar;            // mbarrier of the shell's bulk copies (8 bytes), then the wait's outcome
+  int* wait_flag;          //   (4 bytes)
 };
 
 // Scratch for one batch: batch_th theta sequences (2 Ntheta slots each) or batch_ph phi pairs
@@ -780,6 +840,9 @@ __device__ Layout<P> carve(const ShellArgs2& A, unsigned char* base) {
   L.circ = take((size_t)(A.Nph / 2 + A.Nth + (A.Nph / 2 + 1) / 2));
   L.ring = L.circ + A.Nph / 2;
   L.thsel = L.ring + A.Nth;
+  unsigned char* b = take(16);
+  L.bar = saddr(b);
+  L.wait_flag = reinterpret_cast<int*>(b + 8);
   return L;
 }
 
@@ -814,10 +877,34 @@ __device__ __forceinline__ bool in_place_sparse(const LaunchIO& io) {
          io.map_out == kOutNone && !io.hybrid;  // hybrid fields: every row may be transformed
 }
 
-// Start the asynchronous copy of shell s into a buffer (16-byte pieces into the padded rows). The
-// sizes are compile-time constants for the fixed lengths.
+// The shell's bulk copies (TMA engine), issued by warp 0: one per row (Nphi values, contiguous in
+// the state) into the padded rows of the buffer (row stride Nphi + 2: 16-byte aligned, Nphi even),
+// all completing on the shell's mbarrier.
 template <int LEN>
-__device__ __forceinline__ void issue_load(const ShellArgs2& A, const LaunchIO& io, int s, unsigned char* buf) {
+__device__ __forceinline__ void issue_shell_copies(const ShellArgs2& A, const LaunchIO& io, int s,
+                                                   const unsigned char* buf, uint32_t bar) {
+  int v, i;
+  const double* src = static_cast<const double*>(io.in) + shell_offset(A, io, s, &v, &i);
+  const int Nth = LEN ? LEN / 2 : A.Nth, Nph = LEN ? LEN : A.Nph, ldS = LEN ? LEN + 2 : A.ldS;
+  const uint32_t lane = threadIdx.x & 31, dst = saddr(buf), row_bytes = 8u * (uint32_t)Nph;
+  if (lane == 0) bar_expect(bar, row_bytes * (uint32_t)Nth);
+  __syncwarp();
+  for (int row = (int)lane; row < Nth; row += 32)
+    bulk_g2s(dst + (uint32_t)(row * ldS) * 8u, src + (size_t)row * Nph, row_bytes, bar);
+}
+
+// Staging policy: the FP64 form stages its shells by bulk copies; the compensated-FP32 form by
+// 16-byte cp.async from every thread, which measured faster there (its two CTAs per SM overlap the
+// copies with each other's arithmetic either way).
+template <class P>
+__host__ __device__ constexpr bool bulk_staging() {
+  return std::is_same<P, F64>::value;
+}
+
+// The shell's copies by 16-byte cp.async from every thread into the padded rows (waited for with
+// cp.async.wait_group).
+template <int LEN>
+__device__ __forceinline__ void issue_shell_async(const ShellArgs2& A, const LaunchIO& io, int s, unsigned char* buf) {
   int v, i;
   const double* src = static_cast<const double*>(io.in) + shell_offset(A, io, s, &v, &i);
   const int Nth = LEN ? LEN / 2 : A.Nth, Nph = LEN ? LEN : A.Nph, ldS = LEN ? LEN + 2 : A.ldS;
@@ -825,9 +912,9 @@ __device__ __forceinline__ void issue_load(const ShellArgs2& A, const LaunchIO& 
   const uint32_t dst = saddr(buf);
   for (int c = threadIdx.x; c < total; c += blockDim.x) {
     const int row = c / half, k2 = c - row * half;
-    const uint32_t d = dst + (uint32_t)(row * ldS + 2 * k2) * 8u;
-    const double* g = src + (size_t)row * Nph + 2 * k2;
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(g) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + (uint32_t)(row * ldS + 2 * k2) * 8u),
+                 "l"(src + (size_t)row * Nph + 2 * k2)
+                 : "memory");
   }
 }
 
@@ -1027,8 +1114,16 @@ __device__ __noinline__ void detect_shell(const G g, bool odd, double eps, float
 // HYB: the kernel variant for launches with hybrid fields (the other variant has none of their code).
 template <class P, int LEN, bool HYB>
 __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layout<P>& L, unsigned char* buf, int s,
-                             const Consts<P>& K) {
+                             const Consts<P>& K, bool copies_issued) {
   constexpr bool dfp = std::is_same<P, DF>::value;
+  // the shell's bulk copies (issued by the kernel, or below by an in-place call) are awaited once,
+  // where the values are first needed
+  bool pending = copies_issued;
+  auto arrived = [&]() -> bool {
+    if (!pending) return true;
+    pending = false;
+    return wait_copies(A.status, L.bar, L.wait_flag);
+  };
   int v, i;
   const size_t off = shell_offset(A, io, s, &v, &i);
   const VarInfo vi = A.var[v];
@@ -1075,6 +1170,7 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
   if (hyb) {
     // a hybrid field's choices come from the whole FP64 shell: wait for it, run the detector
     asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (!arrived()) return;
     __syncthreads();
     DetShell<LEN> geo;
     geo.S = saddr(buf);
@@ -1152,17 +1248,31 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
       asm volatile("cp.async.wait_all;" ::: "memory");
       return;
     }
-    const double* src = static_cast<const double*>(io.in) + off;
-    const uint32_t dst = saddr(buf);
-    for (int c = threadIdx.x; c < na * (Nph / 2); c += blockDim.x) {
-      const int row = (int)L.arow[c / (Nph / 2)], k2 = c % (Nph / 2);
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + (uint32_t)(row * ld + 2 * k2) * 8u),
-                   "l"(src + (size_t)row * Nph + 2 * k2)
-                   : "memory");
+    // copies of the transformed rows only (bulk: warp 0, one per row)
+    if (!bulk_staging<P>()) {
+      const double* src = static_cast<const double*>(io.in) + off;
+      const uint32_t dst = saddr(buf);
+      for (int c = threadIdx.x; c < na * (Nph / 2); c += blockDim.x) {
+        const int row = (int)L.arow[c / (Nph / 2)], k2 = c % (Nph / 2);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + (uint32_t)(row * ld + 2 * k2) * 8u),
+                     "l"(src + (size_t)row * Nph + 2 * k2)
+                     : "memory");
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    } else if (threadIdx.x < 32) {
+      const double* src = static_cast<const double*>(io.in) + off;
+      const uint32_t dst = saddr(buf), row_bytes = 8u * (uint32_t)Nph;
+      if (threadIdx.x == 0) bar_expect(L.bar, row_bytes * (uint32_t)na);
+      __syncwarp();
+      for (int c = (int)threadIdx.x; c < na; c += 32) {
+        const int row = (int)L.arow[c];
+        bulk_g2s(dst + (uint32_t)(row * ld) * 8u, src + (size_t)row * Nph, row_bytes, L.bar);
+      }
     }
-    asm volatile("cp.async.commit_group;" ::: "memory");
+    pending = bulk_staging<P>();
   }
   asm volatile("cp.async.wait_group 0;" ::: "memory");
+  if (!arrived()) return;
   __syncthreads();  // tables, twiddles, pair list and the shell's values are in place
 
   // input map on every value; block exponent and conversion to the working precision (in place)
@@ -1317,10 +1427,18 @@ __global__ void __launch_bounds__(512) shell_kernel(ShellArgs2 A, LaunchIO io) {
   const Layout<P> L = carve<P>(A, smem_raw);
   // a launch over a list of shells reads its shell index there (same encoding as the grid's)
   const int sidx = io.list ? __ldg(io.list + blockIdx.x) : (int)blockIdx.x;
-  // the shell's asynchronous copy first, then the twiddles (16-byte table entries copied as they
-  // are); the tables in filter_shell are fetched while these are in flight. An in-place call
-  // copies only the rows a pass transforms, once filter_shell knows them.
-  if (!io.is_f32 && io.async_ok && !in_place_sparse<LEN>(io)) issue_load<LEN>(A, io, sidx, L.buf);
+  // the shell's copies first (bulk copies by warp 0, or cp.async by every thread; see
+  // bulk_staging), then the twiddles (16-byte table entries copied as they are); the tables in
+  // filter_shell are fetched while these are in flight. An in-place call copies only the rows a
+  // pass transforms, once filter_shell knows them.
+  const bool stage = !io.is_f32 && io.async_ok && !in_place_sparse<LEN>(io);
+  const bool bulk = stage && bulk_staging<P>();
+  if (bulk_staging<P>()) {
+    if (threadIdx.x == 0) bar_init(L.bar);
+    __syncthreads();  // the mbarrier is initialised
+  }
+  if (bulk && threadIdx.x < 32) issue_shell_copies<LEN>(A, io, sidx, L.buf, L.bar);
+  if (stage && !bulk) issue_shell_async<LEN>(A, io, sidx, L.buf);
   const typename P::C* twth_g = static_cast<const typename P::C*>(A.tw_th);
   const typename P::C* twph_g = static_cast<const typename P::C*>(A.tw_ph);
   for (int n = threadIdx.x; n < 2 * A.Nth; n += blockDim.x)
@@ -1332,7 +1450,7 @@ __global__ void __launch_bounds__(512) shell_kernel(ShellArgs2 A, LaunchIO io) {
   K.c8 = P::from_tab(A.consts, 0);
   K.s3 = P::from_tab(A.consts, 1);
 
-  filter_shell<P, LEN, HYB>(A, io, L, L.buf, sidx, K);
+  filter_shell<P, LEN, HYB>(A, io, L, L.buf, sidx, K, bulk);
 }
 
 
@@ -1946,6 +2064,7 @@ size_t shell_smem(const ShellArgs2& a) {
   s += up((size_t)a.Nth);
   s += up(sizeof(unsigned short) * (size_t)a.Nth);
   s += up((size_t)(a.Nph / 2 + a.Nth + (a.Nph / 2 + 1) / 2));
+  s += 16;  // mbarrier and the wait's outcome
   return s;
 }
 

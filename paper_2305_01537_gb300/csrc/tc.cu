@@ -272,14 +272,6 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float f[8]) {
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-// Offset of element q of a vector: theta circles run down meridian k, then back up meridian
-// k + Nphi/2 (Sec. II.C double covering); rings are contiguous.
-__device__ __forceinline__ long long elem_off(const TcArgs& A, int pass, long long base, int q) {
-  if (pass == 0)
-    return q < A.Nth ? base + (long long)q * A.Nph : base + (long long)(2 * A.Nth - 1 - q) * A.Nph + A.Nph / 2;
-  return base + q;
-}
-
 struct Kern {
   const TcArgs* A;           // the current item's grid
   const PassDesc* d;         // the current tile's pass
@@ -422,12 +414,8 @@ __device__ void mid_step(Kern& k, const GemmDesc& g) {
       tmem_wait_ld();
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        const int j = 8 * c + i;
-        long long yy = 0;
-        if (j < cnt) {
-          const long long dd = combine5(f[0][i], f[1][i], f[2][i], f[3][i], f[4][i], mlt);
-          yy = mul_mu(dd, __ldg(mu + ms * j));
-        }
+        const long long yy =
+            8 * c + i < cnt ? mul_mu(combine5(f[0][i], f[1][i], f[2][i], f[3][i], f[4][i], mlt), __ldg(mu + ms * (8 * c + i))) : 0;
         y[ci][i] = yy;
         orv |= (unsigned long long)(yy ^ (yy >> 63));
       }
@@ -506,36 +494,48 @@ __device__ void epilogue_direct(Kern& k, const GemmDesc& g, int Pb) {
   }
 }
 
-// Runs f(v, p) for every vector v of the tile and p < count, without divisions: theta circles take
-// the vector from the thread (consecutive threads, consecutive circles: coalesced meridian rows),
-// rings one warp per vector (consecutive lanes, consecutive positions).
-template <class Fn>
-__device__ __forceinline__ void for_tasks(const Kern& k, int count, Fn f) {
+// Runs f(st, p) for every vector v of the tile and p < count, st = init(v) computed once per vector
+// a thread visits, without divisions: theta circles take the vector from the thread (consecutive
+// threads, consecutive circles: coalesced meridian rows), rings one warp per vector (consecutive
+// lanes, consecutive positions).
+template <class Init, class Fn>
+__device__ __forceinline__ void for_vec(const Kern& k, int count, Init init, Fn f) {
   if (k.pass == 0) {
-    const int v = k.tid & (kV - 1);
-    for (int p = k.tid >> 6; p < count; p += (int)(blockDim.x >> 6)) f(v, p);
+    const auto st = init(k.tid & (kV - 1));
+    for (int p = k.tid >> 6; p < count; p += (int)(blockDim.x >> 6)) f(st, p);
   } else {
-    for (int v = k.warp; v < kV; v += (int)(blockDim.x >> 5))
-      for (int p = k.lane; p < count; p += 32) f(v, p);
+    for (int v = k.warp; v < kV; v += (int)(blockDim.x >> 5)) {
+      const auto st = init(v);
+      for (int p = k.lane; p < count; p += 32) f(st, p);
+    }
   }
+}
+
+// A vector's store row and the conversion of its raw FP64 values: base = 53 - F + its exponent; on
+// a theta circle the second meridian carries the field's parity sign (neg).
+struct VecIn {
+  long long* s;
+  int base;
+  bool neg;
+};
+__device__ __forceinline__ VecIn vec_in(const Kern& k, int v) {
+  return VecIn{k.store + (size_t)v * k.pitch, 53 - k.d->F + k.C.vexp[v], k.pass == 0 && k.C.row[v].neg != 0};
 }
 
 // In-place level stage (forward) on the first n entries of every vector's store.
 __device__ void level_fwd(Kern& k, int n, bool convert) {
   const int q = n / 4;
-  for_tasks(k, q, [&](int v, int p) {
-    long long* s = k.store + (size_t)v * k.pitch;
+  for_vec(k, q, [&](int v) { return vec_in(k, v); }, [&](const VecIn& V, int p) {
+    long long* s = V.s;
     long long vp = s[p], vq = s[p + n / 2], vr = s[n / 2 - 1 - p], vs = s[n - 1 - p];
     if (convert) {
       // the outermost level reads the raw FP64 values; on a theta circle positions p + n/2 and
-      // n - 1 - p lie on the second meridian, which carries the field's parity sign
-      const int base = 53 - k.d->F + k.C.vexp[v];
-      const bool neg = k.pass == 0 && k.C.row[v].neg;
-      vp = to_fixed(vp, base);
-      vq = to_fixed(vq, base);
-      vr = to_fixed(vr, base);
-      vs = to_fixed(vs, base);
-      if (neg) {
+      // n - 1 - p lie on the second meridian
+      vp = to_fixed(vp, V.base);
+      vq = to_fixed(vq, V.base);
+      vr = to_fixed(vr, V.base);
+      vs = to_fixed(vs, V.base);
+      if (V.neg) {
         vq = -vq;
         vs = -vs;
       }
@@ -549,67 +549,97 @@ __device__ void level_fwd(Kern& k, int n, bool convert) {
 }
 
 __device__ void base_fwd(Kern& k, int nb, bool convert) {
-  for_tasks(k, nb / 2, [&](int v, int p) {
-    long long* s = k.store + (size_t)v * k.pitch;
+  for_vec(k, nb / 2, [&](int v) { return vec_in(k, v); }, [&](const VecIn& V, int p) {
+    long long* s = V.s;
     long long a = s[p], b = s[nb - 1 - p];
     if (convert) {
       // no levels: nb = L; on a theta circle position nb - 1 - p is on the second meridian
-      const int base = 53 - k.d->F + k.C.vexp[v];
-      a = to_fixed(a, base);
-      b = to_fixed(b, base);
-      if (k.pass == 0 && k.C.row[v].neg) b = -b;
+      a = to_fixed(a, V.base);
+      b = to_fixed(b, V.base);
+      if (V.neg) b = -b;
     }
     s[p] = a + b;
     s[nb - 1 - p] = a - b;
   });
 }
 
-// Writes value x (scaled by 2^expo) of position q of vector v to the destination state (the
-// parity sign of a circle's second meridian applied to the integer).
-__device__ __forceinline__ void put_out(const Kern& k, int v, int q, long long x, int expo) {
+// A vector's store row and its destination: position q of a theta circle is at top + q Nphi on the
+// first meridian (q < Ntheta) and at bot - q Nphi on the second, with the parity sign applied to
+// the integer; a ring's position q is at top + q. Values are scaled by 2^expo.
+struct VecOut {
+  long long* s;
+  double* top;
+  double* bot;
+  int expo, nth, nph;
+  bool neg, valid;
+};
+__device__ __forceinline__ VecOut vec_out(const Kern& k, int v, int shift) {
   const RowInfo& R = k.C.row[v];
-  if (k.pass == 0 && R.neg && q >= k.A->Nth) x = -x;
-  k.A->out[elem_off(*k.A, k.pass, R.base, q)] = from_fixed(x, expo);
+  const int nth = k.A->Nth, nph = k.A->Nph;
+  double* top = k.A->out + R.base;
+  return VecOut{k.store + (size_t)v * k.pitch, top, top + (long long)(2 * nth - 1) * nph + nph / 2,
+                (k.C.vexp[v] - 1022) - k.d->F - shift, nth, nph, k.pass == 0 && R.neg != 0, R.valid != 0};
+}
+__device__ __forceinline__ void put_out(const Kern& k, const VecOut& V, int q, long long x) {
+  double* dst;
+  if (k.pass == 0) {
+    const bool up = q < V.nth;
+    if (V.neg && !up) x = -x;
+    dst = up ? V.top + (long long)q * V.nph : V.bot - (long long)q * V.nph;
+  } else {
+    dst = V.top + q;
+  }
+  *dst = from_fixed(x, V.expo);
 }
 
 // Inverse base stage: values become 2 v; `out` writes them to the destination (no levels).
 __device__ void base_inv(Kern& k, int nb, bool out) {
-  for_tasks(k, nb / 2, [&](int v, int p) {
-    long long* s = k.store + (size_t)v * k.pitch;
+  if (out) {
+    for_vec(k, nb / 2, [&](int v) { return vec_out(k, v, 1); }, [&](const VecOut& V, int p) {
+      if (!V.valid) return;
+      const long long a = V.s[p], b = V.s[nb - 1 - p];
+      put_out(k, V, p, a + b);
+      put_out(k, V, nb - 1 - p, a - b);
+    });
+    return;
+  }
+  for_vec(k, nb / 2, [&](int v) { return k.store + (size_t)v * k.pitch; }, [&](long long* s, int p) {
     const long long a = s[p], b = s[nb - 1 - p];
-    if (out) {
-      if (!k.C.row[v].valid) return;
-      const int expo = (k.C.vexp[v] - 1022) - k.d->F - 1;
-      put_out(k, v, p, a + b, expo);
-      put_out(k, v, nb - 1 - p, a - b, expo);
-    } else {
-      s[p] = a + b;
-      s[nb - 1 - p] = a - b;
-    }
+    s[p] = a + b;
+    s[nb - 1 - p] = a - b;
   });
 }
 
 // Inverse level stage for the level of length n, with the T-even part scaled by 2^sc (sc >= 1);
 // results scaled by 2^(sc + 1). `out` writes them to the destination (outermost level).
 __device__ void level_inv(Kern& k, int n, int sc, bool out) {
-  for_tasks(k, n / 4, [&](int v, int p) {
-    long long* s = k.store + (size_t)v * k.pitch;
+  auto butterfly = [&](const long long* s, int p, long long y[4]) {
     const long long E0 = s[p], E1 = s[n / 2 - 1 - p], a = s[n / 2 + p], o = s[n - 1 - p];
     const long long zp = (o + a) << (sc - 1), zq = (o - a) << (sc - 1);
-    const long long y0 = E0 + zp, y1 = E0 - zp, y2 = E1 + zq, y3 = E1 - zq;
-    if (out) {
-      if (!k.C.row[v].valid) return;
-      const int expo = (k.C.vexp[v] - 1022) - k.d->F - (sc + 1);
-      put_out(k, v, p, y0, expo);
-      put_out(k, v, p + n / 2, y1, expo);
-      put_out(k, v, n / 2 - 1 - p, y2, expo);
-      put_out(k, v, n - 1 - p, y3, expo);
-    } else {
-      s[p] = y0;
-      s[p + n / 2] = y1;
-      s[n / 2 - 1 - p] = y2;
-      s[n - 1 - p] = y3;
-    }
+    y[0] = E0 + zp;
+    y[1] = E0 - zp;
+    y[2] = E1 + zq;
+    y[3] = E1 - zq;
+  };
+  if (out) {
+    for_vec(k, n / 4, [&](int v) { return vec_out(k, v, sc + 1); }, [&](const VecOut& V, int p) {
+      if (!V.valid) return;
+      long long y[4];
+      butterfly(V.s, p, y);
+      put_out(k, V, p, y[0]);
+      put_out(k, V, p + n / 2, y[1]);
+      put_out(k, V, n / 2 - 1 - p, y[2]);
+      put_out(k, V, n - 1 - p, y[3]);
+    });
+    return;
+  }
+  for_vec(k, n / 4, [&](int v) { return k.store + (size_t)v * k.pitch; }, [&](long long* s, int p) {
+    long long y[4];
+    butterfly(s, p, y);
+    s[p] = y[0];
+    s[p + n / 2] = y[1];
+    s[n / 2 - 1 - p] = y[2];
+    s[n - 1 - p] = y[3];
   });
 }
 
@@ -758,20 +788,36 @@ __device__ __forceinline__ void run_items(const TcArgs* grids, int ngrids, const
     // then each vector's exponent. A ring read back after its shell's theta tiles cannot be stale in
     // this SM's L1: the only earlier reads of those lines in this launch are by the theta tile that
     // wrote them (and this SM's own writes keep its L1 current)
-    for_tasks(k, L, [&](int v, int q) {
-      const RowInfo& R = C.row[v];
-      if (!R.valid) return;
-      const double* g = R.src + elem_off(A, pass, R.base, q);
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(su32(store + (size_t)v * pitch + q)), "l"(g)
-                   : "memory");
-    });
+    {
+      struct Src {
+        const double* top;
+        const double* bot;
+        uint32_t dst;
+        bool valid;
+      };
+      const int Nth = A.Nth, Nph = A.Nph;
+      for_vec(k, L,
+              [&](int v) {
+                const RowInfo& R = C.row[v];
+                const double* top = R.src + R.base;
+                return Src{top, top + (long long)(2 * Nth - 1) * Nph + Nph / 2, su32(store + (size_t)v * pitch),
+                           R.valid != 0};
+              },
+              [&](const Src& S, int q) {
+                if (!S.valid) return;
+                const double* g = pass != 0 ? S.top + q : (q < Nth ? S.top + (long long)q * Nph : S.bot - (long long)q * Nph);
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(S.dst + 8u * (uint32_t)q), "l"(g) : "memory");
+              });
+    }
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
     if (pass == 0) {
       int e = 0;
-      for_tasks(k, L, [&](int v, int q) {
-        if (C.row[v].valid) e = max(e, (int)((store[(size_t)v * pitch + q] >> 52) & 0x7FF));
-      });
-      atomicMax(&C.vexp[tid & (kV - 1)], e);
+      const int v = tid & (kV - 1);
+      if (C.row[v].valid) {
+        const long long* s = store + (size_t)v * pitch;
+        for (int q = tid >> 6; q < L; q += (int)(blockDim.x >> 6)) e = max(e, (int)((s[q] >> 52) & 0x7FF));
+      }
+      atomicMax(&C.vexp[v], e);
     } else {
       for (int v = warp; v < kV; v += blockDim.x / 32) {
         int e = 0;
