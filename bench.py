@@ -481,8 +481,8 @@ def run_constraints(args):
     return 0
 
 
-PRECISIONS = ("f64", "f32x2", "tc")
-DTYPE_NAME = {"f64": "f64", "f32x2": "f32x2", "tc": "bf16x_split"}
+PRECISIONS = ("f64", "f32x2", "tc", "spectral")
+DTYPE_NAME = {"f64": "f64", "f32x2": "f32x2", "tc": "bf16x_split", "spectral": "f64"}
 
 
 def roofline_for(precision, g, avg_kernel_s, points, peaks, src, traffic, label):
@@ -491,7 +491,7 @@ def roofline_for(precision, g, avg_kernel_s, points, peaks, src, traffic, label)
     tensor pipe for the split-precision form."""
     flops = algorithmic_flops(g)
     tflops = flops / avg_kernel_s / 1e12
-    if precision == "f64":
+    if precision in ("f64", "spectral"):
         return {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": tflops / FP64_PEAK_TFLOPS, "traffic": traffic, "peak_source": FP64_PEAK_SOURCE,
                 "kernel": label, "flops_per_launch": flops}
@@ -697,13 +697,13 @@ def main():
 
     import torch
     import torch.distributed as dist
-    from paper_2305_01537_gb300 import Plan, SPH_PREC_F64, SPH_PREC_F32X2, SPH_PREC_SPLIT_TC
+    from paper_2305_01537_gb300 import Plan, SPH_PREC_F64, SPH_PREC_F32X2, SPH_PREC_SPLIT_TC, SPH_PREC_SPECTRAL
 
     world, rank, local = dist_setup()
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    prec_code = {"f64": SPH_PREC_F64, "f32x2": SPH_PREC_F32X2, "tc": SPH_PREC_SPLIT_TC}
+    prec_code = {"f64": SPH_PREC_F64, "f32x2": SPH_PREC_F32X2, "tc": SPH_PREC_SPLIT_TC, "spectral": SPH_PREC_SPECTRAL}
 
     wl = single_grid_workload(args.workload)
     g = wl.grids[0]
@@ -758,8 +758,12 @@ def main():
 
     # the other precisions on the same state, for the same line (rank 0 alone, N = 1)
     var_runs = {}
+    from paper_2305_01537_gb300 import SphFilterError
     for p in variants:
-        vplan = Plan.from_grid(g, precision=prec_code[p])
+        try:
+            vplan = Plan.from_grid(g, precision=prec_code[p])
+        except SphFilterError:  # a form that does not run this shape (the spectral form: one-CTA shells)
+            continue
         vy = x.clone() if args.inplace else torch.empty_like(x)
         xin = vy if args.inplace else x
         v_elapsed, v_kernel_ms, v_launched = time_plan(vplan, xin, vy, args.steps, args.warmup, stream)
@@ -794,10 +798,11 @@ def main():
         def label_for(p, pl):
             if p == "tc":
                 return "tc_pass_kernel: one persistent launch per application (theta tiles, phi tiles, copies)"
-            name = {"f64": "F64", "f32x2": "DF"}[p]
+            name = {"f64": "F64", "f32x2": "DF", "spectral": "F64, spectral form"}[p]
+            uname = {"f64": "F64", "f32x2": "DF", "spectral": "F64"}[p]
             if pl.launches < 3:
                 return f"shell_kernel<{name}>"
-            return (f"one application: shell_kernel<{name}> over the shells with a theta pass, units_kernel<{name}> "
+            return (f"one application: shell_kernel<{name}> over the shells with a theta pass, units_kernel<{uname}> "
                     "over the active ring pairs of the others" + ("" if args.inplace else ", copy_shells_kernel"))
 
         avg_kernel_s = statistics.mean(kernel_ms) * 1e-3

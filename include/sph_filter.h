@@ -83,8 +83,18 @@ typedef enum { SPH_FILTER_EXP = 0, SPH_FILTER_GAUSS = 1, SPH_FILTER_SHARP = 2, S
  *  SPH_PREC_F64     plain form: FFTs in FP64 arithmetic.
  *  SPH_PREC_F32X2   plain form with FFTs in compensated FP32-pair arithmetic (about 48-bit
  *                   significands).
- *  SPH_PREC_SPLIT_TC split-precision tensor-core form. */
-typedef enum { SPH_PREC_F64 = 0, SPH_PREC_SPLIT_TC = 1, SPH_PREC_F32X2 = 2 } sph_precision;
+ *  SPH_PREC_SPLIT_TC split-precision tensor-core form.
+ *  SPH_PREC_SPECTRAL the same filter in its spectral form, FP64: the theta pass is diagonal in
+ *                   the azimuthal mode m (shifting phi by pi multiplies mode m by (-1)^m), so a
+ *                   shell with a theta pass is filtered as one phi transform per ring, per mode m
+ *                   the theta filter of the even or odd extension over the Ntheta values (a
+ *                   cosine or sine transform pair, through a complex FFT of length Ntheta), the
+ *                   phi multiply, and one inverse phi transform; shells without a theta pass take
+ *                   the phi pass alone, as in SPH_PREC_F64. Requires Ntheta even and a shell that
+ *                   one CTA stages (Ntheta (Nphi + 2) 8 bytes plus scratch within the shared
+ *                   memory of one SM); plans with hybrid fields or other shapes fail to create
+ *                   with SPH_EUNSUPPORTED. */
+typedef enum { SPH_PREC_F64 = 0, SPH_PREC_SPLIT_TC = 1, SPH_PREC_F32X2 = 2, SPH_PREC_SPECTRAL = 3 } sph_precision;
 
 /* Cutoff parameters (Sec. II.C, cutoff equations), copied into the plan at creation. */
 typedef struct {

@@ -4,7 +4,7 @@ The compute path is the CUDA library libsph_filter.so behind the C ABI of includ
 `binding` marshals arguments to it. PyTorch provides device memory and streams only.
 """
 from .binding import (Plan, Batch, SphFilterError, SPH_FILTER_EXP, SPH_FILTER_GAUSS, SPH_FILTER_SHARP, SPH_FILTER_HYBRID,
-                      SPH_PREC_F64, SPH_PREC_SPLIT_TC, SPH_PREC_F32X2, load, enforce_constraints)
+                      SPH_PREC_F64, SPH_PREC_SPLIT_TC, SPH_PREC_F32X2, SPH_PREC_SPECTRAL, load, enforce_constraints)
 
 __all__ = ["Plan", "Batch", "SphFilterError", "SPH_FILTER_EXP", "SPH_FILTER_GAUSS", "SPH_FILTER_SHARP", "SPH_FILTER_HYBRID",
-           "SPH_PREC_F64", "SPH_PREC_SPLIT_TC", "SPH_PREC_F32X2", "load", "enforce_constraints"]
+           "SPH_PREC_F64", "SPH_PREC_SPLIT_TC", "SPH_PREC_F32X2", "SPH_PREC_SPECTRAL", "load", "enforce_constraints"]

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libsph_filter.so")
 
 SPH_OK, SPH_EINVAL, SPH_ENOMEM, SPH_ECUDA, SPH_EUNSUPPORTED, SPH_ETIMEOUT, SPH_EALIAS, SPH_EDEVICE = range(8)
 SPH_FILTER_EXP, SPH_FILTER_GAUSS, SPH_FILTER_SHARP, SPH_FILTER_HYBRID = 0, 1, 2, 3
-SPH_PREC_F64, SPH_PREC_SPLIT_TC, SPH_PREC_F32X2 = 0, 1, 2
+SPH_PREC_F64, SPH_PREC_SPLIT_TC, SPH_PREC_F32X2, SPH_PREC_SPECTRAL = 0, 1, 2, 3
 
 # Every symbol include/sph_filter.h declares (checked by the tests).
 EXPORTED = (

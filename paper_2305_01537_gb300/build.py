@@ -31,6 +31,7 @@ def nvcc() -> str:
 # shell_inst.cu is compiled once per (precision, FFT length, hybrid variant) instantiation of the
 # shell kernels (for length 256 the hybrid object holds only the cluster-pair kernel)
 SHELL_INST = [(d, n, h) for d in (0, 1) for n in (0, 32, 64, 96, 128, 192, 256) for h in (0, 1)]
+SHELL_INST += [(2, 0, 0), (2, 128, 0)]  # the FP64 spectral form
 
 
 def jobs():

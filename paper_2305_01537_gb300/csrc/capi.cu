@@ -132,6 +132,8 @@ sph_status setup_v2(sph_filter_plan_s* p) {
   a.nvars = p->nvars;
   a.ldS = p->Nph + 2;  // even: value pairs are 16-byte aligned
   if (!factorize_v2(2 * p->Nth, &a.f_th) || !factorize_v2(p->Nph, &a.f_ph)) return SPH_EUNSUPPORTED;
+  const bool spectral = p->precision == SPH_PREC_SPECTRAL;
+  if (spectral && !factorize_v2(p->Nth, &a.f_sp)) return SPH_EUNSUPPORTED;
   // Two CTAs of 256 threads per SM when the shell plus a scratch batch fits half the shared memory
   // (their copies and barriers then overlap each other's arithmetic); otherwise one CTA of 512.
   const int nseq = (p->Nph / 2 + 1) / 2, npair = (p->Nth + 1) / 2;
@@ -215,10 +217,7 @@ sph_status setup_v2(sph_filter_plan_s* p) {
   // twiddles stage by stage, in the order of the kernels' radix sequence: the stage that follows
   // Ns points already combined, with radix R, holds exp(-2 pi i t kk / (Ns R)) at entry
   // kk (R - 1) + t - 1 (kk < Ns, 1 <= t < R); the tables add up to N - 1 entries
-  for (int t = 0; t < 2; ++t) {
-    const int N = t == 0 ? 2 * Nth : Nph;
-    const size_t o = t == 0 ? o_tth : o_tph;
-    const Factors f = kernel_radices(a, N, p->precision);
+  auto stage_twiddles = [&](size_t o, const Factors& f) {
     size_t e = 0;
     int Ns = 1;
     for (int s = 0; s < f.nst; ++s) {
@@ -230,6 +229,20 @@ sph_status setup_v2(sph_filter_plan_s* p) {
           W.real(o + 16 * e + 8, -sinl(ang));
         }
       Ns *= R;
+    }
+  };
+  stage_twiddles(o_tph, kernel_radices(a, Nph, p->precision));
+  if (!spectral) {
+    stage_twiddles(o_tth, kernel_radices(a, 2 * Nth, p->precision));
+  } else {
+    // the spectral form's theta-table space (2 Ntheta entries): the stage twiddles of its
+    // length-Ntheta transforms, then e^{i pi l / Ntheta}, l < Ntheta (the theta pass on doubled
+    // circles never runs in these plans)
+    stage_twiddles(o_tth, a.f_sp);
+    for (int l = 0; l < Nth; ++l) {
+      const long double ang = pi * (long double)l / (long double)Nth;
+      W.real(o_tth + 16 * (size_t)(Nth + l), cosl(ang));
+      W.real(o_tth + 16 * (size_t)(Nth + l) + 8, sinl(ang));
     }
   }
   W.real(o_con, sqrtl(0.5L));
@@ -496,7 +509,8 @@ sph_status sph_filter_plan_create(sph_filter_plan* out, int Nr, int Ntheta, int 
   if (Nr < 1 || Ntheta < 1 || nvars < 1 || Nphi < 2 || (Nphi % 2) != 0) return SPH_EINVAL;
   if (!(prm->dr_min > 0) || !(prm->floor >= 0) || !std::isfinite(prm->dr_min) || !std::isfinite(prm->floor))
     return SPH_EINVAL;
-  if (prm->precision != SPH_PREC_F64 && prm->precision != SPH_PREC_SPLIT_TC && prm->precision != SPH_PREC_F32X2)
+  if (prm->precision != SPH_PREC_F64 && prm->precision != SPH_PREC_SPLIT_TC && prm->precision != SPH_PREC_F32X2 &&
+      prm->precision != SPH_PREC_SPECTRAL)
     return SPH_EINVAL;
   bool hybrid = false;
   for (int v = 0; v < nvars; ++v) {
@@ -506,8 +520,11 @@ sph_status sph_filter_plan_create(sph_filter_plan* out, int Nr, int Ntheta, int 
     hybrid |= prm->kind[v] == SPH_FILTER_HYBRID;
   }
   if (hybrid && (!(prm->eps >= 0) || !std::isfinite(prm->eps))) return SPH_EINVAL;
-  // the tensor-core form builds one operator per pass and class: no per-circle switch
-  if (hybrid && prm->precision == SPH_PREC_SPLIT_TC) return SPH_EUNSUPPORTED;
+  // the tensor-core form builds one operator per pass and class: no per-circle switch; the spectral
+  // form filters whole modes, not circles
+  if (hybrid && (prm->precision == SPH_PREC_SPLIT_TC || prm->precision == SPH_PREC_SPECTRAL)) return SPH_EUNSUPPORTED;
+  // the spectral form's per-mode transform pairs rows 2n and 2n + 1
+  if (prm->precision == SPH_PREC_SPECTRAL && (Ntheta % 2) != 0) return SPH_EUNSUPPORTED;
   for (int i = 0; i < Nr; ++i)
     if (!(prm->r[i] >= 0) || !std::isfinite(prm->r[i])) return SPH_EINVAL;
 
@@ -598,6 +615,11 @@ sph_status sph_filter_plan_create(sph_filter_plan* out, int Nr, int Ntheta, int 
   }
   if (hybrid && !p->use_v2) {
     // the detector and the per-circle multipliers live in the staged shell kernels
+    free_plan(p);
+    return SPH_EUNSUPPORTED;
+  }
+  if (p->precision == SPH_PREC_SPECTRAL && (!p->use_v2 || p->cluster)) {
+    // the spectral form runs in the single-CTA staged shell kernel only
     free_plan(p);
     return SPH_EUNSUPPORTED;
   }

@@ -75,6 +75,7 @@ struct ShellArgs2 {
   int ldS;                    // row stride of the staged shell (elements)
   int batch_th, batch_ph;     // sequences per FFT batch (sizes the scratch buffer)
   Factors f_th, f_ph;         // radices (2, 3, 4, 8) of 2 Ntheta and Nphi
+  Factors f_sp;               // radices of Ntheta (the spectral form's per-mode transforms)
   const double* lmax;         // [ncls][Nr]
   const VarInfo* var;         // [nvars]
   const uint8_t* ring_info;   // [ncls][Nr][Nth]: bit 0 ring active, bit 1 mirror ring differs
@@ -116,6 +117,8 @@ SPH_DECLARE_SHELL_INST_2(1, 96)
 SPH_DECLARE_SHELL_INST_2(1, 128)
 SPH_DECLARE_SHELL_INST_2(1, 192)
 SPH_DECLARE_SHELL_INST(1, 256, 0)
+SPH_DECLARE_SHELL_INST(2, 0, 0)    // FP64 spectral form (generic lengths)
+SPH_DECLARE_SHELL_INST(2, 128, 0)  // FP64 spectral form, 2 Ntheta = Nphi = 128
 #undef SPH_DECLARE_SHELL_INST_2
 #undef SPH_DECLARE_SHELL_INST
 // Cluster-pair instantiations for shells too large for one CTA (lengths 256 and generic), with and

@@ -49,6 +49,12 @@ static cudaError_t launch_p(const ShellArgs2& a, int threads, size_t smem, const
 
 cudaError_t launch_shell(const ShellArgs2& a, int precision, int threads, size_t smem, const LaunchIO& io,
                          cudaStream_t s) {
+  if (precision == SPH_PREC_SPECTRAL) {
+    // the FP64 spectral form (plans with hybrid fields are rejected at creation)
+    if (io.hybrid) return cudaErrorInvalidValue;
+    return fixed_length(a) == 128 ? launch_shell_inst<2, 128, 0>(a, threads, smem, io, s)
+                                  : launch_shell_inst<2, 0, 0>(a, threads, smem, io, s);
+  }
   // launches with hybrid fields run the kernel variant that has their detector and tables
   if (precision == SPH_PREC_F32X2)
     return io.hybrid ? launch_p<1, 1>(a, threads, smem, io, s) : launch_p<1, 0>(a, threads, smem, io, s);
@@ -136,8 +142,10 @@ static cudaError_t set_attr_p(int bytes) {
 cudaError_t set_shell_smem_attr(int device) {
   const int bytes = max_smem_optin(device);
   cudaError_t e = set_attr_p<0>(bytes);
-  if (e != cudaSuccess) return e;
-  return set_attr_p<1>(bytes);
+  if (e == cudaSuccess) e = set_attr_p<1>(bytes);
+  if (e == cudaSuccess) e = set_attr_inst<2, 0, 0>(bytes);
+  if (e == cudaSuccess) e = set_attr_inst<2, 128, 0>(bytes);
+  return e;
 }
 
 }  // namespace sph

@@ -790,6 +790,253 @@ __device__ __noinline__ void phi_split_pass_fn(PhiSplitAcc<P> PA, int npairs, bo
   }
 }
 
+// ------------------------------------------------------------------ spectral form (FP64)
+//
+// The theta pass is diagonal in the azimuthal mode m: shifting phi by pi multiplies mode m by
+// (-1)^m, so the doubled circle of mode m is c[q] = X_q[m] (q < Ntheta) and (-1)^(a + m)
+// X_{2 Ntheta - 1 - q}[m] (q >= Ntheta), X_j the phi spectrum of ring j. The filter
+// F = Phi^-1 D T Phi (Sec. II.C, theta then phi) is then: one forward phi transform per ring, per
+// mode m the theta filter T of the (anti)symmetric extension, the phi multiply D_m(j) =
+// f(m, m_max(i, j)), one inverse phi transform; the transpose applies D before T. T runs on the
+// Ntheta values X_j[m] themselves: with v_n = z_2n, v_{N-1-n} = z_{2n+1} (N = Ntheta, z_j = X_j[m],
+// times (-1)^j for odd symmetry), V = FFT_N(v), U_l = a_l V_l + b_l V_{N-l} with a_l = g_l + g_{N-l},
+// b_l = +-(g_l - g_{N-l}) e^{i pi l / N} (+ even, - odd; g_l = f(l) / (2 Ntheta)), u = IFFT_N(U)
+// unnormalised, z'_2n = u_n, z'_{2n+1} = u_{N-1-n}: the cosine/sine (DCT-II/III, DST-II/III) pair
+// written through a complex FFT of half the circle's length. The half spectra live in the rows
+// (row stride Nphi + 2 holds Nphi/2 + 1 complex values).
+
+// Theta filter of the modes m of the shell's half spectra: sequence b is mode m = b, its slots are
+// the value pairs (2m, 2m + 1) of the rows (row index XOR-swizzled in groups of 8).
+template <class P>
+struct SpecAcc {
+  using C = typename P::C;
+  using T = typename P::T;
+  struct Seq {
+    int m;
+    bool odd;      // (-1)^(a + m) = -1: antisymmetric extension
+    bool general;  // unused (no split multiply)
+  };
+  uint32_t S, lin;
+  int ld, N, N8, b0, parity, nh;
+  bool phi_first;     // transpose: the phi multiply before the theta filter
+  const void* gtab;   // phi multipliers f(|m|)/Nphi of this shell: [Ntheta][Nphi/2 + 1] (global)
+  size_t gbase;
+
+  __device__ __forceinline__ Seq seq(int b) const { return Seq{b, ((parity + b) & 1) != 0, false}; }
+  __device__ __forceinline__ int seq_len() const { return N; }
+  __device__ __forceinline__ uint32_t el(int row, int m) const { return S + (uint32_t)(row * ld + 2 * m) * 8u; }
+  __device__ __forceinline__ int row_of(int n) const { return n < N / 2 ? 2 * n : 2 * (N - 1 - n) + 1; }
+  __device__ __forceinline__ T phi_mult(int j, int m) const { return P::from_tab(gtab, gbase + (size_t)j * nh + m); }
+  __device__ __forceinline__ C gather(const Seq& s, int n) const {
+    const int j = row_of(n);
+    C v = P::ld16(el(j, s.m));
+    if (s.odd && (j & 1)) v = Cx<P>::neg(v);
+    if (phi_first) v = Cx<P>::scale(v, phi_mult(j, s.m));
+    return v;
+  }
+  __device__ __forceinline__ void scatter(const Seq& s, int n, C v) const {
+    const int j = row_of(n);
+    if (s.odd && (j & 1)) v = Cx<P>::neg(v);
+    if (!phi_first) v = Cx<P>::scale(v, phi_mult(j, s.m));
+    P::st16(el(j, s.m), v);
+  }
+  __device__ __forceinline__ C slot_ld(const Seq& s, int n) const { return P::ld16(el(swz(n, N8), s.m)); }
+  __device__ __forceinline__ void slot_st(const Seq& s, int n, C v) const { P::st16(el(swz(n, N8), s.m), v); }
+  __device__ __forceinline__ T mult(const Seq&, int) const { return P::zero(); }  // not used
+  __device__ __forceinline__ uint32_t lin_at(int b, int n) const {
+    return lin + 16u * (uint32_t)((b - b0) * N + swz(n, N8));
+  }
+  __device__ __forceinline__ C lin_ld(int b, int n) const { return P::ld16(lin_at(b, n)); }
+  __device__ __forceinline__ void lin_st(int b, int n, C v) const { P::st16(lin_at(b, n), v); }
+};
+
+// The inverse phi transform of a ring pair starts from the rings' half spectra: Z_m = X_j1[m] +
+// i X_j2[m] for m <= Nphi/2, and conj(X_j1[N-m]) + i conj(X_j2[N-m]) above.
+template <class P>
+struct PhiHalfAcc : PhiAcc<P> {
+  using C = typename P::C;
+  using Seq = typename PhiAcc<P>::Seq;
+  __device__ __forceinline__ C gather(const Seq& s, int m) const {
+    const bool lo = m <= this->hN;
+    const int mm = lo ? m : this->N - m;
+    const C x1 = P::ld16(this->el(s.j1, 2 * mm)), x2 = P::ld16(this->el(s.j2, 2 * mm));
+    return lo ? C{P::sub(x1.re, x2.im), P::add(x1.im, x2.re)} : C{P::add(x1.re, x2.im), P::sub(x2.re, x1.im)};
+  }
+};
+
+// After the forward phi transform Z of x_j1 + i x_j2 (in the slots or the scratch): the half
+// spectra X_j1[m] = (Z_m + conj Z_{N-m}) / 2 and X_j2[m] = (Z_m - conj Z_{N-m}) / (2i), m = 0 .. N/2,
+// over the rows. A spectrum in the slots (the rows themselves) is first moved to the scratch, so
+// that no write of the split lands on a value still to be read.
+template <class P>
+__device__ void split_spectra(const PhiAcc<P>& A, int B, bool in_slots) {
+  using C = typename P::C;
+  const int N = A.N, nh = N / 2 + 1;
+  if (in_slots) {
+    for (int w = threadIdx.x; w < B * N; w += blockDim.x) {
+      const int bl = w / N, n = w - bl * N;
+      const int b = A.b0 + bl;
+      A.lin_st(b, n, A.slot_ld(A.seq(b), n));
+    }
+    __syncthreads();
+  }
+  for (int base = 0; base < B * nh; base += blockDim.x) {
+    const int w = base + threadIdx.x;
+    const bool act = w < B * nh;
+    typename PhiAcc<P>::Seq sq{};
+    int m = 0;
+    C x1{}, x2{};
+    if (act) {
+      const int bl = w / nh;
+      const int b = A.b0 + bl;
+      m = w - bl * nh;
+      sq = A.seq(b);
+      const C zm = A.lin_ld(b, m), zn = A.lin_ld(b, (N - m) % N);
+      x1 = C{P::half(P::add(zm.re, zn.re)), P::half(P::sub(zm.im, zn.im))};
+      x2 = C{P::half(P::add(zm.im, zn.im)), P::half(P::sub(zn.re, zm.re))};
+    }
+    __syncthreads();
+    if (act) {
+      P::st16(A.el(sq.j1, 2 * m), x1);
+      P::st16(A.el(sq.j2, 2 * m), x2);
+    }
+    __syncthreads();
+  }
+}
+
+// The theta filter between the forward and inverse length-N transforms of each mode in the batch:
+// U_l = a_l V_l + b_l V_{N-l}, U_{N-l} = a_l V_{N-l} + conj(b_l) V_l (pairs l <= N/2). g: the theta
+// multipliers f(l)/(2 Ntheta), l = 0 .. N (shared); e: e^{i pi l / N}, l < N (shared).
+template <class P>
+__device__ void dct_multiply(const SpecAcc<P>& A, int B, bool in_slots, uint32_t g, uint32_t e) {
+  using C = typename P::C;
+  using T = typename P::T;
+  const int N = A.N, half = N / 2;
+  for (int base = 0; base < B * (half + 1); base += blockDim.x) {
+    const int w = base + threadIdx.x;
+    const bool act = w < B * (half + 1);
+    typename SpecAcc<P>::Seq sq{};
+    int l = 0, ln = 0, b = 0;
+    C u1{}, u2{};
+    if (act) {
+      const int bl = w / (half + 1);
+      b = A.b0 + bl;
+      l = w - bl * (half + 1);
+      ln = (N - l) % N;
+      sq = A.seq(b);
+      const C v1 = in_slots ? A.slot_ld(sq, l) : A.lin_ld(b, l);
+      const C v2 = in_slots ? A.slot_ld(sq, ln) : A.lin_ld(b, ln);
+      const T gl = P::ld8(g + 8u * (uint32_t)l), gn = P::ld8(g + 8u * (uint32_t)(N - l));
+      const T a = P::add(gl, gn);
+      const T d = sq.odd ? P::sub(gn, gl) : P::sub(gl, gn);
+      const C ez = P::ld16(e + 16u * (uint32_t)l);
+      const C bc{P::mul(d, ez.re), P::mul(d, ez.im)};
+      u1 = Cx<P>::add(Cx<P>::scale(v1, a), P::cmul(v2, bc));
+      u2 = Cx<P>::add(Cx<P>::scale(v2, a), P::cmul(v1, Cx<P>::conj(bc)));
+    }
+    __syncthreads();
+    if (act) {
+      if (in_slots) {
+        A.slot_st(sq, l, u1);
+        if (ln != l) A.slot_st(sq, ln, u2);
+      } else {
+        A.lin_st(b, l, u1);
+        if (ln != l) A.lin_st(b, ln, u2);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Forward stages of a batch (first stage gathers); true if the spectrum lands in the slots.
+// Compile-time radix sequences for the FP64 128-point (8, 8, 2) and 64-point (8, 8) transforms,
+// else the plan's factorisation f.
+template <class P, class Acc, int NLEN>
+__device__ __forceinline__ bool fwd_stages(const Acc& A, int N, int B, const Factors& f, uint32_t tw,
+                                           const Consts<P>& k) {
+  if constexpr (NLEN == 128) {
+    run_stages<P, Acc, -1, kFirst, true, 8, 8, 2>(A, N, B, 1, tw, k);
+    return false;
+  } else if constexpr (NLEN == 64) {
+    run_stages<P, Acc, -1, kFirst, true, 8, 8>(A, N, B, 1, tw, k);
+    return true;
+  } else {
+    int Ns = 1;
+    uint32_t ts = tw;
+    for (int s = 0; s < f.nst; ++s) {
+      const int R = f.radix[s];
+      if (s == 0) stage_r<P, Acc, -1, kFirst>(R, A, N, B, Ns, ts, k, true);
+      else stage_r<P, Acc, -1, 0>(R, A, N, B, Ns, ts, k, (s & 1) == 0);
+      ts += 16u * (uint32_t)(Ns * (R - 1));
+      Ns *= R;
+    }
+    return (f.nst & 1) == 0;
+  }
+}
+
+// Inverse stages of a batch: the first stage gathers (FIRST) or reads the slots/scratch holding the
+// forward result (the slots when `slots`); the last stage scatters.
+template <class P, class Acc, int NLEN, bool FIRST>
+__device__ __forceinline__ void inv_stages(const Acc& A, int N, int B, const Factors& f, uint32_t tw,
+                                           const Consts<P>& k, bool slots) {
+  constexpr int M0 = FIRST ? kFirst : 0;
+  if constexpr (NLEN == 128) {
+    if (FIRST || slots) run_stages<P, Acc, 1, M0, true, 8, 8, 2>(A, N, B, 1, tw, k);
+    else run_stages<P, Acc, 1, M0, false, 8, 8, 2>(A, N, B, 1, tw, k);
+  } else if constexpr (NLEN == 64) {
+    if (FIRST || slots) run_stages<P, Acc, 1, M0, true, 8, 8>(A, N, B, 1, tw, k);
+    else run_stages<P, Acc, 1, M0, false, 8, 8>(A, N, B, 1, tw, k);
+  } else {
+    int Ns = 1;
+    uint32_t ts = tw;
+    for (int s = 0; s < f.nst; ++s) {
+      const int R = f.radix[s];
+      const bool first = s == 0, last = s == f.nst - 1;
+      const bool from_slots = (FIRST || slots) ? (s & 1) == 0 : (s & 1) == 1;
+      if (first && last) stage_r<P, Acc, 1, M0 | kLast>(R, A, N, B, Ns, ts, k, from_slots);
+      else if (first) stage_r<P, Acc, 1, M0>(R, A, N, B, Ns, ts, k, from_slots);
+      else if (last) stage_r<P, Acc, 1, kLast>(R, A, N, B, Ns, ts, k, from_slots);
+      else stage_r<P, Acc, 1, 0>(R, A, N, B, Ns, ts, k, from_slots);
+      ts += 16u * (uint32_t)(Ns * (R - 1));
+      Ns *= R;
+    }
+  }
+}
+
+// The spectral form on a shell whose theta pass is active (every ring pair in PA's list): forward
+// phi transforms and half spectra; per mode the theta filter and the phi multiply; inverse phi
+// transforms. tw_sp: the length-Ntheta stage twiddles, then e^{i pi l / Ntheta} (Ntheta entries
+// each); g_th: the theta multipliers.
+template <class P, int LEN>
+__device__ __noinline__ void spectral_fn(PhiAcc<P> PA, SpecAcc<P> SA, int npairs, Factors fph, Factors fsp,
+                                         uint32_t tw_ph, uint32_t tw_sp, uint32_t g_th, Consts<P> K, int batch_ph,
+                                         int batch_sp) {
+  PA.template fix<LEN>();
+  const int Nph = PA.N, Nth = SA.N;
+  for (int b0 = 0; b0 < npairs; b0 += batch_ph) {
+    PA.b0 = b0;
+    const int B = min(batch_ph, npairs - b0);
+    const bool in_slots = fwd_stages<P, PhiAcc<P>, LEN>(PA, Nph, B, fph, tw_ph, K);
+    split_spectra<P>(PA, B, in_slots);
+  }
+  const int nm = Nph / 2 + 1;
+  const uint32_t dct = tw_sp + 16u * (uint32_t)Nth;
+  for (int b0 = 0; b0 < nm; b0 += batch_sp) {
+    SA.b0 = b0;
+    const int B = min(batch_sp, nm - b0);
+    const bool in_slots = fwd_stages<P, SpecAcc<P>, LEN / 2>(SA, Nth, B, fsp, tw_sp, K);
+    dct_multiply<P>(SA, B, in_slots, g_th, dct);
+    inv_stages<P, SpecAcc<P>, LEN / 2, false>(SA, Nth, B, fsp, tw_sp, K, in_slots);
+  }
+  PhiHalfAcc<P> HA;
+  static_cast<PhiAcc<P>&>(HA) = PA;
+  for (int b0 = 0; b0 < npairs; b0 += batch_ph) {
+    HA.b0 = b0;
+    const int B = min(batch_ph, npairs - b0);
+    inv_stages<P, PhiHalfAcc<P>, LEN, true>(HA, Nph, B, fph, tw_ph, K, true);
+  }
+}
+
 // ------------------------------------------------------------------ kernel
 
 template <class P>
@@ -1112,7 +1359,7 @@ __device__ __noinline__ void detect_shell(const G g, bool odd, double eps, float
 }
 
 // HYB: the kernel variant for launches with hybrid fields (the other variant has none of their code).
-template <class P, int LEN, bool HYB>
+template <class P, int LEN, bool HYB, bool SPEC = false>
 __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layout<P>& L, unsigned char* buf, int s,
                              const Consts<P>& K, bool copies_issued) {
   constexpr bool dfp = std::is_same<P, DF>::value;
@@ -1195,7 +1442,8 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
       const uint8_t a = in ? ring_info[j] : 0, b = in ? ring_info[jj] : 0;
       // hybrid field: a ring whose detector fired takes the Gaussian table (never the identity)
       const int fa = (hyb && in) ? L.ring[j] : 0, fb = (hyb && in) ? L.ring[jj] : 0;
-      const bool act = ((a | b) & 1) != 0 || fa || fb;  // bit 0: ring active
+      // bit 0: ring active; the spectral form transforms every ring of a shell with a theta pass
+      const bool act = ((a | b) & 1) != 0 || fa || fb || (SPEC && theta_on && in);
       // the multipliers of j and its mirror differ: different tables, or one table whose cutoffs
       // differ beyond rounding (bit 1)
       const int g = fa != fb ? 1 : ((fa ? (in ? ring_alt[j] : 0) : a) >> 1) & 1;
@@ -1355,7 +1603,24 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
   PA.nh = Nph / 2 + 1;
   PA.b0 = 0;
 
-  // the filter: theta pass then phi pass, or the reverse order for the transpose
+  // the filter: theta pass then phi pass, or the reverse order for the transpose; the spectral form
+  // runs both at once on shells with a theta pass
+  if (SPEC && theta_on) {
+    SpecAcc<P> SA;
+    SA.S = saddr(buf);
+    SA.lin = L.lin;
+    SA.ld = ld;
+    SA.N = Nth;
+    SA.N8 = Nth & ~7;
+    SA.b0 = 0;
+    SA.parity = vi.parity;
+    SA.nh = Nph / 2 + 1;
+    SA.phi_first = io.transpose != 0;
+    SA.gtab = A.g_ph;
+    SA.gbase = PA.gbase;
+    const int batch_sp = (int)(scratch_bytes(A) / (16 * (size_t)Nth));
+    spectral_fn<P, LEN>(PA, SA, npairs, A.f_ph, A.f_sp, L.tw_ph, L.tw_th, L.g_th, K, A.batch_ph, batch_sp);
+  } else
   for (int step = 0; step < 2; ++step) {
     if ((step == 0) != (io.transpose != 0)) {
       if (theta_on) {
@@ -1421,7 +1686,7 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
   }
 }
 
-template <class P, int LEN, bool HYB>
+template <class P, int LEN, bool HYB, bool SPEC = false>
 __global__ void __launch_bounds__(512) shell_kernel(ShellArgs2 A, LaunchIO io) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Layout<P> L = carve<P>(A, smem_raw);
@@ -1450,7 +1715,7 @@ __global__ void __launch_bounds__(512) shell_kernel(ShellArgs2 A, LaunchIO io) {
   K.c8 = P::from_tab(A.consts, 0);
   K.s3 = P::from_tab(A.consts, 1);
 
-  filter_shell<P, LEN, HYB>(A, io, L, L.buf, sidx, K, bulk);
+  filter_shell<P, LEN, HYB, SPEC>(A, io, L, L.buf, sidx, K, bulk);
 }
 
 
@@ -2068,16 +2333,16 @@ size_t shell_smem(const ShellArgs2& a) {
   return s;
 }
 
-template <class P, int LEN, bool HYB>
+template <class P, int LEN, bool HYB, bool SPEC = false>
 cudaError_t launch_impl(const ShellArgs2& a, int threads, size_t smem, const LaunchIO& io, cudaStream_t s) {
   const dim3 grid((unsigned)(io.list ? io.nlist : io.var_count * a.Nr));
-  shell_kernel<P, LEN, HYB><<<grid, threads, smem, s>>>(a, io);
+  shell_kernel<P, LEN, HYB, SPEC><<<grid, threads, smem, s>>>(a, io);
   return cudaGetLastError();
 }
 
-template <class P, int LEN, bool HYB>
+template <class P, int LEN, bool HYB, bool SPEC = false>
 cudaError_t set_attr_impl(int bytes) {
-  return cudaFuncSetAttribute(shell_kernel<P, LEN, HYB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return cudaFuncSetAttribute(shell_kernel<P, LEN, HYB, SPEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 template <class P>

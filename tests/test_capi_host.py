@@ -94,6 +94,13 @@ def test_hybrid_plans_the_tensor_core_form_cannot_run(lib):
     assert _create(lib, kind=(0, 3), parity=(0, 1), L=(3.0, 12.0), precision=1) == 4
 
 
+def test_spectral_form_rejects_what_it_cannot_run(lib):
+    """The spectral form (precision 3) pairs rows 2n and 2n + 1 of every mode and filters whole
+    modes: odd Ntheta and hybrid fields are rejected before any device work (SPH_EUNSUPPORTED)."""
+    assert _create(lib, Nth=5, Nph=10, precision=3) == 4
+    assert _create(lib, kind=(0, 3), parity=(0, 1), L=(3.0, 12.0), precision=3) == 4
+
+
 def test_calls_on_null_plan_are_rejected(lib):
     assert lib.sph_filter_apply(None, None, None, None) == 1
     assert lib.sph_filter_apply_adjoint(None, None, None, None) == 1
