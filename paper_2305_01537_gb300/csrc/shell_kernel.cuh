@@ -904,6 +904,21 @@ __device__ void split_spectra(const PhiAcc<P>& A, int B, bool in_slots) {
   }
 }
 
+// Before an inverse phi transform with an odd number of stages: Z_m (as PhiHalfAcc::gather forms it)
+// for every m into the scratch, so that the stages run scratch -> slots -> ... and the last one,
+// which writes the rows, reads the scratch (a last stage reading the slots, the rows themselves,
+// would race with its own writes).
+template <class P>
+__device__ void merge_spectra(const PhiHalfAcc<P>& A, int B) {
+  const int N = A.N;
+  for (int w = threadIdx.x; w < B * N; w += blockDim.x) {
+    const int bl = w / N, m = w - bl * N;
+    const int b = A.b0 + bl;
+    A.lin_st(b, m, A.gather(A.seq(b), m));
+  }
+  __syncthreads();
+}
+
 // The theta filter between the forward and inverse length-N transforms of each mode in the batch:
 // U_l = a_l V_l + b_l V_{N-l}, U_{N-l} = a_l V_{N-l} + conj(b_l) V_l (pairs l <= N/2). g: the theta
 // multipliers f(l)/(2 Ntheta), l = 0 .. N (shared); e: e^{i pi l / N}, l < N (shared).
@@ -1028,12 +1043,20 @@ __device__ __noinline__ void spectral_fn(PhiAcc<P> PA, SpecAcc<P> SA, int npairs
     dct_multiply<P>(SA, B, in_slots, g_th, dct);
     inv_stages<P, SpecAcc<P>, LEN / 2, false>(SA, Nth, B, fsp, tw_sp, K, in_slots);
   }
+  // inverse phi transforms: the last stage must read the scratch (its writes go to the rows), so an
+  // odd number of stages starts from the scratch (merge_spectra), an even one gathers directly
   PhiHalfAcc<P> HA;
   static_cast<PhiAcc<P>&>(HA) = PA;
+  const bool odd_stages = LEN == 128 ? true : (fph.nst & 1) != 0;
   for (int b0 = 0; b0 < npairs; b0 += batch_ph) {
     HA.b0 = b0;
     const int B = min(batch_ph, npairs - b0);
-    inv_stages<P, PhiHalfAcc<P>, LEN, true>(HA, Nph, B, fph, tw_ph, K, true);
+    if (odd_stages) {
+      merge_spectra<P>(HA, B);
+      inv_stages<P, PhiHalfAcc<P>, LEN, false>(HA, Nph, B, fph, tw_ph, K, false);
+    } else {
+      inv_stages<P, PhiHalfAcc<P>, LEN, true>(HA, Nph, B, fph, tw_ph, K, true);
+    }
   }
 }
 

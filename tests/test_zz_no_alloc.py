@@ -34,7 +34,7 @@ def test_noalloc_matches_allocating_call_twice(torch_cuda):
     torch = torch_cuda
     from paper_2305_01537_gb300 import Plan, binding
     lib = binding.load()
-    for prec in (0, 2, 1):  # FP64, compensated FP32, split-precision tensor-core form
+    for prec in (0, 2, 1, 3):  # FP64, compensated FP32, split-precision tensor-core form, spectral form
         g = W.grid_28(8, 32, 64)  # 458,752 points, within the 2,097,152-point capacity
         g.r = np.linspace(0.5, 30.5, 8)
         plan = Plan.from_grid(g, precision=prec)
