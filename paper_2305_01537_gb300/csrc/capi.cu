@@ -432,13 +432,16 @@ sph_status launch_plan_vars(sph_filter_plan_s* p, const void* in, const void* au
     // kernel; dense shells: the shell kernel over their list (both orders: a sparse shell's only
     // pass is the symmetric phi pass). The two sets of shells are disjoint, so when both have work
     // the copy (high-priority side stream) and then the units kernel (normal-priority side stream)
-    // run beside the shell kernel on the caller's stream.
+    // run beside the shell kernel on the caller's stream. The chunks of the host-buffer pipeline
+    // (tc_set > 0) run all three on their own stream: the chunks on the pipeline's three streams
+    // overlap one another, which forking every chunk to the plan's one pair of side streams would
+    // serialise.
     const int vb = var_begin, ve = var_begin + var_count;
     const int d0 = p->dense_off[(size_t)vb], d1 = p->dense_off[(size_t)ve];
     const int s0 = p->sparse_off[(size_t)vb], s1 = p->sparse_off[(size_t)ve];
     const int u0 = p->units_off[(size_t)vb], u1 = p->units_off[(size_t)ve];
     const bool copy = in != out && s1 > s0, dense_work = d1 > d0, side_work = copy || u1 > u0;
-    const bool fork = dense_work && side_work;
+    const bool fork = dense_work && side_work && tc_set == 0;
     std::lock_guard<std::mutex> lock(p->split_mu);
     cudaStream_t s_main = (cudaStream_t)stream, aux_s = fork ? p->side : s_main;
     cudaStream_t copy_s = fork ? p->side_copy : s_main;
