@@ -62,7 +62,7 @@ def test_traffic_record_names_known_families():
         for key, val in entry.items():
             if key != "sources_sha256_16":
                 prec, wl = key.split(":")
-                assert prec in ("f64", "f32x2", "tc")
+                assert prec in bench.PRECISIONS
                 assert bench.single_grid_workload(wl).name == wl  # a workload bench.py runs
                 assert isinstance(val, int) and val > 0
     for fam in bench.KERNEL_FAMILIES:
