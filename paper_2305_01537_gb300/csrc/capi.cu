@@ -734,23 +734,29 @@ sph_status sph_filter_apply_host(sph_filter_plan plan, const double* host_in, do
     for (cudaEvent_t& e : plan->pipe_ev)
       if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return SPH_ECUDA;
   }
-  // Pipeline over chunks of whole fields on three streams: the copy in of one chunk, the filter of
-  // another and the copy out of a third overlap (both directions of the host link are in use).
+  // Pipeline over chunks of whole fields on several streams: the copies in, the filters and the copies
+  // out of different chunks overlap (both directions of the host link are in use).
   cudaStream_t s = (cudaStream_t)stream;
   // chunks of about 16 MiB: small enough that filling and draining the pipeline costs little, large
   // enough that each copy runs at the link's full rate
   const size_t field_bytes = sizeof(double) * field;
   const int chunk = (int)std::min<size_t>(plan->nvars, std::max<size_t>(1, ((16u << 20) + field_bytes / 2) / field_bytes));
-  if (cudaEventRecord(plan->pipe_ev[3], s) != cudaSuccess) return SPH_ECUDA;
-  for (cudaStream_t ps : plan->pipe)
-    if (cudaStreamWaitEvent(ps, plan->pipe_ev[3], 0) != cudaSuccess) return SPH_ECUDA;
+  // streams in use: an FP64 chunk's kernels take about one shell's time (one wave of CTAs, ~0.23 ms
+  // for 64 x 128 shells), so six streams keep the copies busy; the compensated-FP32 chunks are short
+  // enough for three (six measured no better and noisier), and the tensor-core form has three
+  // pipeline counter sets
+  constexpr int kP = sph_filter_plan_s::kPipeStreams;
+  const int nstreams = (plan->tc || plan->precision == SPH_PREC_F32X2) ? 3 : kP;
+  if (cudaEventRecord(plan->pipe_ev[kP], s) != cudaSuccess) return SPH_ECUDA;
+  for (int q = 0; q < nstreams; ++q)
+    if (cudaStreamWaitEvent(plan->pipe[q], plan->pipe_ev[kP], 0) != cudaSuccess) return SPH_ECUDA;
   // the first and the last chunk hold one field: the pipeline fills and drains faster
   const bool taper = chunk > 1 && plan->nvars > 2;
   int k = 0;
   for (int v0 = 0, nv = 0; v0 < plan->nvars; v0 += nv, ++k) {
     const int left = plan->nvars - v0;
     nv = (taper && (k == 0 || left == 1)) ? 1 : std::max(1, std::min(chunk, taper ? left - 1 : left));
-    cudaStream_t ps = plan->pipe[k % 3];
+    cudaStream_t ps = plan->pipe[k % nstreams];
     const size_t off = field * v0, cnt = field * nv;
     if (cudaMemcpyAsync(plan->d_stage_in + off, host_in + off, sizeof(double) * cnt, cudaMemcpyHostToDevice, ps) !=
         cudaSuccess)
@@ -763,7 +769,7 @@ sph_status sph_filter_apply_host(sph_filter_plan plan, const double* host_in, do
         cudaSuccess)
       return SPH_ECUDA;
   }
-  for (int q = 0; q < 3; ++q) {
+  for (int q = 0; q < nstreams; ++q) {
     if (cudaEventRecord(plan->pipe_ev[q], plan->pipe[q]) != cudaSuccess) return SPH_ECUDA;
     if (cudaStreamWaitEvent(s, plan->pipe_ev[q], 0) != cudaSuccess) return SPH_ECUDA;
   }

@@ -244,8 +244,11 @@ struct sph_filter_plan_s {
   // staging buffers and pipeline streams of sph_filter_apply_host (created on first use)
   double* d_stage_in = nullptr;
   double* d_stage_out = nullptr;
-  cudaStream_t pipe[3] = {nullptr, nullptr, nullptr};
-  cudaEvent_t pipe_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  // host-buffer pipeline: kPipeStreams streams (the tensor-core form uses the first three, one per
+  // counter set), one event per stream plus the start event (the last)
+  static constexpr int kPipeStreams = 6;
+  cudaStream_t pipe[kPipeStreams] = {};
+  cudaEvent_t pipe_ev[kPipeStreams + 1] = {};
 };
 
 namespace sph {
