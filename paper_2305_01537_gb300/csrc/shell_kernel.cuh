@@ -41,6 +41,7 @@
 #include <type_traits>
 
 #include "df32.h"
+#include "dfmath.h"
 #include "internal.h"
 
 namespace sph {
@@ -312,6 +313,23 @@ struct Dft<P, 3, DIR> {
     v[2] = X::sub(m, w);
   }
 };
+
+// The chain steps' pointwise maps, tanh and its derivative 1 - tanh^2, in the form's arithmetic:
+// FP64 for the FP64 form, compensated FP32 pairs (dfmath.h) for the compensated-FP32 form.
+template <class P>
+__device__ __forceinline__ double map_tanh(double x) {
+  if constexpr (std::is_same<P, DF>::value) return df_tanh(x);
+  else return tanh(x);
+}
+template <class P>
+__device__ __forceinline__ double map_sech2(double x) {
+  if constexpr (std::is_same<P, DF>::value) {
+    return df_sech2(x);
+  } else {
+    const double t = tanh(x);
+    return 1.0 - t * t;
+  }
+}
 
 // ------------------------------------------------------------------ pass accessors
 
@@ -1554,7 +1572,7 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
     for (int n = threadIdx.x; n < npts; n += blockDim.x) {
       const int jrow = n / Nph;
       const int o = jrow * ld + n % Nph;
-      const double x = tanh(Sd[o]);
+      const double x = map_tanh<P>(Sd[o]);
       Sd[o] = x;
       if (dfp && L.rowact[jrow]) emax = max(emax, (unsigned)df_exp_field(x));
     }
@@ -1701,8 +1719,7 @@ __device__ void filter_shell(const ShellArgs2& A, const LaunchIO& io, const Layo
     if (io.map_out == kOutTanhGrad) {
       const double z = io.is_f32 ? (double)static_cast<const float*>(io.aux)[off + n]
                                  : static_cast<const double*>(io.aux)[off + n];
-      const double t = tanh(z);
-      y *= (1.0 - t * t);
+      y *= map_sech2<P>(z);
     }
     if (io.is_f32) __stcs(static_cast<float*>(io.out) + off + n, (float)y);
     else __stcs(static_cast<double*>(io.out) + off + n, y);
@@ -2147,7 +2164,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512) shell_kernel_cl
       const uint32_t a = addr_of(j, c);
       double x = F64::ld8(a);
       if (io.map_in == kMapTanh) {
-        x = tanh(x);
+        x = map_tanh<P>(x);
         F64::st8(a, x);
       }
       if (dfp && row_on(L.rowact, j)) emax = max(emax, (unsigned)df_exp_field(x));
@@ -2318,8 +2335,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512) shell_kernel_cl
     const size_t o = off + (size_t)j * Nph + c;
     if (io.map_out == kOutTanhGrad) {
       const double z = io.is_f32 ? (double)static_cast<const float*>(io.aux)[o] : static_cast<const double*>(io.aux)[o];
-      const double t = tanh(z);
-      y *= (1.0 - t * t);
+      y *= map_sech2<P>(z);
     }
     if (io.is_f32) __stcs(static_cast<float*>(io.out) + o, (float)y);
     else __stcs(static_cast<double*>(io.out) + o, y);

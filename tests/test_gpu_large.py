@@ -42,14 +42,15 @@ def test_cluster_shells_all_classes(torch_cuda, prec):
     assert field_errors(yt, oracle.filter_T(x, *args)).max() <= TOL
 
 
-def test_cluster_tanh_maps_fp32(torch_cuda):
+@pytest.mark.parametrize("prec", [0, 2])
+def test_cluster_tanh_maps_fp32(torch_cuda, prec):
     torch = torch_cuda
     from paper_2305_01537_gb300 import Plan
     p, k, L = W.field_mix_8()
     g = W.Grid(2, 128, 256, p, k, L, np.array([0.5, 30.5]))
     z = W.random_state(g.shape, 4)
     gr = W.random_state(g.shape, 5)
-    plan = Plan.from_grid(g)
+    plan = Plan.from_grid(g, precision=prec)
     zd, gd = torch.from_numpy(z).cuda(), torch.from_numpy(gr).cuda()
     args = (g.parity, g.kind, g.L, g.r, g.dr_min, g.floor)
     y = plan.apply_tanh(zd).cpu().numpy()
