@@ -178,3 +178,21 @@ def test_repeated_applications_are_identical(torch_cuda, prec):
     got = first[:, idx].cpu().numpy()
     tol = 1e-11 if prec == 1 else TOL
     assert field_errors(got, ref).max() <= tol
+
+
+def test_tanh_maps(torch_cuda):
+    """The fused chain steps F(tanh z) and (1 - tanh(z)^2) F^T g in the spectral form, on a grid
+    with shells of both kinds (the split launch's spectral shell kernel, copy and units kernels)."""
+    from paper_2305_01537_gb300 import Plan
+    torch = torch_cuda
+    wl = W.chain_8field()
+    g = W.Grid(6, 16, 32, wl.grids[0].parity, wl.grids[0].kind, wl.grids[0].L)
+    z = W.random_state(g.shape, 3)
+    gr = W.random_state(g.shape, 4)
+    plan = Plan.from_grid(g, precision=SPECTRAL)
+    zd, gd = torch.from_numpy(z).cuda(), torch.from_numpy(gr).cuda()
+    y = plan.apply_tanh(zd).cpu().numpy()
+    assert field_errors(y, oracle.filter(np.tanh(z), *args_of(g))).max() <= TOL
+    d = plan.apply_adjoint_tanh(gd, zd).cpu().numpy()
+    ref = (1 - np.tanh(z) ** 2) * oracle.filter_T(gr, *args_of(g))
+    assert field_errors(d, ref).max() <= TOL
