@@ -137,7 +137,9 @@ sph_status sph_filter_apply_adjoint(sph_filter_plan plan, const double* in, doub
  * composed with an elementwise nonlinearity):
  *   sph_filter_apply_tanh:          out = F(tanh(z))
  *   sph_filter_apply_adjoint_tanh:  out = (1 - tanh(z)^2) * F^T(g)    (chain rule through tanh)
- * z, g, out are device FP64 states; out may alias g (not z). */
+ * z, g, out are device FP64 states; out may alias g (not z). tanh is evaluated in the plan's
+ * arithmetic: FP64 for SPH_PREC_F64 and SPH_PREC_SPECTRAL, compensated FP32 pairs (relative error
+ * below 2^-45) for SPH_PREC_F32X2; the tensor-core form returns SPH_EUNSUPPORTED. */
 sph_status sph_filter_apply_tanh(sph_filter_plan plan, const double* z, double* out,
                                  sph_stream_t stream);
 sph_status sph_filter_apply_adjoint_tanh(sph_filter_plan plan, const double* g, const double* z,
