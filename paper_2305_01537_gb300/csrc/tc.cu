@@ -695,6 +695,7 @@ __device__ __forceinline__ void run_items(const TcArgs* grids, int ngrids, const
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&C.mma_bar)));
     asm volatile("fence.mbarrier_init.release.cluster;");
     C.abort = 0;
+    C.item[0] = atomicAdd(&work[0], 1);  // the first item
   }
   for (int i = tid; i < kM; i += blockDim.x) C.rowbl[i] = 0;
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -706,12 +707,12 @@ __device__ __forceinline__ void run_items(const TcArgs* grids, int ngrids, const
   k.h = k.r >> 6;
   k.v = k.r & (kV - 1);
   for (int n = 0;; ++n) {
-    // two slots: a slot is rewritten two iterations later, after a barrier every thread passed
-    // having read it
-    if (tid == 0) C.item[n & 1] = atomicAdd(&work[0], 1);
+    // two slots: the item of iteration n + 1 is fetched during iteration n (its atomic's latency
+    // hidden behind the tile), into the slot that iteration n - 1 read before the barrier below
     __syncthreads();
     const int it = C.item[n & 1];
     if (it >= nitems || C.abort) break;
+    if (tid == 0) C.item[(n + 1) & 1] = atomicAdd(&work[0], 1);
     int4 w = items[it];
     const TcArgs& A = grids[MULTI ? (w.x >> 4) : 0];
     w.x &= 15;
