@@ -57,7 +57,7 @@ DF_PEAK_SOURCE = ("FP64-equivalent rate of compensated FP32 pairs: measured FP32
 
 KERNEL_FAMILIES = {
     # CUDA sources whose device code each kernel family compiles from
-    "plain": ["shell_kernel.cuh", "shell_inst.cu", "shell_dispatch.cu", "filter_plain.cu", "df32.h",
+    "plain": ["shell_kernel.cuh", "shell_inst.cu", "shell_dispatch.cu", "filter_plain.cu", "df32.h", "dfmath.h",
               "capi.cu"],  # capi.cu: which kernels an application launches (the split)
     "tc": ["tc.cu", "tc_plan.cu", "tc2_host.h"],
 }
