@@ -157,8 +157,11 @@ sph_status sph_filter_apply_adjoint_tanh_f32(sph_filter_plan plan, const float* 
                                              float* out, sph_stream_t stream);
 
 /* End-to-end variant for host-resident states: copies host_in to the device, filters, copies
- * the result to host_out, all on `stream`, and returns after enqueueing. host_in/host_out should
- * be page-locked for the copies to overlap. The device staging buffers are allocated by the plan
+ * the result to host_out, ordered on `stream` (the work starts after what `stream` already holds and
+ * `stream` continues after the last copy out), and returns after enqueueing. Internally the state
+ * moves in chunks of whole fields: the copies in on one stream of the plan, each chunk's kernels on
+ * one of several compute streams, the copies out on another stream, so both copy directions and
+ * the kernels overlap. host_in/host_out should be page-locked for the copies to overlap. The device staging buffers are allocated by the plan
  * on first use and kept until the plan is destroyed (for the tensor-core form also the work lists
  * of the field chunks the call filters one at a time); calls of this function on one plan share
  * them, so order such calls (one stream, or a synchronisation between them). Synchronise the

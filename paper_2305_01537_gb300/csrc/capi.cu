@@ -352,8 +352,13 @@ void free_plan(sph_filter_plan_s* p) {
   cudaFree(p->d_stage_out);
   for (cudaStream_t s : p->pipe)
     if (s) cudaStreamDestroy(s);
-  for (cudaEvent_t e : p->pipe_ev)
+  for (cudaStream_t s : {p->pipe_in, p->pipe_out})
+    if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t e : {p->pipe_start, p->pipe_end})
     if (e) cudaEventDestroy(e);
+  for (const std::vector<cudaEvent_t>* v : {&p->chunk_in, &p->chunk_done})
+    for (cudaEvent_t e : *v)
+      if (e) cudaEventDestroy(e);
   delete p;
 }
 
@@ -433,7 +438,7 @@ sph_status launch_plan_vars(sph_filter_plan_s* p, const void* in, const void* au
     // pass is the symmetric phi pass). The two sets of shells are disjoint, so when both have work
     // the copy (high-priority side stream) and then the units kernel (normal-priority side stream)
     // run beside the shell kernel on the caller's stream. The chunks of the host-buffer pipeline
-    // (tc_set > 0) run all three on their own stream: the chunks on the pipeline's three streams
+    // (tc_set > 0) run all three on their own stream: the chunks on the pipeline's compute streams
     // overlap one another, which forking every chunk to the plan's one pair of side streams would
     // serialise.
     const int vb = var_begin, ve = var_begin + var_count;
@@ -728,51 +733,73 @@ sph_status sph_filter_apply_host(sph_filter_plan plan, const double* host_in, do
     const sph_status st = tc_reserve_pipeline(plan);
     if (st != SPH_OK) return st;
   }
-  if (!plan->pipe[0]) {
-    for (cudaStream_t& s : plan->pipe)
-      if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return SPH_ECUDA;
-    for (cudaEvent_t& e : plan->pipe_ev)
-      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return SPH_ECUDA;
+  if (!plan->pipe_in) {
+    for (cudaStream_t* q : {&plan->pipe[0], &plan->pipe[1], &plan->pipe[2], &plan->pipe[3], &plan->pipe[4],
+                            &plan->pipe[5], &plan->pipe_out, &plan->pipe_in})  // pipe_in last: the "created" mark
+      if (cudaStreamCreateWithFlags(q, cudaStreamNonBlocking) != cudaSuccess) {
+        *q = nullptr;
+        return SPH_ECUDA;
+      }
   }
-  // Pipeline over chunks of whole fields on several streams: the copies in, the filters and the copies
-  // out of different chunks overlap (both directions of the host link are in use).
+  if (!plan->pipe_end) {
+    for (cudaEvent_t* e : {&plan->pipe_start, &plan->pipe_end})
+      if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) {
+        *e = nullptr;
+        return SPH_ECUDA;
+      }
+  }
+  if ((int)plan->chunk_done.size() < plan->nvars) {  // one chunk per field at most
+    for (std::vector<cudaEvent_t>* v : {&plan->chunk_in, &plan->chunk_done})
+      while ((int)v->size() < plan->nvars) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return SPH_ECUDA;
+        v->push_back(e);
+      }
+  }
+  // Pipeline over chunks of whole fields: the copies in run back to back on one stream, each chunk's
+  // kernels on a compute stream once its copy has landed, and the copies out back to back on another
+  // stream, each once its chunk's kernels are done. The staging buffers hold the whole state, so no
+  // chunk waits for another's buffer: both directions of the host link stay busy from the first
+  // chunk to the last, and the kernels of several chunks overlap.
   cudaStream_t s = (cudaStream_t)stream;
   // chunks of about 16 MiB: small enough that filling and draining the pipeline costs little, large
   // enough that each copy runs at the link's full rate
   const size_t field_bytes = sizeof(double) * field;
   const int chunk = (int)std::min<size_t>(plan->nvars, std::max<size_t>(1, ((16u << 20) + field_bytes / 2) / field_bytes));
-  // streams in use: an FP64 chunk's kernels take about one shell's time (one wave of CTAs, ~0.23 ms
-  // for 64 x 128 shells), so six streams keep the copies busy; the compensated-FP32 chunks are short
-  // enough for three (six measured no better and noisier), and the tensor-core form has three
-  // pipeline counter sets
+  // compute streams: an FP64 chunk's kernels take about one shell's time (one partial wave of CTAs,
+  // ~0.23 ms for 64 x 128 shells) while a chunk arrives every ~0.08 ms, so up to six chunks run at
+  // once; the tensor-core form has three pipeline counter sets, one per stream
   constexpr int kP = sph_filter_plan_s::kPipeStreams;
-  const int nstreams = (plan->tc || plan->precision == SPH_PREC_F32X2) ? 3 : kP;
-  if (cudaEventRecord(plan->pipe_ev[kP], s) != cudaSuccess) return SPH_ECUDA;
-  for (int q = 0; q < nstreams; ++q)
-    if (cudaStreamWaitEvent(plan->pipe[q], plan->pipe_ev[kP], 0) != cudaSuccess) return SPH_ECUDA;
+  const int nstreams = plan->tc ? 3 : kP;
+  if (cudaEventRecord(plan->pipe_start, s) != cudaSuccess) return SPH_ECUDA;
+  if (cudaStreamWaitEvent(plan->pipe_in, plan->pipe_start, 0) != cudaSuccess) return SPH_ECUDA;
   // the first and the last chunk hold one field: the pipeline fills and drains faster
   const bool taper = chunk > 1 && plan->nvars > 2;
   int k = 0;
   for (int v0 = 0, nv = 0; v0 < plan->nvars; v0 += nv, ++k) {
     const int left = plan->nvars - v0;
     nv = (taper && (k == 0 || left == 1)) ? 1 : std::max(1, std::min(chunk, taper ? left - 1 : left));
-    cudaStream_t ps = plan->pipe[k % nstreams];
+    cudaStream_t cs = plan->pipe[k % nstreams];
     const size_t off = field * v0, cnt = field * nv;
-    if (cudaMemcpyAsync(plan->d_stage_in + off, host_in + off, sizeof(double) * cnt, cudaMemcpyHostToDevice, ps) !=
-        cudaSuccess)
+    if (cudaMemcpyAsync(plan->d_stage_in + off, host_in + off, sizeof(double) * cnt, cudaMemcpyHostToDevice,
+                        plan->pipe_in) != cudaSuccess)
       return SPH_ECUDA;
+    if (cudaEventRecord(plan->chunk_in[k], plan->pipe_in) != cudaSuccess) return SPH_ECUDA;
+    if (cudaStreamWaitEvent(cs, plan->chunk_in[k], 0) != cudaSuccess) return SPH_ECUDA;
     // the tensor-core form's scratch set of this stream (chunks on different streams may overlap)
     const sph_status st = launch_plan_vars(plan, plan->d_stage_in, nullptr, plan->d_stage_out, kMapNone, kOutNone, 0,
-                                           0, v0, nv, ps, 1 + k % 3);
+                                           0, v0, nv, cs, 1 + k % 3);
     if (st != SPH_OK) return st;
-    if (cudaMemcpyAsync(host_out + off, plan->d_stage_out + off, sizeof(double) * cnt, cudaMemcpyDeviceToHost, ps) !=
-        cudaSuccess)
+    if (cudaEventRecord(plan->chunk_done[k], cs) != cudaSuccess) return SPH_ECUDA;
+    if (cudaStreamWaitEvent(plan->pipe_out, plan->chunk_done[k], 0) != cudaSuccess) return SPH_ECUDA;
+    if (cudaMemcpyAsync(host_out + off, plan->d_stage_out + off, sizeof(double) * cnt, cudaMemcpyDeviceToHost,
+                        plan->pipe_out) != cudaSuccess)
       return SPH_ECUDA;
   }
-  for (int q = 0; q < nstreams; ++q) {
-    if (cudaEventRecord(plan->pipe_ev[q], plan->pipe[q]) != cudaSuccess) return SPH_ECUDA;
-    if (cudaStreamWaitEvent(s, plan->pipe_ev[q], 0) != cudaSuccess) return SPH_ECUDA;
-  }
+  // every chunk's kernels precede its copy out, and the copies out run in order: the caller's stream
+  // continues after the last one
+  if (cudaEventRecord(plan->pipe_end, plan->pipe_out) != cudaSuccess) return SPH_ECUDA;
+  if (cudaStreamWaitEvent(s, plan->pipe_end, 0) != cudaSuccess) return SPH_ECUDA;
   return SPH_OK;
 }
 

@@ -244,11 +244,15 @@ struct sph_filter_plan_s {
   // staging buffers and pipeline streams of sph_filter_apply_host (created on first use)
   double* d_stage_in = nullptr;
   double* d_stage_out = nullptr;
-  // host-buffer pipeline: kPipeStreams streams (the tensor-core form uses the first three, one per
-  // counter set), one event per stream plus the start event (the last)
+  // host-buffer pipeline: one stream for the copies in, one for the copies out, kPipeStreams compute
+  // streams (the tensor-core form uses the first three, one per counter set); the call's start and
+  // end events, and per chunk (at most one per field) an event after its copy in and one after its
+  // kernels
   static constexpr int kPipeStreams = 6;
   cudaStream_t pipe[kPipeStreams] = {};
-  cudaEvent_t pipe_ev[kPipeStreams + 1] = {};
+  cudaStream_t pipe_in = nullptr, pipe_out = nullptr;
+  cudaEvent_t pipe_start = nullptr, pipe_end = nullptr;
+  std::vector<cudaEvent_t> chunk_in, chunk_done;
 };
 
 namespace sph {
