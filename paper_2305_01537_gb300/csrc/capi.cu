@@ -217,17 +217,52 @@ sph_status setup_v2(sph_filter_plan_s* p) {
   // twiddles stage by stage, in the order of the kernels' radix sequence: the stage that follows
   // Ns points already combined, with radix R, holds exp(-2 pi i t kk / (Ns R)) at entry
   // kk (R - 1) + t - 1 (kk < Ns, 1 <= t < R); the tables add up to N - 1 entries
+  // FP64 kernels (every precision but compensated FP32) run their radix-2, -4 and -8 stages as
+  // radix-2 butterfly levels with FMA-form twiddles: per kk the slots hold w^4, w^2, w, w omega
+  // (R = 8), w^2, w (R = 4) or w (R = 2), w = exp(-2 pi i kk / (Ns R)), omega = exp(-2 pi i / 8),
+  // each as (m, r): m (1 + i r) with m = Re z, r = Im z / Re z when |Re z| >= |Im z|, else
+  // i m (1 + i r) with m = Im z, r = -Re z / Im z, marked by the lowest significand bit of m.
+  const bool fma_form = !W.pair;
+  auto fma_twiddle = [&](size_t at, long double ang) {  // z = exp(-i ang)
+    const long double zr = cosl(ang), zi = -sinl(ang);
+    const bool cot = fabsl(zi) > fabsl(zr);
+    double m = cot ? (double)zi : (double)zr;
+    const double r = cot ? (double)(-zr / zi) : (double)(zi / zr);
+    uint64_t bits;
+    std::memcpy(&bits, &m, 8);
+    bits = (bits & ~1ull) | (cot ? 1ull : 0ull);
+    std::memcpy(&m, &bits, 8);
+    W.real(at, m);
+    W.real(at + 8, r);
+  };
   auto stage_twiddles = [&](size_t o, const Factors& f) {
     size_t e = 0;
     int Ns = 1;
     for (int s = 0; s < f.nst; ++s) {
       const int R = f.radix[s];
-      for (int kk = 0; kk < Ns; ++kk)
-        for (int q = 1; q < R; ++q, ++e) {
-          const long double ang = 2.0L * pi * (long double)(q * kk) / (long double)(Ns * R);
-          W.real(o + 16 * e, cosl(ang));
-          W.real(o + 16 * e + 8, -sinl(ang));
+      if (fma_form && (R == 2 || R == 4 || R == 8)) {
+        for (int kk = 0; kk < Ns; ++kk, e += R - 1) {
+          const long double a1 = 2.0L * pi * (long double)kk / (long double)(Ns * R);  // w = exp(-i a1)
+          if (R == 8) {
+            fma_twiddle(o + 16 * e, 4 * a1);
+            fma_twiddle(o + 16 * (e + 1), 2 * a1);
+            fma_twiddle(o + 16 * (e + 2), a1);
+            fma_twiddle(o + 16 * (e + 3), a1 + pi / 4);
+          } else if (R == 4) {
+            fma_twiddle(o + 16 * e, 2 * a1);
+            fma_twiddle(o + 16 * (e + 1), a1);
+          } else {
+            fma_twiddle(o + 16 * e, a1);
+          }
         }
+      } else {
+        for (int kk = 0; kk < Ns; ++kk)
+          for (int q = 1; q < R; ++q, ++e) {
+            const long double ang = 2.0L * pi * (long double)(q * kk) / (long double)(Ns * R);
+            W.real(o + 16 * e, cosl(ang));
+            W.real(o + 16 * e + 8, -sinl(ang));
+          }
+      }
       Ns *= R;
     }
   };

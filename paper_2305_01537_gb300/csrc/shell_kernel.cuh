@@ -314,6 +314,140 @@ struct Dft<P, 3, DIR> {
   }
 };
 
+// FP64 radix-8 without twiddles: the two products by sqrt(1/2) fold into the output additions
+// (one FMA per output component instead of a multiply and an addition).
+template <int DIR>
+struct Dft<F64, 8, DIR> {
+  using X = Cx<F64>;
+  using C = F64::C;
+  static __device__ __forceinline__ void run(C* v, const Consts<F64>& k) {
+    C e[4] = {v[0], v[2], v[4], v[6]};
+    C o[4] = {v[1], v[3], v[5], v[7]};
+    Dft<F64, 4, DIR>::run(e, k);
+    Dft<F64, 4, DIR>::run(o, k);
+    // w8 o1 = sqrt(1/2) (o1 + DIR i o1), w8^3 o3 = sqrt(1/2) (DIR i o3 - o3)
+    const C g1 = X::add(o[1], X::template mul_i<DIR>(o[1]));
+    const C o2 = X::template mul_i<DIR>(o[2]);
+    const C g3 = X::sub(X::template mul_i<DIR>(o[3]), o[3]);
+    const double c = k.c8;
+    v[0] = X::add(e[0], o[0]);
+    v[4] = X::sub(e[0], o[0]);
+    v[1] = C{fma(c, g1.re, e[1].re), fma(c, g1.im, e[1].im)};
+    v[5] = C{fma(-c, g1.re, e[1].re), fma(-c, g1.im, e[1].im)};
+    v[2] = X::add(e[2], o2);
+    v[6] = X::sub(e[2], o2);
+    v[3] = C{fma(c, g3.re, e[3].re), fma(c, g3.im, e[3].im)};
+    v[7] = C{fma(-c, g3.re, e[3].re), fma(-c, g3.im, e[3].im)};
+  }
+};
+
+// ------------------------------------------------------------------ FP64 twiddled butterflies
+// A twiddled radix-R stage (R = 2, 4, 8) in FP64 runs as log2 R levels of radix-2 butterflies
+// a +- z b, each z a power of the stage twiddle w = exp(-2 pi i kk / (Ns R)) (conjugated for the
+// inverse) times a power of i, which costs nothing. Every z is stored as a pair (m, r):
+//   tangent form (|Re z| >= |Im z|):   z = m (1 + i r),    m = Re z, r = Im z / Re z;
+//   cotangent form (|Im z| > |Re z|):  z = i m (1 + i r),  m = Im z, r = -Re z / Im z;
+// so that with g = b + i r b (two FMAs) z b = m g or i m g, and both outputs a +- z b take one
+// FMA per component: six FP64 operations per butterfly instead of ten (complex product and two
+// complex additions). |r| <= 1 in both forms, so g carries no cancellation. The lowest significand
+// bit of m marks the cotangent form (a change of at most one unit in the last place of m).
+//
+// The factorisation: with x_t = w^t v_t and omega = exp(DIR 2 pi i / 8),
+//   V_u = sum_t x_t omega^(t u) = sum_{t<4} w^t omega^(t u) (v_t + (-1)^u w^4 v_{t+4}),
+// so the first level pairs v_t with v_{t+4} under z = w^4; the even outputs are then a twiddled
+// 4-point transform with twiddle w, the odd outputs one with twiddle w omega. A twiddled 4-point
+// transform with twiddle y pairs q_a with q_{a+2} under y^2, then combines r_0 with r_1 under y
+// (outputs 0 and 2) and under y DIR i (outputs 1 and 3). The table holds, per kk, w^4, w^2, w and
+// w omega for R = 8; w^2 and w for R = 4; w for R = 2 (in the stage's R - 1 slots).
+struct Tw {
+  double m, mx, r;  // mx: the factor of the real output component (m, or -m in the cotangent form)
+  bool cot;
+};
+
+template <int DIR>
+__device__ __forceinline__ Tw tw_load(uint32_t a) {
+  const F64::C e = F64::ld16(a);
+  const bool cot = (__double2loint(e.re) & 1) != 0;
+  // the conjugate (inverse): r changes sign; in the cotangent form m changes sign too
+  const double m = (DIR > 0 && cot) ? -e.re : e.re;
+  return Tw{m, cot ? -m : m, DIR > 0 ? -e.im : e.im, cot};
+}
+
+// (a, b) <- (a + z b, a - z b)
+__device__ __forceinline__ void tw_bfly(F64::C& a, F64::C& b, const Tw& z) {
+  const double gre = fma(-z.r, b.im, b.re);
+  const double gim = fma(z.r, b.re, b.im);
+  const double x = z.cot ? gim : gre;  // z b = (mx x, m y)
+  const double y = z.cot ? gre : gim;
+  const F64::C a0 = a;
+  a = F64::C{fma(z.mx, x, a0.re), fma(z.m, y, a0.im)};
+  b = F64::C{fma(-z.mx, x, a0.re), fma(-z.m, y, a0.im)};
+}
+
+template <int R, int DIR>
+struct TwDft;
+
+template <int DIR>
+struct TwDft<2, DIR> {
+  static __device__ __forceinline__ void run(F64::C* v, uint32_t tw) { tw_bfly(v[0], v[1], tw_load<DIR>(tw)); }
+};
+
+template <int DIR>
+struct TwDft<4, DIR> {
+  using X = Cx<F64>;
+  static __device__ __forceinline__ void run(F64::C* v, uint32_t tw) {
+    const Tw z2 = tw_load<DIR>(tw), z1 = tw_load<DIR>(tw + 16u);
+    tw_bfly(v[0], v[2], z2);
+    tw_bfly(v[1], v[3], z2);
+    F64::C b = X::template mul_i<DIR>(v[3]);
+    tw_bfly(v[0], v[1], z1);  // outputs 0, 2
+    tw_bfly(v[2], b, z1);     // outputs 1, 3
+    const F64::C u2 = v[1];
+    v[1] = v[2];
+    v[2] = u2;
+    v[3] = b;
+  }
+};
+
+template <int DIR>
+struct TwDft<8, DIR> {
+  using X = Cx<F64>;
+  static __device__ __forceinline__ void run(F64::C* v, uint32_t tw) {
+    const Tw z4 = tw_load<DIR>(tw), z2 = tw_load<DIR>(tw + 16u);
+    const Tw z1 = tw_load<DIR>(tw + 32u), z1w = tw_load<DIR>(tw + 48u);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) tw_bfly(v[t], v[t + 4], z4);
+    // even outputs: twiddled 4-point transform of v[0..3] with twiddle w
+    tw_bfly(v[0], v[2], z2);
+    tw_bfly(v[1], v[3], z2);
+    F64::C be = X::template mul_i<DIR>(v[3]);
+    tw_bfly(v[0], v[1], z1);  // V0, V4
+    tw_bfly(v[2], be, z1);    // V2, V6
+    // odd outputs: twiddled 4-point transform of v[4..7] with twiddle w omega ((w omega)^2 = w^2 DIR i)
+    F64::C b6 = X::template mul_i<DIR>(v[6]);
+    F64::C b7 = X::template mul_i<DIR>(v[7]);
+    tw_bfly(v[4], b6, z2);
+    tw_bfly(v[5], b7, z2);
+    F64::C bo = X::template mul_i<DIR>(b7);
+    tw_bfly(v[4], v[5], z1w);  // V1, V5
+    tw_bfly(b6, bo, z1w);      // V3, V7
+    const F64::C V1 = v[4], V2 = v[2], V4 = v[1], V5 = v[5];
+    v[1] = V1;
+    v[2] = V2;
+    v[3] = b6;
+    v[4] = V4;
+    v[5] = V5;
+    v[6] = be;
+    v[7] = bo;
+  }
+};
+
+// Stages whose twiddles use the FMA form: FP64 with radix 2, 4 or 8.
+template <class P, int R>
+__host__ __device__ constexpr bool fma_twiddles() {
+  return std::is_same<P, F64>::value && (R == 2 || R == 4 || R == 8);
+}
+
 // The chain steps' pointwise maps, tanh and its derivative 1 - tanh^2, in the form's arithmetic:
 // FP64 for the FP64 form, compensated FP32 pairs (dfmath.h) for the compensated-FP32 form.
 template <class P>
@@ -619,15 +753,20 @@ __device__ __forceinline__ void stage(const Acc& A, int N, int B, int Ns, uint32
       if ((MODE & kMul) && !sq.general) x = X::scale(x, A.mult(sq, n));
       v[t] = x;
     }
-    if (Ns > 1) {
+    if constexpr (fma_twiddles<P, R>()) {
+      if (Ns > 1) TwDft<R, DIR>::run(v, tw + 16u * (uint32_t)(kk * (R - 1)));
+      else Dft<P, R, DIR>::run(v, k);
+    } else {
+      if (Ns > 1) {
 #pragma unroll
-      for (int t = 1; t < R; ++t) {
-        C wt = P::ld16(tw + 16u * (uint32_t)(kk * (R - 1) + t - 1));
-        if (DIR > 0) wt = X::conj(wt);
-        v[t] = P::cmul(v[t], wt);
+        for (int t = 1; t < R; ++t) {
+          C wt = P::ld16(tw + 16u * (uint32_t)(kk * (R - 1) + t - 1));
+          if (DIR > 0) wt = X::conj(wt);
+          v[t] = P::cmul(v[t], wt);
+        }
       }
+      Dft<P, R, DIR>::run(v, k);
     }
-    Dft<P, R, DIR>::run(v, k);
     const int base = (j / Ns) * Ns * R + kk;
 #pragma unroll
     for (int t = 0; t < R; ++t) {
