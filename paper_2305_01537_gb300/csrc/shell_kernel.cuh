@@ -315,29 +315,53 @@ struct Dft<P, 3, DIR> {
 };
 
 // FP64 radix-8 without twiddles: the two products by sqrt(1/2) fold into the output additions
-// (one FMA per output component instead of a multiply and an addition).
+// (one FMA per output component instead of a multiply and an addition). run_scaled multiplies the
+// inputs by real factors mu_t first (the spectral multipliers of an inverse transform's first
+// stage), folded into the first level: mu_t v_t +- mu_{t+4} v_{t+4} takes one multiply and two
+// FMAs per component instead of two multiplies and two additions.
 template <int DIR>
 struct Dft<F64, 8, DIR> {
   using X = Cx<F64>;
   using C = F64::C;
   static __device__ __forceinline__ void run(C* v, const Consts<F64>& k) {
-    C e[4] = {v[0], v[2], v[4], v[6]};
-    C o[4] = {v[1], v[3], v[5], v[7]};
-    Dft<F64, 4, DIR>::run(e, k);
-    Dft<F64, 4, DIR>::run(o, k);
-    // w8 o1 = sqrt(1/2) (o1 + DIR i o1), w8^3 o3 = sqrt(1/2) (DIR i o3 - o3)
-    const C g1 = X::add(o[1], X::template mul_i<DIR>(o[1]));
-    const C o2 = X::template mul_i<DIR>(o[2]);
-    const C g3 = X::sub(X::template mul_i<DIR>(o[3]), o[3]);
+    C p[4], q[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      p[t] = X::add(v[t], v[t + 4]);
+      q[t] = X::sub(v[t], v[t + 4]);
+    }
+    finish(v, p, q, k);
+  }
+  static __device__ __forceinline__ void run_scaled(C* v, const double* mu, const Consts<F64>& k) {
+    C p[4], q[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const double ar = mu[t] * v[t].re, ai = mu[t] * v[t].im;
+      p[t] = C{fma(mu[t + 4], v[t + 4].re, ar), fma(mu[t + 4], v[t + 4].im, ai)};
+      q[t] = C{fma(-mu[t + 4], v[t + 4].re, ar), fma(-mu[t + 4], v[t + 4].im, ai)};
+    }
+    finish(v, p, q, k);
+  }
+  // the rest from the first level p_t = v_t + v_{t+4}, q_t = v_t - v_{t+4}: the 4-point transforms
+  // of the even inputs (p0, q0, p2, q2) and of the odd ones (p1, q1, p3, q3), then the radix-2
+  // combination with the eighth roots
+  static __device__ __forceinline__ void finish(C* v, const C* p, const C* q, const Consts<F64>& k) {
+    const C de = X::template mul_i<DIR>(q[2]), dd = X::template mul_i<DIR>(q[3]);
+    const C e0 = X::add(p[0], p[2]), e2 = X::sub(p[0], p[2]), e1 = X::add(q[0], de), e3 = X::sub(q[0], de);
+    const C o0 = X::add(p[1], p[3]), o2 = X::sub(p[1], p[3]), o1 = X::add(q[1], dd), o3 = X::sub(q[1], dd);
+    // w8 o1 = sqrt(1/2) (o1 + DIR i o1), w8^2 o2 = DIR i o2, w8^3 o3 = sqrt(1/2) (DIR i o3 - o3)
+    const C g1 = X::add(o1, X::template mul_i<DIR>(o1));
+    const C r2 = X::template mul_i<DIR>(o2);
+    const C g3 = X::sub(X::template mul_i<DIR>(o3), o3);
     const double c = k.c8;
-    v[0] = X::add(e[0], o[0]);
-    v[4] = X::sub(e[0], o[0]);
-    v[1] = C{fma(c, g1.re, e[1].re), fma(c, g1.im, e[1].im)};
-    v[5] = C{fma(-c, g1.re, e[1].re), fma(-c, g1.im, e[1].im)};
-    v[2] = X::add(e[2], o2);
-    v[6] = X::sub(e[2], o2);
-    v[3] = C{fma(c, g3.re, e[3].re), fma(c, g3.im, e[3].im)};
-    v[7] = C{fma(-c, g3.re, e[3].re), fma(-c, g3.im, e[3].im)};
+    v[0] = X::add(e0, o0);
+    v[4] = X::sub(e0, o0);
+    v[1] = C{fma(c, g1.re, e1.re), fma(c, g1.im, e1.im)};
+    v[5] = C{fma(-c, g1.re, e1.re), fma(-c, g1.im, e1.im)};
+    v[2] = X::add(e2, r2);
+    v[6] = X::sub(e2, r2);
+    v[3] = C{fma(c, g3.re, e3.re), fma(c, g3.im, e3.im)};
+    v[7] = C{fma(-c, g3.re, e3.re), fma(-c, g3.im, e3.im)};
   }
 };
 
@@ -359,25 +383,32 @@ struct Dft<F64, 8, DIR> {
 // transform with twiddle y pairs q_a with q_{a+2} under y^2, then combines r_0 with r_1 under y
 // (outputs 0 and 2) and under y DIR i (outputs 1 and 3). The table holds, per kk, w^4, w^2, w and
 // w omega for R = 8; w^2 and w for R = 4; w for R = 2 (in the stage's R - 1 slots).
+// The conjugate (inverse) has r of the other sign, and in the cotangent form m of the other sign
+// too; the sign of r goes into the FMAs' operand modifiers. With mx the factor of the real output
+// component (z b = (mx x, m y) below): forward, m as stored and mx = -m in the cotangent form;
+// inverse, mx = m as stored and m = -m in the cotangent form. Those sign changes flip the sign bit
+// with an integer operation (a negation of a selected FP64 value would cost an FP64 addition).
 struct Tw {
-  double m, mx, r;  // mx: the factor of the real output component (m, or -m in the cotangent form)
+  double m, mx, r;
   bool cot;
 };
 
 template <int DIR>
 __device__ __forceinline__ Tw tw_load(uint32_t a) {
   const F64::C e = F64::ld16(a);
-  const bool cot = (__double2loint(e.re) & 1) != 0;
-  // the conjugate (inverse): r changes sign; in the cotangent form m changes sign too
-  const double m = (DIR > 0 && cot) ? -e.re : e.re;
-  return Tw{m, cot ? -m : m, DIR > 0 ? -e.im : e.im, cot};
+  const int lo = __double2loint(e.re), hi = __double2hiint(e.re);
+  const double flipped = __hiloint2double(hi ^ (int)((unsigned)(lo & 1) << 31), lo);  // -m if cotangent
+  if (DIR < 0) return Tw{e.re, flipped, e.im, (lo & 1) != 0};
+  return Tw{flipped, e.re, e.im, (lo & 1) != 0};
 }
 
 // (a, b) <- (a + z b, a - z b)
+template <int DIR>
 __device__ __forceinline__ void tw_bfly(F64::C& a, F64::C& b, const Tw& z) {
-  const double gre = fma(-z.r, b.im, b.re);
-  const double gim = fma(z.r, b.re, b.im);
-  const double x = z.cot ? gim : gre;  // z b = (mx x, m y)
+  // g = b + i r b (r of the conjugate's sign for the inverse)
+  const double gre = DIR < 0 ? fma(-z.r, b.im, b.re) : fma(z.r, b.im, b.re);
+  const double gim = DIR < 0 ? fma(z.r, b.re, b.im) : fma(-z.r, b.re, b.im);
+  const double x = z.cot ? gim : gre;
   const double y = z.cot ? gre : gim;
   const F64::C a0 = a;
   a = F64::C{fma(z.mx, x, a0.re), fma(z.m, y, a0.im)};
@@ -389,7 +420,7 @@ struct TwDft;
 
 template <int DIR>
 struct TwDft<2, DIR> {
-  static __device__ __forceinline__ void run(F64::C* v, uint32_t tw) { tw_bfly(v[0], v[1], tw_load<DIR>(tw)); }
+  static __device__ __forceinline__ void run(F64::C* v, uint32_t tw) { tw_bfly<DIR>(v[0], v[1], tw_load<DIR>(tw)); }
 };
 
 template <int DIR>
@@ -397,11 +428,11 @@ struct TwDft<4, DIR> {
   using X = Cx<F64>;
   static __device__ __forceinline__ void run(F64::C* v, uint32_t tw) {
     const Tw z2 = tw_load<DIR>(tw), z1 = tw_load<DIR>(tw + 16u);
-    tw_bfly(v[0], v[2], z2);
-    tw_bfly(v[1], v[3], z2);
+    tw_bfly<DIR>(v[0], v[2], z2);
+    tw_bfly<DIR>(v[1], v[3], z2);
     F64::C b = X::template mul_i<DIR>(v[3]);
-    tw_bfly(v[0], v[1], z1);  // outputs 0, 2
-    tw_bfly(v[2], b, z1);     // outputs 1, 3
+    tw_bfly<DIR>(v[0], v[1], z1);  // outputs 0, 2
+    tw_bfly<DIR>(v[2], b, z1);     // outputs 1, 3
     const F64::C u2 = v[1];
     v[1] = v[2];
     v[2] = u2;
@@ -416,21 +447,21 @@ struct TwDft<8, DIR> {
     const Tw z4 = tw_load<DIR>(tw), z2 = tw_load<DIR>(tw + 16u);
     const Tw z1 = tw_load<DIR>(tw + 32u), z1w = tw_load<DIR>(tw + 48u);
 #pragma unroll
-    for (int t = 0; t < 4; ++t) tw_bfly(v[t], v[t + 4], z4);
+    for (int t = 0; t < 4; ++t) tw_bfly<DIR>(v[t], v[t + 4], z4);
     // even outputs: twiddled 4-point transform of v[0..3] with twiddle w
-    tw_bfly(v[0], v[2], z2);
-    tw_bfly(v[1], v[3], z2);
+    tw_bfly<DIR>(v[0], v[2], z2);
+    tw_bfly<DIR>(v[1], v[3], z2);
     F64::C be = X::template mul_i<DIR>(v[3]);
-    tw_bfly(v[0], v[1], z1);  // V0, V4
-    tw_bfly(v[2], be, z1);    // V2, V6
+    tw_bfly<DIR>(v[0], v[1], z1);  // V0, V4
+    tw_bfly<DIR>(v[2], be, z1);    // V2, V6
     // odd outputs: twiddled 4-point transform of v[4..7] with twiddle w omega ((w omega)^2 = w^2 DIR i)
     F64::C b6 = X::template mul_i<DIR>(v[6]);
     F64::C b7 = X::template mul_i<DIR>(v[7]);
-    tw_bfly(v[4], b6, z2);
-    tw_bfly(v[5], b7, z2);
+    tw_bfly<DIR>(v[4], b6, z2);
+    tw_bfly<DIR>(v[5], b7, z2);
     F64::C bo = X::template mul_i<DIR>(b7);
-    tw_bfly(v[4], v[5], z1w);  // V1, V5
-    tw_bfly(b6, bo, z1w);      // V3, V7
+    tw_bfly<DIR>(v[4], v[5], z1w);  // V1, V5
+    tw_bfly<DIR>(b6, bo, z1w);      // V3, V7
     const F64::C V1 = v[4], V2 = v[2], V4 = v[1], V5 = v[5];
     v[1] = V1;
     v[2] = V2;
@@ -745,15 +776,22 @@ __device__ __forceinline__ void stage(const Acc& A, int N, int B, int Ns, uint32
     const int b = A.b0 + bl;
     const int kk = j % Ns;
     const auto sq = A.seq(b);
+    // FP64 radix 8: the multipliers fold into the transform's first level (run_scaled)
+    constexpr bool fold_mul = (MODE & kMul) && std::is_same<P, F64>::value && R == 8;
     C v[R];
+    double mu[fold_mul ? R : 1];
 #pragma unroll
     for (int t = 0; t < R; ++t) {
       const int n = j + t * NR;
       C x = (MODE & kFirst) ? A.gather(sq, n) : (FROM_SLOTS ? A.slot_ld(sq, n) : A.lin_ld(b, n));
-      if ((MODE & kMul) && !sq.general) x = X::scale(x, A.mult(sq, n));
+      if constexpr (fold_mul) mu[t] = sq.general ? 1.0 : A.mult(sq, n);
+      else if ((MODE & kMul) && !sq.general) x = X::scale(x, A.mult(sq, n));
       v[t] = x;
     }
-    if constexpr (fma_twiddles<P, R>()) {
+    if constexpr (fold_mul) {
+      // kMul marks an inverse transform's first stage, which has no twiddles (Ns = 1)
+      Dft<F64, 8, DIR>::run_scaled(v, mu, k);
+    } else if constexpr (fma_twiddles<P, R>()) {
       if (Ns > 1) TwDft<R, DIR>::run(v, tw + 16u * (uint32_t)(kk * (R - 1)));
       else Dft<P, R, DIR>::run(v, k);
     } else {
