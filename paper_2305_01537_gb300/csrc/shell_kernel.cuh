@@ -759,11 +759,13 @@ struct PhiSplitAcc {
 enum { kFirst = 1, kLast = 2, kMul = 4 };
 
 // One radix-R Stockham stage over all B sequences: from the shell slots to the scratch (FROM_SLOTS)
-// or back. tw is the stage's own twiddle table: entry kk (R - 1) + t - 1 holds exp(-2 pi i t kk /
-// (Ns R)), so the R - 1 twiddles of a butterfly are adjacent and the threads of a quarter warp (kk
-// consecutive) read entries R - 1 apart: different banks for R = 2, 4, 8. kFirst reads the logical sequence out of the shell layout, kLast writes it back there,
-// kMul multiplies each input by the spectral multiplier (sequences flagged `general` were
-// multiplied before, by general_multiply).
+// or back. tw is the stage's own twiddle table of Ns (R - 1) entries, R - 1 per kk: entry
+// kk (R - 1) + t - 1 holds exp(-2 pi i t kk / (Ns R)) (compensated FP32 and radix 3), or the FP64
+// FMA-form factors of TwDft in the first slots of kk's group (FP64, R = 2, 4, 8). A butterfly's
+// twiddles are adjacent and the threads of a quarter warp (kk consecutive) read entries R - 1
+// apart: different banks for R = 2, 4, 8. kFirst reads the logical sequence out of the shell
+// layout, kLast writes it back there, kMul multiplies each input by the spectral multiplier
+// (sequences flagged `general` were multiplied before, by general_multiply).
 template <class P, class Acc, int R, int DIR, int MODE, bool FROM_SLOTS>
 __device__ __forceinline__ void stage(const Acc& A, int N, int B, int Ns, uint32_t tw, const Consts<P>& k) {
   using C = typename P::C;
