@@ -238,6 +238,17 @@ struct Cx {
     return DIR < 0 ? C{v.im, P::neg(v.re)} : C{P::neg(v.im), v.re};
   }
   static __device__ __forceinline__ C conj(C w) { return C{w.re, P::neg(w.im)}; }
+  // -v if `flip`, else v. In FP64 the sign bits change by integer operations: a negation chosen
+  // at run time would otherwise cost FP64 additions (the pipe that bounds the FP64 form).
+  static __device__ __forceinline__ C neg_if(C v, bool flip) {
+    if constexpr (std::is_same<T, double>::value) {
+      const int m = (int)((unsigned)flip << 31);
+      return C{__hiloint2double(__double2hiint(v.re) ^ m, __double2loint(v.re)),
+               __hiloint2double(__double2hiint(v.im) ^ m, __double2loint(v.im))};
+    } else {
+      return flip ? neg(v) : v;
+    }
+  }
 };
 
 // Constants of the radix kernels in the policy's precision (from FP64 host values).
@@ -562,13 +573,12 @@ struct ThetaAcc {
   __device__ __forceinline__ C gather(const Seq& s, int q) const {
     const bool up = q < Nth;
     const uint32_t a = el(up ? q : M - 1 - q, up ? 2 * s.b : 2 * s.b + h);
-    C v = s.lone ? C{P::ld8(a), P::zero()} : pair_ld(a, hodd && !up);
-    if (!up && odd) v = Cx<P>::neg(v);
-    return v;
+    const C v = s.lone ? C{P::ld8(a), P::zero()} : pair_ld(a, hodd && !up);
+    return Cx<P>::neg_if(v, !up && odd);
   }
   __device__ __forceinline__ void scatter(const Seq& s, int q, C v) const {
     const bool up = q < Nth;
-    if (!up && odd) v = Cx<P>::neg(v);
+    v = Cx<P>::neg_if(v, !up && odd);
     const uint32_t a = el(up ? q : M - 1 - q, up ? 2 * s.b : 2 * s.b + h);
     if (s.lone) P::st8(a, v.re);
     else pair_st(a, hodd && !up, v);
@@ -1026,14 +1036,13 @@ struct SpecAcc {
   __device__ __forceinline__ T phi_mult(int j, int m) const { return P::from_tab(gtab, gbase + (size_t)j * nh + m); }
   __device__ __forceinline__ C gather(const Seq& s, int n) const {
     const int j = row_of(n);
-    C v = P::ld16(el(j, s.m));
-    if (s.odd && (j & 1)) v = Cx<P>::neg(v);
+    C v = Cx<P>::neg_if(P::ld16(el(j, s.m)), s.odd && (j & 1));
     if (phi_first) v = Cx<P>::scale(v, phi_mult(j, s.m));
     return v;
   }
   __device__ __forceinline__ void scatter(const Seq& s, int n, C v) const {
     const int j = row_of(n);
-    if (s.odd && (j & 1)) v = Cx<P>::neg(v);
+    v = Cx<P>::neg_if(v, s.odd && (j & 1));
     if (!phi_first) v = Cx<P>::scale(v, phi_mult(j, s.m));
     P::st16(el(j, s.m), v);
   }
