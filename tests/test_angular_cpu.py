@@ -85,7 +85,7 @@ def _run(shape, Pth, Pph, mode):
     return g, full
 
 
-@pytest.mark.parametrize("Pth,Pph", [(2, 1), (1, 2), (2, 2)])
+@pytest.mark.parametrize("Pth,Pph", [(2, 1), (1, 2), (2, 2), (3, 1)])
 def test_matches_whole_state_filter(Pth, Pph):
     import sys
     sys.path.insert(0, ROOT)
